@@ -1,0 +1,169 @@
+/*
+ * sgw.h -- C ABI of the GB300 shifted-Sternheimer library.
+ *
+ * The library solves, for every right-hand side r and frequency omega_j,
+ *
+ *     (P_c H P_c - z_rj) dpsi_rj = -P_c rhs_r,     z_rj = e_ref[r] + omega_j + i eta,
+ *
+ * the Sternheimer equation of SternheimerGW (arXiv:1812.03717, Sec. 2.3, Eq. 6) with the
+ * Coulomb-response operator of Eq. 7 read as H restricted to the conduction subspace
+ * (P_c = 1 - sum_v |psi_v><psi_v|; on b in range(P_c) this has the same solution as
+ * H + alpha P_occ - z for any alpha > 0), and the driving field of Eq. 8 given by the
+ * caller as rhs_r = dV psi_v expressed in this system's plane-wave basis.  All shifts
+ * of one right-hand side share one Krylov space (Sec. 2.2): one seed system carries them.
+ *
+ * Units: Hartree atomic units (Ha, bohr).  E_cut is in Ry: the basis of Eq. 1 is the
+ * sphere |k+G|^2 <= E_cut[Ry] (bohr^-2).  Complex numbers are interleaved FP64 pairs
+ * (re, im) = C99 double complex / numpy complex128.
+ *
+ * Memory: every vector argument marked "host or device" may be a host pointer or a CUDA
+ * device pointer of the current device; the library detects which.  The library copies
+ * what it keeps (the system owns its device copies); the caller owns every buffer it
+ * passes.  Work is ordered on the stream given (NULL = the legacy default stream); calls
+ * that return results to host memory synchronise that stream before returning.
+ *
+ * Errors: every call returns an sgw_status; nothing throws across the ABI and nothing
+ * aborts.  sgw_last_error() returns a message for the last failing call of this host
+ * thread.  A system handle must be used by one host thread at a time.
+ */
+#ifndef SGW_H
+#define SGW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgw_system sgw_system;   /* opaque, owned by the library */
+
+typedef enum {
+    SGW_OK = 0,
+    SGW_EINVAL = 1,       /* invalid argument (sizes, NaN/Inf, eta <= 0, non-orthonormal psi_v, ...) */
+    SGW_ENOMEM = 2,       /* device allocation failed */
+    SGW_ECUDA = 3,        /* a CUDA call failed; the message names it */
+    SGW_ENOCONV = 4,      /* some (rhs, omega) pair missed the tolerance; results and report still written */
+    SGW_EALIAS = 5,       /* FFT box smaller than 2 m_rho + 1 along some axis */
+    SGW_ESTATE = 6,       /* call out of order (e.g. solve before sgw_set_occupied) */
+    SGW_EUNSUPPORTED = 7  /* a size this build does not handle (named in the message) */
+} sgw_status;
+
+/* Per-pair status codes written to sgw_report.status. */
+enum {
+    SGW_PAIR_CONVERGED = 0,
+    SGW_PAIR_MAXITER = 1,    /* matrix-vector budget exhausted */
+    SGW_PAIR_BREAKDOWN = 2,  /* a Krylov denominator vanished */
+    SGW_PAIR_NONFINITE = 3   /* a NaN/Inf appeared in the recurrences */
+};
+
+typedef struct {
+    double a[3][3];        /* rows = lattice vectors a1, a2, a3 (bohr) */
+    int n_atoms;
+    const double* tau;     /* [n_atoms][3] Cartesian positions (bohr), host */
+} sgw_cell;
+
+/* Kleinman-Bylander non-local part, one s-type Gaussian projector per entry:
+ * beta_p(r) = (pi w_p^2)^(-3/4) exp(-|r - tau_{atom[p]}|^2 / (2 w_p^2)),
+ * V_NL = sum_p |beta_p> D_p <beta_p|  (Sec. 2.1: non-local part applied in reciprocal space). */
+typedef struct {
+    int n_proj;
+    const int* atom;       /* [n_proj] atom index of each projector, host */
+    const double* width;   /* [n_proj] w_p (bohr), host */
+    const double* D;       /* [n_proj] D_p (Ha), host */
+} sgw_kb;
+
+/* Builds the plane-wave basis of Eq. 1 at Bloch vector k (the basis the response lives
+ * in: k+q in perturbation-theory terms) and uploads the Hamiltonian of Sec. 2.1.
+ *   cell      lattice and atoms (host).
+ *   ecut_ry   E_cut in Ry (> 0).
+ *   k_frac    k in fractional coordinates of the reciprocal lattice (host, 3 doubles).
+ *   fft_dims  box N1, N2, N3 (host); each must factor into 2, 3 and 5 and satisfy
+ *             N_i >= 2 m_rho,i + 1 with m_rho the largest |Miller index| of |G|^2 <= 4 E_cut
+ *             (else SGW_EALIAS).
+ *   vloc_r    real local potential V(r_j) on the box, r_j = sum_i (j_i / N_i) a_i, C order
+ *             [N1][N2][N3] (host), Ha.
+ *   kb        projectors (host arrays; n_proj may be 0).
+ *   out       receives the handle.
+ * The sphere is built on the GPU with an FP64 test evaluated without fused multiply-add:
+ *   k_x = (k1 b1x + k2 b2x) + k3 b3x,  g_x = ((k_x + m1 b1x) + m2 b2x) + m3 b3x,
+ *   |k+G|^2 = (g_x^2 + g_y^2) + g_z^2 <= E_cut, Miller triples in lexicographic order
+ *   (m1 outermost, each ascending): the canonical order of every coefficient array. */
+sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double k_frac[3],
+                             const int fft_dims[3], const double* vloc_r, const sgw_kb* kb,
+                             sgw_system** out);
+
+/* Number of plane waves; optionally the Miller triples [n_pw][3] and kinetic energies
+ * |k+G|^2 / 2 (Ha) [n_pw] in canonical order (host buffers, or NULL). */
+sgw_status sgw_get_gvectors(const sgw_system* sys, int* n_pw, int* miller, double* kin);
+
+/* Sphere -> box map, entry g = ((m1 mod N1) N2 + (m2 mod N2)) N3 + (m3 mod N3), host int[n_pw]. */
+sgw_status sgw_get_box_map(const sgw_system* sys, int* map);
+
+/* Occupied manifold of this basis (Eq. 7-8: P_occ): psi_v complex [n_occ][n_pw] (host or
+ * device) and eps_v [n_occ] (host, Ha).  Rejected with SGW_EINVAL unless
+ * max |psi^H psi - I| <= 1e-10.  May be called again to replace the manifold. */
+sgw_status sgw_set_occupied(sgw_system* sys, int n_occ, const void* psi_v, const double* eps_v);
+
+/* Driving field of Eq. 8 for the periodic perturbations dV = exp(i (q + G_p).r):
+ *   rhs[v * n_pert + p][G'] = psi_k[v][G' - G_p]  if G' - G_p is in sys_k's sphere, else 0,
+ * for G' in sys_kq's sphere (sys_kq at k+q, sys_k at k).  psi_k complex [n_v][n_pw(sys_k)]
+ * (host or device); gp_miller int [n_pert][3] (host); rhs complex [n_v*n_pert][n_pw(sys_kq)]
+ * (host or device).  An exact gather: bit-identical to the definition. */
+sgw_status sgw_make_rhs(const sgw_system* sys_kq, const sgw_system* sys_k, int n_v, const void* psi_k,
+                        int n_pert, const int* gp_miller, void* rhs, void* stream);
+
+/* y = H x for nvec vectors [nvec][n_pw] (host or device): kinetic + non-local in
+ * reciprocal space, local through the FFT box (Sec. 2.1).  Test hook. */
+sgw_status sgw_apply_h(sgw_system* sys, int nvec, const void* x, void* y, void* stream);
+
+/* y_i = (P_c H P_c - z_i) x_i, z complex [nvec] as (re, im) pairs (host).  Requires
+ * sgw_set_occupied.  Test hook for the operator the solver iterates with. */
+sgw_status sgw_apply_shifted(sgw_system* sys, int nvec, const void* x, const double* z, void* y,
+                             void* stream);
+
+typedef struct {
+    int ell;          /* degree of the minimal-residual polynomial of BiCGstab(ell): 1, 2 or 4 (0 -> 4) */
+    int seed_index;   /* shift that carries the Krylov space; -1 -> the largest omega */
+    int max_matvec;   /* matrix-vector budget per right-hand side (0 -> 40000) */
+    void* stream;     /* cudaStream_t, NULL = default stream */
+} sgw_solve_opts;
+
+/* Per-pair outputs, each [nrhs][nomega] host arrays (any may be NULL). */
+typedef struct {
+    int* matvecs;       /* H applications spent when the pair converged (or the budget) */
+    double* est_res;    /* recursive residual estimate |r| / |b| at exit */
+    int* status;        /* SGW_PAIR_* */
+} sgw_report;
+
+/* Multishift solve (the hot path).  For every r < nrhs and j < nomega solves
+ *   (P_c H P_c - z_rj) dpsi[r][j] = -P_c rhs[r],   z_rj = e_ref[r] + omega[j] + i eta
+ * with a shifted BiCGstab(ell) (Frommer 2003, the solver the paper cites in Sec. 2.2):
+ * one seed system per right-hand side builds the Krylov space, every shift is advanced
+ * from the seed's vectors through scalar recurrences, and a shift stops updating once its
+ * residual estimate drops to tol |b|.
+ *   rhs    complex [nrhs][n_pw] (host or device): dV psi_v in this basis.
+ *   e_ref  [nrhs] host, Ha.   omega [nomega] host, Ha.   eta > 0 (Ha), else SGW_EINVAL.
+ *   tol    relative residual target (e.g. 1e-10).
+ *   dpsi   complex [nrhs][nomega][n_pw] (host or device), overwritten.
+ *   report optional per-pair report.
+ * A zero right-hand side gives dpsi = 0 with status CONVERGED.  Returns SGW_ENOCONV if any
+ * pair missed tol (results and report are still written). */
+sgw_status sgw_solve_shifted(sgw_system* sys, int nrhs, const void* rhs, const double* e_ref,
+                             int nomega, const double* omega, double eta, double tol,
+                             const sgw_solve_opts* opts, void* dpsi, sgw_report* report);
+
+/* True FP64 residual of given solutions: for every pair
+ *   r = -P_c rhs - (P_c H P_c - z) dpsi,  rel_res = |r| / |P_c rhs|,  cert = |r| / (eta |dpsi|).
+ * Since P_c H P_c - z is normal with every eigenvalue at distance >= eta from 0, cert bounds
+ * the relative error |dpsi - dpsi*| / |dpsi|.  rel_res, cert: host [nrhs][nomega] (either may be NULL). */
+sgw_status sgw_residual(sgw_system* sys, int nrhs, const void* rhs, const double* e_ref, int nomega,
+                        const double* omega, double eta, const void* dpsi, double* rel_res,
+                        double* cert, void* stream);
+
+void sgw_destroy_system(sgw_system* sys);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* sgw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGW_H */

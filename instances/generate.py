@@ -1,0 +1,284 @@
+"""Seeded synthetic instances of the shifted Sternheimer problem (SternheimerGW, Sec. 2.1-2.3).
+
+This module is the one input generator that both the CUDA path and the CPU oracle consume.
+It builds what the method takes as *given*:
+
+* the crystal (lattice rows a_i in bohr, atom positions), the cutoff and the FFT box;
+* the local potential sampled on the FFT box, V_loc(r_j) (a real array: what the
+  library receives), made of one Gaussian v(r) = A exp(-r^2 / (2 sigma^2)) per atom with
+  A = -4 Ha, sigma = 0.9 bohr, band-limited to |G|^2 <= 4 E_cut;
+* one s-type Gaussian Kleinman-Bylander projector per atom (width 0.9 bohr, D = +1 Ha);
+* k-points, q, the perturbation wave vectors G_p, the frequencies omega_j and eta;
+* the Kohn-Sham ground state (occupied psi_v and eps_v at k and at k+q).  In the paper
+  this comes from a DFT code (Sec. 2.1); here a dense FP64 diagonalisation of the
+  synthetic Hamiltonian stands in for that code.  It uses the closed-form Fourier
+  coefficients of the potential, not the sampled box, so it is a different numerical
+  route from the one the oracle and the CUDA path take.
+
+Units: Hartree atomic units (energy Ha, length bohr); E_cut is given in Ry, so the
+plane-wave sphere is |k+G|^2 <= E_cut[Ry] in bohr^-2.  Random draws use numpy's PCG64
+(``numpy.random.default_rng(seed)``); the draw order is documented at each config.
+
+The G-sphere enumeration below follows the library's documented canonical order
+(Miller triples lexicographic, m1 outermost, each ascending) and its documented FP64
+membership test, so that coefficient arrays line up between producer and consumers.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+import scipy.linalg
+
+HA_EV = 27.211386245988          # eV per Hartree (CODATA 2018)
+VLOC_DEPTH = -4.0                # Ha
+VLOC_SIGMA = 0.9                 # bohr
+KB_WIDTH = 0.9                   # bohr
+KB_D = 1.0                       # Ha
+BOUNDARY_MARGIN = 1e-10          # relative distance from the sphere surface no G may have
+
+
+@dataclass
+class KPointData:
+    k_frac: np.ndarray                # Bloch vector of the unperturbed states (fractional, of B)
+    kq_frac: np.ndarray               # k+q: basis the response lives in
+    miller_k: np.ndarray              # int32 [npw_k][3]
+    miller_kq: np.ndarray             # int32 [npw_kq][3]
+    psi_k: np.ndarray                 # c128 [n_occ][npw_k]
+    eps_k: np.ndarray                 # f64 [n_occ]
+    psi_kq: np.ndarray                # c128 [n_occ][npw_kq]
+    eps_kq: np.ndarray                # f64 [n_occ]
+    gap_k: float = 0.0
+    gap_kq: float = 0.0
+
+
+@dataclass
+class Instance:
+    name: str
+    seed: int
+    a: np.ndarray                     # [3][3], rows = lattice vectors, bohr
+    tau: np.ndarray                   # [n_atoms][3] cartesian bohr
+    ecut_ry: float
+    fft_dims: tuple
+    vloc_r: np.ndarray                # f64 [N1][N2][N3] (C order), Ha
+    kb_atom: np.ndarray               # int32 [n_proj]
+    kb_width: np.ndarray              # f64 [n_proj]
+    kb_d: np.ndarray                  # f64 [n_proj]
+    n_occ: int
+    gp_miller: np.ndarray             # int32 [n_pert][3]
+    omega: np.ndarray                 # f64 [n_omega], Ha
+    eta: float                        # Ha
+    kpoints: list = field(default_factory=list)
+
+    @property
+    def n_pert(self) -> int:
+        return len(self.gp_miller)
+
+    @property
+    def volume(self) -> float:
+        return abs(float(np.linalg.det(self.a)))
+
+    def e_ref(self, ik: int) -> np.ndarray:
+        """eps_{v,k} for each right-hand side r = v * n_pert + p of k-point ik."""
+        return np.repeat(self.kpoints[ik].eps_k, self.n_pert)
+
+
+# ----------------------------------------------------------------------------- lattice
+
+def recip(a: np.ndarray) -> np.ndarray:
+    """Rows b_i with a_i . b_j = 2 pi delta_ij."""
+    return 2.0 * math.pi * np.linalg.inv(np.asarray(a, dtype=np.float64)).T
+
+
+def _kcart(k_frac, b):
+    k = np.asarray(k_frac, dtype=np.float64)
+    return (k[0] * b[0] + k[1] * b[1]) + k[2] * b[2]
+
+
+def sphere(a, k_frac, ecut_ry, check_margin=True):
+    """Canonical plane-wave sphere {m : |k + m.B|^2 <= ecut}; returns (miller int32, |k+G|^2)."""
+    b = recip(a)
+    kc = _kcart(k_frac, b)
+    amax = np.linalg.norm(a, axis=1)
+    kf = np.abs(np.asarray(k_frac, dtype=np.float64))
+    bound = [int(math.floor(math.sqrt(ecut_ry) * amax[i] / (2 * math.pi) + kf[i])) + 1 for i in range(3)]
+    r = [np.arange(-bound[i], bound[i] + 1) for i in range(3)]
+    m1, m2, m3 = np.meshgrid(r[0], r[1], r[2], indexing="ij")
+    m1 = m1.ravel().astype(np.float64)
+    m2 = m2.ravel().astype(np.float64)
+    m3 = m3.ravel().astype(np.float64)
+    g = [((kc[x] + m1 * b[0, x]) + m2 * b[1, x]) + m3 * b[2, x] for x in range(3)]
+    n2 = (g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]
+    near = np.abs(n2 - ecut_ry) < BOUNDARY_MARGIN * ecut_ry
+    if check_margin and np.any(near):
+        raise ValueError("a plane wave lies within the boundary margin of the cutoff sphere")
+    keep = n2 <= ecut_ry
+    mil = np.stack([m1[keep], m2[keep], m3[keep]], axis=1).astype(np.int32)
+    return mil, n2[keep]
+
+
+# ------------------------------------------------------------------ synthetic potential
+
+def vloc_coeffs(a, tau, mil):
+    """Closed-form Fourier coefficients V(G) of the periodic sum of atomic Gaussians."""
+    b = recip(a)
+    omega_cell = abs(np.linalg.det(a))
+    g = mil.astype(np.float64) @ b
+    g2 = np.einsum("ij,ij->i", g, g)
+    pref = VLOC_DEPTH * (2 * math.pi * VLOC_SIGMA ** 2) ** 1.5 / omega_cell
+    sf = np.exp(-1j * (g @ np.asarray(tau).T)).sum(axis=1)
+    return pref * np.exp(-0.5 * VLOC_SIGMA ** 2 * g2) * sf
+
+
+def vloc_box(a, tau, ecut_ry, dims):
+    """V_loc(r_j) on the box, r_j = sum_i (j_i / N_i) a_i; V(G) kept for |G|^2 <= 4 E_cut."""
+    mil, _ = sphere(a, (0.0, 0.0, 0.0), 4.0 * ecut_ry, check_margin=False)
+    for i in range(3):
+        if dims[i] < 2 * int(np.abs(mil[:, i]).max()) + 1:
+            raise ValueError("FFT box too small for the band-limited potential")
+    vg = vloc_coeffs(a, tau, mil)
+    box = np.zeros(dims, dtype=np.complex128)
+    idx = tuple(np.mod(mil[:, i], dims[i]) for i in range(3))
+    box[idx] = vg
+    vr = np.fft.ifftn(box) * (dims[0] * dims[1] * dims[2])
+    if np.abs(vr.imag).max() > 1e-12 * max(1.0, np.abs(vr.real).max()):
+        raise AssertionError("potential is not real")
+    return np.ascontiguousarray(vr.real)
+
+
+def kb_coeffs(a, tau, k_frac, mil, width):
+    """<k+G|beta_a> for s-type Gaussian projectors, one per atom: [n_atoms][npw]."""
+    b = recip(a)
+    omega_cell = abs(np.linalg.det(a))
+    kg = mil.astype(np.float64) @ b + _kcart(k_frac, b)
+    kg2 = np.einsum("ij,ij->i", kg, kg)
+    out = []
+    for ia, t in enumerate(np.asarray(tau)):
+        w = width[ia]
+        amp = omega_cell ** -0.5 * (4 * math.pi * w * w) ** 0.75 * np.exp(-0.5 * w * w * kg2)
+        out.append(amp * np.exp(-1j * (kg @ t)))
+    return np.array(out)
+
+
+def ground_state(inst: Instance, k_frac, n_bands: int):
+    """Lowest n_bands eigenpairs of the synthetic Hamiltonian at k (stand-in for the DFT input)."""
+    mil, n2 = sphere(inst.a, k_frac, inst.ecut_ry)
+    b = recip(inst.a)
+    d = mil[:, None, :] - mil[None, :, :]
+    flat = d.reshape(-1, 3)
+    uniq, inv = np.unique(flat, axis=0, return_inverse=True)
+    vg = vloc_coeffs(inst.a, inst.tau, uniq)
+    g2 = np.einsum("ij,ij->i", uniq @ b, uniq @ b)
+    vg[g2 > 4.0 * inst.ecut_ry * (1 + 1e-12)] = 0.0
+    h = vg[inv.ravel()].reshape(len(mil), len(mil))
+    h[np.diag_indices(len(mil))] += 0.5 * n2
+    beta = kb_coeffs(inst.a, inst.tau, k_frac, mil, inst.kb_width)
+    for p in range(len(inst.kb_atom)):
+        bp = beta[inst.kb_atom[p]]
+        h += inst.kb_d[p] * np.outer(bp, bp.conj())
+    h = 0.5 * (h + h.conj().T)
+    w, v = scipy.linalg.eigh(h, subset_by_index=[0, n_bands])
+    return mil, np.ascontiguousarray(v[:, :n_bands].T), w[:n_bands], float(w[n_bands] - w[n_bands - 1])
+
+
+# ------------------------------------------------------------------------ perturbations
+
+def shortest_g(a, count, include_zero=True):
+    """The `count` shortest G, ranked by |G|^2, ties broken by the Miller triple ascending."""
+    b = recip(a)
+    rng_m = 4
+    while True:
+        r = np.arange(-rng_m, rng_m + 1)
+        m = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+        if not include_zero:
+            m = m[np.any(m != 0, axis=1)]
+        g = m.astype(np.float64) @ b
+        g2 = np.round(np.einsum("ij,ij->i", g, g), 10)
+        order = np.lexsort((m[:, 2], m[:, 1], m[:, 0], g2))
+        sel = m[order[:count]]
+        if np.abs(sel).max() < rng_m:
+            return sel.astype(np.int32)
+        rng_m *= 2
+
+
+# ------------------------------------------------------------------------------ configs
+
+def fcc_cell(alat):
+    a = np.array([[0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]]) * alat
+    tau = np.array([[0.0, 0.0, 0.0], [0.25, 0.25, 0.25]]) * alat
+    return a, tau
+
+
+DIAMOND_FRAC = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
+                         [.25, .25, .25], [.25, .75, .75], [.75, .25, .75], [.75, .75, .25]])
+
+
+def cubic8_cell(alat):
+    return np.eye(3) * alat, DIAMOND_FRAC * alat
+
+
+def make_instance(name, seed, a, tau, ecut_ry, dims, n_occ, kq_pairs, gp, omega, eta):
+    n_at = len(tau)
+    inst = Instance(name=name, seed=seed, a=np.asarray(a, float), tau=np.asarray(tau, float),
+                    ecut_ry=float(ecut_ry), fft_dims=tuple(int(x) for x in dims),
+                    vloc_r=vloc_box(a, tau, ecut_ry, dims),
+                    kb_atom=np.arange(n_at, dtype=np.int32),
+                    kb_width=np.full(n_at, KB_WIDTH), kb_d=np.full(n_at, KB_D),
+                    n_occ=int(n_occ), gp_miller=np.asarray(gp, np.int32),
+                    omega=np.asarray(omega, float), eta=float(eta))
+    for k, kq in kq_pairs:
+        mk, pk, ek, gk = ground_state(inst, k, n_occ)
+        mq, pq, eq, gq = ground_state(inst, kq, n_occ)
+        inst.kpoints.append(KPointData(k_frac=np.asarray(k, float), kq_frac=np.asarray(kq, float),
+                                       miller_k=mk, miller_kq=mq, psi_k=pk, eps_k=ek,
+                                       psi_kq=pq, eps_kq=eq, gap_k=gk, gap_kq=gq))
+    return inst
+
+
+def _frac_of_cart(a, v_cart):
+    """Fractional coordinates (of B) of a cartesian reciprocal-space vector."""
+    return np.asarray(v_cart, float) @ np.asarray(a, float).T / (2 * math.pi)
+
+
+def config1(seed: int = 0, ecut_ry: float = 10.0, dims=(16, 16, 16), n_occ: int = 4,
+            n_pert: int = 8, n_omega: int = 16):
+    """fcc Si-like cell a = 10.26 bohr, k = Gamma, q = (0.1,0,0) 2pi/a, 8 shortest G,
+    omega = linspace(0, 50 eV, 16), eta = 0.1 eV.  No random draws (seed is recorded only)."""
+    alat = 10.26
+    a, tau = fcc_cell(alat)
+    q = _frac_of_cart(a, np.array([0.1, 0.0, 0.0]) * 2 * math.pi / alat)
+    k = np.zeros(3)
+    omega = np.linspace(0.0, 50.0, n_omega) / HA_EV
+    return make_instance("fcc2-ecut%g" % ecut_ry, seed, a, tau, ecut_ry, dims, n_occ,
+                         [(k, k + q)], shortest_g(a, n_pert, True), omega, 0.1 / HA_EV)
+
+
+def tiny_fcc(ecut_ry: float = 4.0, dims=(12, 12, 12), n_occ: int = 4, n_pert: int = 3,
+             n_omega: int = 5, q_cart=(0.1, 0.0, 0.0)):
+    """Small-basis variant of config1 for brute-force checks (tens of plane waves)."""
+    alat = 10.26
+    a, tau = fcc_cell(alat)
+    q = _frac_of_cart(a, np.asarray(q_cart) * 2 * math.pi / alat)
+    omega = np.linspace(0.0, 50.0, n_omega) / HA_EV
+    return make_instance("tiny-fcc-ecut%g" % ecut_ry, 0, a, tau, ecut_ry, dims, n_occ,
+                         [(np.zeros(3), q)], shortest_g(a, n_pert, True), omega, 0.1 / HA_EV)
+
+
+def config2(seed: int = 0, n_k: int = 4, ecut_ry: float = 20.0, dims=(36, 36, 36),
+            n_occ: int = 16, n_pert: int = 32, n_omega: int = 64, k_subset=None):
+    """8-atom cubic diamond cell a = 10.26 bohr, ecut 20 Ry, 36^3 box, 16 occupied bands,
+    32 shortest G, omega = linspace(0, 60 eV, 64), eta = 0.1 eV.
+    Draws: rng = default_rng(seed); k = rng.uniform(-1/2, 1/2, (n_k, 3)) then
+    q = rng.uniform(-1/2, 1/2, 3), all fractional coordinates of B."""
+    alat = 10.26
+    a, tau = cubic8_cell(alat)
+    rng = np.random.default_rng(seed)
+    ks = rng.uniform(-0.5, 0.5, size=(n_k, 3))
+    q = rng.uniform(-0.5, 0.5, size=3)
+    pairs = [(k, k + q) for k in ks]
+    if k_subset is not None:
+        pairs = [pairs[i] for i in k_subset]
+    omega = np.linspace(0.0, 60.0, n_omega) / HA_EV
+    return make_instance("cubic8-ecut%g" % ecut_ry, seed, a, tau, ecut_ry, dims, n_occ,
+                         pairs, shortest_g(a, n_pert, True), omega, 0.1 / HA_EV)

@@ -1,0 +1,237 @@
+"""Plain FP64 CPU oracle for the shifted Sternheimer solve (SternheimerGW, Sec. 2.1-2.3).
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import or run this module:
+only the tests, the smoke check and the timed CPU-baseline leg of the benchmark use it.
+It shares no code with the CUDA library; both consume the same seeded inputs.
+
+What it computes, by plain definition (no blocking, fusion or reordering):
+
+* the plane-wave basis of Eq. 1: the sphere {G : |k+G|^2 <= E_cut[Ry]} in canonical
+  order (Miller triples lexicographic, m1 outermost), kinetic energies |k+G|^2 / 2;
+* the sphere -> FFT-box map ((m1 mod N1) N2 + (m2 mod N2)) N3 + (m3 mod N3);
+* the dense Hamiltonian of Sec. 2.1 in that basis: kinetic and non-local
+  (Kleinman-Bylander) parts in reciprocal space, the local potential through the
+  discrete Fourier transform of its samples on the box, i.e.
+  H[G,G'] = T_G delta + Vhat((m_G - m_G') mod N) + sum_p D_p beta_p(k+G) conj(beta_p(k+G'));
+* the right-hand side of Eq. 8 for the periodic perturbation exp(i(q+G_p).r): the
+  occupied state at k re-expressed in the k+q basis (an exact gather of coefficients),
+  then b = -P_c rhs with P_c = 1 - sum_v |psi_v><psi_v| (the sign follows the problem
+  statement -P_c dV psi_v; Eq. 8 prints +(1 - P_occ), a global sign);
+* the solution of the Sternheimer equation Eq. 6 with the Coulomb-response operator of
+  Eq. 7 read as (P_c H P_c - z) dpsi = b, z = eps_v + omega + i eta, by one dense LU per
+  shift;
+* the sum over all unoccupied eigenstates of the finite basis, which equals that
+  solution (used to pin it on tiny bases);
+* the true residual and the a-posteriori error certificate |r| / (eta |dpsi|).
+
+Each function cites the passage of the paper it restates.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg
+
+
+# ------------------------------------------------------------------------- Eq. 1 basis
+
+def reciprocal(a):
+    """Reciprocal lattice rows b_i = 2 pi (a_j x a_k) / Omega (cyclic), Omega = a_1.(a_2 x a_3)."""
+    a = np.asarray(a, dtype=np.float64)
+    vol = float(np.dot(a[0], np.cross(a[1], a[2])))
+    return np.array([np.cross(a[1], a[2]), np.cross(a[2], a[0]), np.cross(a[0], a[1])]) * (2 * math.pi / vol)
+
+
+def cell_volume(a):
+    a = np.asarray(a, dtype=np.float64)
+    return abs(float(np.dot(a[0], np.cross(a[1], a[2]))))
+
+
+def gsphere(a, k_frac, ecut_ry):
+    """Plane waves of Eq. 1 kept by the cutoff: Miller triples m with |k + m.B|^2 <= E_cut[Ry].
+
+    The membership test is evaluated in FP64 in a fixed order without fused multiply-add:
+    k_x = (k1 b1x + k2 b2x) + k3 b3x;  g_x = ((k_x + m1 b1x) + m2 b2x) + m3 b3x;
+    |g|^2 = (g_x g_x + g_y g_y) + g_z g_z.  Order: m1 outermost, m3 innermost, ascending.
+    Returns (miller int32 [npw][3], kinetic f64 [npw] = |k+G|^2 / 2).
+    """
+    b = reciprocal(a)
+    k = np.asarray(k_frac, dtype=np.float64)
+    kc = [(k[0] * b[0, x] + k[1] * b[1, x]) + k[2] * b[2, x] for x in range(3)]
+    lengths = [math.sqrt(float(np.dot(a[i], a[i]))) for i in range(3)]
+    # |m_i + k_i| = |(k+G).a_i| / 2pi <= sqrt(E_cut) |a_i| / 2pi
+    bound = [int(math.ceil(math.sqrt(ecut_ry) * lengths[i] / (2 * math.pi) + abs(k[i]))) for i in range(3)]
+    m1, m2, m3 = np.meshgrid(np.arange(-bound[0], bound[0] + 1), np.arange(-bound[1], bound[1] + 1),
+                             np.arange(-bound[2], bound[2] + 1), indexing="ij")
+    m = np.stack([m1.ravel(), m2.ravel(), m3.ravel()], axis=1)
+    mf = m.astype(np.float64)
+    g = [((kc[x] + mf[:, 0] * b[0, x]) + mf[:, 1] * b[1, x]) + mf[:, 2] * b[2, x] for x in range(3)]
+    n2 = (g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]
+    keep = n2 <= ecut_ry
+    return m[keep].astype(np.int32), 0.5 * n2[keep]
+
+
+def box_map(miller, dims):
+    """Sphere -> box linear index, box stored C order [N1][N2][N3] (axis 3 fastest)."""
+    m = np.asarray(miller, dtype=np.int64)
+    n1, n2, n3 = dims
+    return (((m[:, 0] % n1) * n2 + (m[:, 1] % n2)) * n3 + (m[:, 2] % n3)).astype(np.int32)
+
+
+def min_box(a, ecut_ry):
+    """Smallest alias-free box: N_i >= 2 max|m_i| + 1 over the potential's sphere |G|^2 <= 4 E_cut."""
+    mil, _ = gsphere(a, (0.0, 0.0, 0.0), 4.0 * ecut_ry)
+    return tuple(2 * int(np.abs(mil[:, i]).max()) + 1 for i in range(3))
+
+
+# --------------------------------------------------------------- Sec. 2.1 Hamiltonian
+
+def vloc_hat(vloc_r):
+    """Vhat(n) = N^-3 sum_j V(r_j) exp(-2 pi i n.j / N): the potential's coefficients on the box."""
+    v = np.asarray(vloc_r, dtype=np.float64)
+    return np.fft.fftn(v) / v.size
+
+
+def kb_beta(a, tau, k_frac, miller, kb_atom, kb_width):
+    """<k+G|beta_p> for s-type Gaussian projectors beta(r) = (pi w^2)^(-3/4) exp(-r^2 / 2w^2)
+    centred on atom tau_{atom[p]}: Omega^(-1/2) (4 pi w^2)^(3/4) exp(-w^2 |k+G|^2 / 2) exp(-i (k+G).tau).
+    Returns [n_proj][npw] c128."""
+    b = reciprocal(a)
+    vol = cell_volume(a)
+    kg = (np.asarray(miller, np.float64) + np.asarray(k_frac, np.float64)[None, :]) @ b
+    kg2 = np.sum(kg * kg, axis=1)
+    out = np.empty((len(kb_atom), len(miller)), dtype=np.complex128)
+    for p, (ia, w) in enumerate(zip(kb_atom, kb_width)):
+        t = np.asarray(tau, np.float64)[ia]
+        out[p] = vol ** -0.5 * (4 * math.pi * w * w) ** 0.75 * np.exp(-0.5 * w * w * kg2) \
+            * np.exp(-1j * (kg @ t))
+    return out
+
+
+def dense_h(a, tau, ecut_ry, k_frac, dims, vloc_r, kb_atom, kb_width, kb_d):
+    """Dense H_k of Sec. 2.1 in the plane-wave basis of Eq. 1.  Returns (H, miller, kinetic)."""
+    miller, kin = gsphere(a, k_frac, ecut_ry)
+    vh = vloc_hat(vloc_r)
+    n = len(miller)
+    h = np.zeros((n, n), dtype=np.complex128)
+    for i in range(n):
+        d = (miller[i][None, :] - miller) % np.asarray(dims)[None, :]
+        h[i, :] = vh[d[:, 0], d[:, 1], d[:, 2]]
+    h[np.diag_indices(n)] += kin
+    beta = kb_beta(a, tau, k_frac, miller, kb_atom, kb_width)
+    for p in range(len(kb_d)):
+        h += kb_d[p] * np.outer(beta[p], beta[p].conj())
+    return h, miller, kin
+
+
+def dense_h_inst(inst, k_frac):
+    return dense_h(inst.a, inst.tau, inst.ecut_ry, k_frac, inst.fft_dims, inst.vloc_r,
+                   inst.kb_atom, inst.kb_width, inst.kb_d)
+
+
+def apply_h_fft(a, tau, ecut_ry, k_frac, dims, vloc_r, kb_atom, kb_width, kb_d, x):
+    """Matrix-free H x as Sec. 2.1 describes it: kinetic and non-local in reciprocal
+    space, V_loc in real space via FFT (numpy's).  x: [nvec][npw].  Used as the
+    matrix-free CPU comparison; it must equal dense_h(...) @ x."""
+    miller, kin = gsphere(a, k_frac, ecut_ry)
+    idx = box_map(miller, dims)
+    n_box = int(np.prod(dims))
+    x = np.atleast_2d(np.asarray(x, np.complex128))
+    beta = kb_beta(a, tau, k_frac, miller, kb_atom, kb_width)
+    y = np.empty_like(x)
+    for v in range(x.shape[0]):
+        box = np.zeros(n_box, dtype=np.complex128)
+        box[idx] = x[v]
+        psi_r = np.fft.ifftn(box.reshape(dims)) * n_box          # sum_G c_G exp(+iG.r)
+        w = np.fft.fftn(psi_r * vloc_r).ravel() / n_box           # back to coefficients
+        y[v] = w[idx] + kin * x[v] + (np.asarray(kb_d)[:, None] * beta * (beta.conj() @ x[v])[:, None]).sum(0)
+    return y
+
+
+# -------------------------------------------------------------- Eq. 7-8 projector, RHS
+
+def project_c(psi_v, x):
+    """P_c x = x - sum_v psi_v <psi_v|x> for rows x ([nvec][npw]); psi_v [n_occ][npw]."""
+    psi = np.asarray(psi_v, np.complex128)
+    x = np.atleast_2d(np.asarray(x, np.complex128))
+    return x - (x @ psi.conj().T) @ psi
+
+
+def make_rhs(miller_kq, miller_k, psi_k, gp_miller):
+    """dV psi_v expressed in the k+q basis for dV = exp(i(q+G_p).r) (Eq. 8 driving field):
+    rhs[v*n_pert + p][G'] = psi_{v,k}(G' - G_p) when G' - G_p is in the k sphere, else 0."""
+    lookup = {tuple(int(c) for c in m): i for i, m in enumerate(miller_k)}
+    n_v, n_p = len(psi_k), len(gp_miller)
+    out = np.zeros((n_v * n_p, len(miller_kq)), dtype=np.complex128)
+    for p, gp in enumerate(gp_miller):
+        for j, m in enumerate(miller_kq):
+            src = lookup.get((int(m[0] - gp[0]), int(m[1] - gp[1]), int(m[2] - gp[2])))
+            if src is not None:
+                for v in range(n_v):
+                    out[v * n_p + p, j] = psi_k[v][src]
+    return out
+
+
+# ------------------------------------------------------------------ Eq. 6-7 the solve
+
+def shifted_operator(h, psi_v, z):
+    """P_c H P_c - z on the full basis (on range(P_v) it acts as -z; z has Im z = eta > 0)."""
+    n = h.shape[0]
+    pc = np.eye(n, dtype=np.complex128) - np.asarray(psi_v).T @ np.asarray(psi_v).conj()
+    return pc @ h @ pc - z * np.eye(n)
+
+
+def solve_shifted(h, psi_v, rhs, e_ref, omega, eta):
+    """dpsi[r][j] solving (P_c H P_c - z_rj) dpsi = -P_c rhs_r, z_rj = e_ref[r] + omega_j + i eta,
+    by one dense LU per distinct shift (Eq. 6 with the operator of Eq. 7)."""
+    rhs = np.atleast_2d(np.asarray(rhs, np.complex128))
+    b = -project_c(psi_v, rhs)
+    n = h.shape[0]
+    pc = np.eye(n, dtype=np.complex128) - np.asarray(psi_v).T @ np.asarray(psi_v).conj()
+    pcp = pc @ h @ pc
+    e_ref = np.asarray(e_ref, np.float64)
+    out = np.zeros((len(rhs), len(omega), n), dtype=np.complex128)
+    for e in np.unique(e_ref):
+        rows = np.nonzero(e_ref == e)[0]
+        for j, w in enumerate(omega):
+            z = e + w + 1j * eta
+            lu = scipy.linalg.lu_factor(pcp - z * np.eye(n), check_finite=False)
+            out[rows, j, :] = scipy.linalg.lu_solve(lu, b[rows].T, check_finite=False).T
+    return out
+
+
+def sum_over_states(h, n_occ, rhs, e_ref, omega, eta):
+    """Sum over all unoccupied eigenstates of the finite basis:
+    dpsi = sum_c psi_c <psi_c|dV psi_v> / (eps_v + omega - eps_c + i eta), with the occupied
+    subspace spanned by the n_occ lowest eigenvectors of h."""
+    w, v = np.linalg.eigh(h)
+    vc = v[:, n_occ:]
+    wc = w[n_occ:]
+    rhs = np.atleast_2d(np.asarray(rhs, np.complex128))
+    coef = rhs @ vc.conj()                       # <psi_c|rhs_r>
+    out = np.zeros((len(rhs), len(omega), h.shape[0]), dtype=np.complex128)
+    for r in range(len(rhs)):
+        for j, om in enumerate(omega):
+            out[r, j] = (coef[r] / (e_ref[r] + om - wc + 1j * eta)) @ vc.T
+    return out, w
+
+
+def residual(h, psi_v, rhs, e_ref, omega, eta, dpsi):
+    """True residual of each pair: rel_res = |b - A x| / |b| and the certificate |r| / (eta |x|).
+    A = P_c H P_c - z is normal with dist(z, spec(A + z)) >= eta, so |x - x*| / |x| <= cert."""
+    rhs = np.atleast_2d(np.asarray(rhs, np.complex128))
+    b = -project_c(psi_v, rhs)
+    nr, nw = dpsi.shape[0], dpsi.shape[1]
+    rel = np.zeros((nr, nw))
+    cert = np.zeros((nr, nw))
+    for r in range(nr):
+        bn = np.linalg.norm(b[r])
+        for j in range(nw):
+            a = shifted_operator(h, psi_v, e_ref[r] + omega[j] + 1j * eta)
+            res = b[r] - a @ dpsi[r, j]
+            rn = np.linalg.norm(res)
+            xn = np.linalg.norm(dpsi[r, j])
+            rel[r, j] = rn / bn if bn > 0 else 0.0
+            cert[r, j] = rn / (eta * xn) if xn > 0 else 0.0
+    return rel, cert
