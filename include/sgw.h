@@ -120,32 +120,41 @@ sgw_status sgw_apply_shifted(sgw_system* sys, int nvec, const void* x, const dou
                              void* stream);
 
 typedef struct {
-    int ell;          /* degree of the minimal-residual polynomial of BiCGstab(ell): 1, 2 or 4 (0 -> 4) */
+    int ell;          /* degree of the minimal-residual polynomial of BiCGstab(ell): 1..4 (0 -> 4) */
     int seed_index;   /* shift that carries the Krylov space; -1 -> the largest omega */
-    int max_matvec;   /* matrix-vector budget per right-hand side (0 -> 40000) */
+    int max_matvec;   /* matrix-vector budget per right-hand side and per correction solve (0 -> 40000) */
+    int max_refine;   /* rounds of per-shift correction solves (0 -> 3, negative -> none) */
     void* stream;     /* cudaStream_t, NULL = default stream */
 } sgw_solve_opts;
 
 /* Per-pair outputs, each [nrhs][nomega] host arrays (any may be NULL). */
 typedef struct {
-    int* matvecs;       /* H applications spent when the pair converged (or the budget) */
-    double* est_res;    /* recursive residual estimate |r| / |b| at exit */
-    int* status;        /* SGW_PAIR_* */
+    int* matvecs;       /* H applications spent on the pair: the seed's count when the pair left the
+                           multishift pass, plus its correction solves */
+    double* est_res;    /* recursive residual estimate |r| / |b| when the multishift pass stopped */
+    double* rel_res;    /* true FP64 residual |b - A x| / |b| of the returned solution */
+    double* cert;       /* error certificate |b - A x| / (eta |x|) >= |x - x*| / |x| */
+    int* status;        /* SGW_PAIR_*: CONVERGED iff rel_res <= tol */
+    int* launches;      /* one int: library kernels launched by this call */
 } sgw_report;
 
 /* Multishift solve (the hot path).  For every r < nrhs and j < nomega solves
- *   (P_c H P_c - z_rj) dpsi[r][j] = -P_c rhs[r],   z_rj = e_ref[r] + omega[j] + i eta
- * with a shifted BiCGstab(ell) (Frommer 2003, the solver the paper cites in Sec. 2.2):
- * one seed system per right-hand side builds the Krylov space, every shift is advanced
- * from the seed's vectors through scalar recurrences, and a shift stops updating once its
- * residual estimate drops to tol |b|.
+ *   (P_c H P_c - z_rj) dpsi[r][j] = -P_c rhs[r],   z_rj = e_ref[r] + omega[j] + i eta.
+ * 1. Multishift pass: a shifted BiCGstab(ell) (Frommer 2003, the solver the paper cites in
+ *    Sec. 2.2): one seed system per right-hand side builds the Krylov space, every shift
+ *    is advanced from the seed's vectors through scalar recurrences, and a shift stops
+ *    updating once its residual estimate drops to tol |b|.
+ * 2. True FP64 residual and certificate of every pair (as sgw_residual).
+ * 3. Pairs whose true residual exceeds tol (recursive/true residual gap, budget exhausted)
+ *    get per-shift correction solves A_j d = r_j, x_j += d, then step 2 again; up to
+ *    max_refine rounds.
  *   rhs    complex [nrhs][n_pw] (host or device): dV psi_v in this basis.
  *   e_ref  [nrhs] host, Ha.   omega [nomega] host, Ha.   eta > 0 (Ha), else SGW_EINVAL.
  *   tol    relative residual target (e.g. 1e-10).
  *   dpsi   complex [nrhs][nomega][n_pw] (host or device), overwritten.
  *   report optional per-pair report.
  * A zero right-hand side gives dpsi = 0 with status CONVERGED.  Returns SGW_ENOCONV if any
- * pair missed tol (results and report are still written). */
+ * pair's true residual stays above tol (results and report are still written). */
 sgw_status sgw_solve_shifted(sgw_system* sys, int nrhs, const void* rhs, const double* e_ref,
                              int nomega, const double* omega, double eta, double tol,
                              const sgw_solve_opts* opts, void* dpsi, sgw_report* report);

@@ -1,0 +1,869 @@
+// C ABI of the shifted-Sternheimer library (declared in include/sgw.h).
+//
+// Host responsibilities: argument validation, the reciprocal lattice, the alias check of
+// the FFT box, the stick tables, staging of host buffers, workspace management and the
+// per-pair report.  Every arithmetic step of the path runs in the kernels of setup.cu
+// and kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "setup.h"
+#include "sgw.h"
+#include "sgw_internal.cuh"
+
+namespace sgw {
+const void* solve_kernel_ptr();
+const void* apply_kernel_ptr();
+const void* residual_kernel_ptr();
+}  // namespace sgw
+
+using namespace sgw;
+
+struct sgw_system {
+    int dev = 0;
+    double a[3][3];
+    double b[3][3];
+    double vol = 0.0;
+    double k[3];
+    double ecut = 0.0;
+    int dims[3];
+    int npw = 0, nstick = 0, nxcol = 0, nproj = 0, nocc = 0;
+    std::vector<int> miller;     // [npw][3]
+    std::vector<double> kin;     // [npw]
+    std::vector<int> map;        // [npw]
+    std::vector<double> eps;
+    int lo[3], ext[3];           // Miller bounding box of the sphere (for Eq. 8 lookups)
+    // device
+    int* d_miller = nullptr;
+    double* d_kin = nullptr;
+    int* d_g2s = nullptr;
+    int* d_stick_xy = nullptr;
+    int* d_xbase = nullptr;
+    double* d_vloc = nullptr;
+    double2* d_twid = nullptr;
+    double2* d_beta = nullptr;
+    double* d_dkb = nullptr;
+    double2* d_psi = nullptr;
+    int* d_lut = nullptr;
+    void* d_ws = nullptr;        // solver workspace, grown on demand
+    size_t ws_bytes = 0;
+    Plan plan;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+sgw_status fail(sgw_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+sgw_status cuda_fail(cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    g_err = m;
+    return e == cudaErrorMemoryAllocation ? SGW_ENOMEM : SGW_ECUDA;
+}
+
+#define SGW_CUDA(call, what)                              \
+    do {                                                  \
+        cudaError_t e__ = (call);                         \
+        if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// A vector argument that may live on the host or the device.  Host data is copied to a
+// temporary device buffer (in) and/or back (out).
+struct Staged {
+    void* dev = nullptr;
+    const void* host_src = nullptr;
+    void* host_dst = nullptr;
+    size_t bytes = 0;
+    bool owned = false;
+    ~Staged() {
+        if (owned && dev) cudaFree(dev);
+    }
+};
+
+sgw_status stage_in(const void* p, size_t bytes, Staged& s, cudaStream_t st, const char* name) {
+    s.bytes = bytes;
+    if (is_device_ptr(p)) {
+        s.dev = const_cast<void*>(p);
+        return SGW_OK;
+    }
+    if (bytes == 0) return SGW_OK;
+    SGW_CUDA(cudaMalloc(&s.dev, bytes), name);
+    s.owned = true;
+    s.host_src = p;
+    SGW_CUDA(cudaMemcpyAsync(s.dev, p, bytes, cudaMemcpyHostToDevice, st), name);
+    return SGW_OK;
+}
+
+sgw_status stage_out(void* p, size_t bytes, Staged& s, const char* name) {
+    s.bytes = bytes;
+    if (is_device_ptr(p)) {
+        s.dev = p;
+        return SGW_OK;
+    }
+    if (bytes == 0) return SGW_OK;
+    SGW_CUDA(cudaMalloc(&s.dev, bytes), name);
+    s.owned = true;
+    s.host_dst = p;
+    return SGW_OK;
+}
+
+sgw_status finish_out(Staged& s, cudaStream_t st, const char* name) {
+    if (s.owned && s.host_dst && s.bytes) {
+        SGW_CUDA(cudaMemcpyAsync(s.host_dst, s.dev, s.bytes, cudaMemcpyDeviceToHost, st), name);
+    }
+    return SGW_OK;
+}
+
+template <typename T>
+sgw_status upload(T** dst, const T* src, size_t n, const char* name) {
+    if (n == 0) return SGW_OK;
+    SGW_CUDA(cudaMalloc((void**)dst, n * sizeof(T)), name);
+    SGW_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice), name);
+    return SGW_OK;
+}
+
+bool factor_235(int n, AxisPlan& ax) {
+    ax.n = n;
+    ax.nst = 0;
+    if (n < 1) return false;
+    int m = n;
+    const int rads[4] = {4, 2, 3, 5};
+    for (int r : rads) {
+        while (m % r == 0) {
+            if (ax.nst >= kMaxStages) return false;
+            ax.rad[ax.nst++] = r;
+            m /= r;
+        }
+    }
+    return m == 1;
+}
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+void free_system(sgw_system* s) {
+    if (!s) return;
+    cudaFree(s->d_miller);
+    cudaFree(s->d_kin);
+    cudaFree(s->d_g2s);
+    cudaFree(s->d_stick_xy);
+    cudaFree(s->d_xbase);
+    cudaFree(s->d_vloc);
+    cudaFree(s->d_twid);
+    cudaFree(s->d_beta);
+    cudaFree(s->d_dkb);
+    cudaFree(s->d_psi);
+    cudaFree(s->d_lut);
+    cudaFree(s->d_ws);
+    delete s;
+}
+
+sgw_status ensure_ws(sgw_system* s, size_t bytes) {
+    if (bytes <= s->ws_bytes) return SGW_OK;
+    if (s->d_ws) cudaFree(s->d_ws);
+    s->d_ws = nullptr;
+    s->ws_bytes = 0;
+    SGW_CUDA(cudaMalloc(&s->d_ws, bytes), "workspace allocation");
+    s->ws_bytes = bytes;
+    return SGW_OK;
+}
+
+int max_optin_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sgw_last_error(void) { return g_err.c_str(); }
+
+sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double k_frac[3], const int fft_dims[3],
+                             const double* vloc_r, const sgw_kb* kb, sgw_system** out) {
+    g_err.clear();
+    if (!out) return fail(SGW_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cell || !k_frac || !fft_dims || !vloc_r) return fail(SGW_EINVAL, "NULL argument");
+    if (!(ecut_ry > 0.0) || !std::isfinite(ecut_ry)) return fail(SGW_EINVAL, "ecut_ry must be positive and finite");
+    if (!finite_all(&cell->a[0][0], 9) || !finite_all(k_frac, 3)) return fail(SGW_EINVAL, "non-finite cell or k");
+    if (cell->n_atoms < 0 || (cell->n_atoms > 0 && !cell->tau)) return fail(SGW_EINVAL, "bad atom list");
+    if (cell->n_atoms > 0 && !finite_all(cell->tau, 3 * (size_t)cell->n_atoms)) return fail(SGW_EINVAL, "non-finite tau");
+    const int nproj = kb ? kb->n_proj : 0;
+    if (nproj < 0 || nproj > kMaxProj) return fail(SGW_EUNSUPPORTED, "n_proj must be in [0, 64]");
+    if (nproj > 0 && (!kb->atom || !kb->width || !kb->D)) return fail(SGW_EINVAL, "NULL projector arrays");
+    for (int p = 0; p < nproj; ++p) {
+        if (kb->atom[p] < 0 || kb->atom[p] >= cell->n_atoms) return fail(SGW_EINVAL, "projector atom index out of range");
+        if (!(kb->width[p] > 0.0) || !std::isfinite(kb->width[p]) || !std::isfinite(kb->D[p]))
+            return fail(SGW_EINVAL, "projector width must be positive, D finite");
+    }
+    int dev = 0;
+    {
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess || ndev == 0) return cuda_fail(e == cudaSuccess ? cudaErrorNoDevice : e, "no CUDA device");
+        SGW_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    }
+    sgw_system* s = new sgw_system();
+    s->dev = dev;
+    std::memcpy(s->a, cell->a, sizeof(s->a));
+    const double* a0 = cell->a[0];
+    const double* a1 = cell->a[1];
+    const double* a2 = cell->a[2];
+    double cr[3][3] = {{a1[1] * a2[2] - a1[2] * a2[1], a1[2] * a2[0] - a1[0] * a2[2], a1[0] * a2[1] - a1[1] * a2[0]},
+                       {a2[1] * a0[2] - a2[2] * a0[1], a2[2] * a0[0] - a2[0] * a0[2], a2[0] * a0[1] - a2[1] * a0[0]},
+                       {a0[1] * a1[2] - a0[2] * a1[1], a0[2] * a1[0] - a0[0] * a1[2], a0[0] * a1[1] - a0[1] * a1[0]}};
+    const double det = a0[0] * cr[0][0] + a0[1] * cr[0][1] + a0[2] * cr[0][2];
+    if (!(std::fabs(det) > 1e-12)) {
+        free_system(s);
+        return fail(SGW_EINVAL, "degenerate lattice");
+    }
+    s->vol = std::fabs(det);
+    const double twopi = 6.283185307179586476925286766559;
+    for (int i = 0; i < 3; ++i)
+        for (int x = 0; x < 3; ++x) s->b[i][x] = cr[i][x] * (twopi / det);
+    std::memcpy(s->k, k_frac, sizeof(s->k));
+    s->ecut = ecut_ry;
+    for (int i = 0; i < 3; ++i) s->dims[i] = fft_dims[i];
+    for (int i = 0; i < 3; ++i) {
+        if (!factor_235(fft_dims[i], s->plan.ax[i])) {
+            free_system(s);
+            return fail(SGW_EINVAL, "FFT dims must be positive products of 2, 3 and 5");
+        }
+    }
+    const size_t nbox = (size_t)fft_dims[0] * fft_dims[1] * fft_dims[2];
+    if (!finite_all(vloc_r, nbox)) {
+        free_system(s);
+        return fail(SGW_EINVAL, "non-finite V_loc");
+    }
+    double len[3];
+    for (int i = 0; i < 3; ++i)
+        len[i] = std::sqrt(cell->a[i][0] * cell->a[i][0] + cell->a[i][1] * cell->a[i][1] + cell->a[i][2] * cell->a[i][2]);
+    // alias check: the box must hold every |G|^2 <= 4 ecut (potential band) without folding.
+    {
+        int mr[3] = {0, 0, 0};
+        int bnd[3];
+        for (int i = 0; i < 3; ++i) bnd[i] = (int)std::ceil(2.0 * std::sqrt(ecut_ry) * len[i] / twopi) + 1;
+        for (int m1 = -bnd[0]; m1 <= bnd[0]; ++m1)
+            for (int m2 = -bnd[1]; m2 <= bnd[1]; ++m2)
+                for (int m3 = -bnd[2]; m3 <= bnd[2]; ++m3) {
+                    double g2 = 0.0;
+                    for (int x = 0; x < 3; ++x) {
+                        const double gx = m1 * s->b[0][x] + m2 * s->b[1][x] + m3 * s->b[2][x];
+                        g2 += gx * gx;
+                    }
+                    if (g2 <= 4.0 * ecut_ry) {
+                        mr[0] = std::max(mr[0], std::abs(m1));
+                        mr[1] = std::max(mr[1], std::abs(m2));
+                        mr[2] = std::max(mr[2], std::abs(m3));
+                    }
+                }
+        for (int i = 0; i < 3; ++i)
+            if (fft_dims[i] < 2 * mr[i] + 1) {
+                free_system(s);
+                char buf[160];
+                std::snprintf(buf, sizeof buf, "FFT box axis %d: %d < 2*%d+1 (potential band |G|^2 <= 4 E_cut would alias)",
+                              i, fft_dims[i], mr[i]);
+                return fail(SGW_EALIAS, buf);
+            }
+    }
+    // ---- G-sphere on the device
+    SphereArgs sa;
+    std::memcpy(sa.b, s->b, sizeof(sa.b));
+    std::memcpy(sa.k, k_frac, sizeof(sa.k));
+    sa.ecut = ecut_ry;
+    long long cand = 1;
+    for (int i = 0; i < 3; ++i) {
+        sa.M[i] = (int)std::ceil(std::sqrt(ecut_ry) * len[i] / twopi + std::fabs(k_frac[i])) + 1;
+        cand *= 2 * sa.M[i] + 1;
+    }
+    if (cand > 50000000LL) {
+        free_system(s);
+        return fail(SGW_EUNSUPPORTED, "Miller box too large");
+    }
+    sa.cap = (int)cand;
+    int *d_mil = nullptr, *d_cnt = nullptr;
+    double* d_kin = nullptr;
+    auto cleanup_tmp = [&]() {
+        cudaFree(d_mil);
+        cudaFree(d_cnt);
+        cudaFree(d_kin);
+    };
+    cudaError_t e = cudaMalloc(&d_mil, sizeof(int) * 3 * cand);
+    if (e == cudaSuccess) e = cudaMalloc(&d_kin, sizeof(double) * cand);
+    if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int));
+    if (e == cudaSuccess) e = launch_sphere(sa, d_mil, d_kin, d_cnt, 0);
+    int npw = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&npw, d_cnt, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cleanup_tmp();
+        free_system(s);
+        return cuda_fail(e, "G-sphere kernel");
+    }
+    if (npw < 1) {
+        cleanup_tmp();
+        free_system(s);
+        return fail(SGW_EINVAL, "empty plane-wave sphere");
+    }
+    s->npw = npw;
+    s->miller.resize(3 * (size_t)npw);
+    s->kin.resize(npw);
+    e = cudaMemcpy(s->miller.data(), d_mil, sizeof(int) * 3 * npw, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(s->kin.data(), d_kin, sizeof(double) * npw, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_miller, sizeof(int) * 3 * npw);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_miller, d_mil, sizeof(int) * 3 * npw, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_kin, sizeof(double) * npw);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_kin, d_kin, sizeof(double) * npw, cudaMemcpyDeviceToDevice);
+    cleanup_tmp();
+    if (e != cudaSuccess) {
+        free_system(s);
+        return cuda_fail(e, "G-sphere copy");
+    }
+    // ---- box map (device) and stick tables (host, integer bookkeeping)
+    {
+        int* d_map = nullptr;
+        e = cudaMalloc(&d_map, sizeof(int) * npw);
+        if (e == cudaSuccess) e = launch_boxmap(s->d_miller, npw, fft_dims, d_map, 0);
+        s->map.resize(npw);
+        if (e == cudaSuccess) e = cudaMemcpy(s->map.data(), d_map, sizeof(int) * npw, cudaMemcpyDeviceToHost);
+        cudaFree(d_map);
+        if (e != cudaSuccess) {
+            free_system(s);
+            return cuda_fail(e, "box map kernel");
+        }
+    }
+    const int n1 = fft_dims[0], n2 = fft_dims[1], n3 = fft_dims[2];
+    std::map<int, int> stick_of;   // xy -> stick id (sorted by xy)
+    std::vector<int> xs_used(n1, 0);
+    for (int g = 0; g < npw; ++g) {
+        const int xy = s->map[g] / n3;
+        stick_of.emplace(xy, 0);
+        xs_used[xy / n2] = 1;
+    }
+    std::vector<int> stick_xy;
+    for (auto& kv : stick_of) {
+        kv.second = (int)stick_xy.size();
+        stick_xy.push_back(kv.first);
+    }
+    std::vector<int> g2s(npw);
+    for (int g = 0; g < npw; ++g) g2s[g] = stick_of[s->map[g] / n3] * n3 + s->map[g] % n3;
+    std::vector<int> xbase;
+    for (int x = 0; x < n1; ++x)
+        if (xs_used[x]) xbase.push_back(x * n2);
+    s->nstick = (int)stick_xy.size();
+    s->nxcol = (int)xbase.size();
+    // potential, one contiguous plane per z: [z][x][y]
+    std::vector<double> vz(nbox);
+    for (int x = 0; x < n1; ++x)
+        for (int y = 0; y < n2; ++y)
+            for (int z = 0; z < n3; ++z) vz[((size_t)z * n1 + x) * n2 + y] = vloc_r[((size_t)x * n2 + y) * n3 + z];
+    sgw_status rs;
+    if ((rs = upload(&s->d_g2s, g2s.data(), g2s.size(), "upload g2s")) != SGW_OK ||
+        (rs = upload(&s->d_stick_xy, stick_xy.data(), stick_xy.size(), "upload sticks")) != SGW_OK ||
+        (rs = upload(&s->d_xbase, xbase.data(), xbase.size(), "upload xbase")) != SGW_OK ||
+        (rs = upload(&s->d_vloc, vz.data(), vz.size(), "upload V_loc")) != SGW_OK) {
+        free_system(s);
+        return rs;
+    }
+    e = cudaMalloc(&s->d_twid, sizeof(double2) * (n1 + n2 + n3));
+    if (e == cudaSuccess) e = launch_twiddles(fft_dims, s->d_twid, 0);
+    if (e != cudaSuccess) {
+        free_system(s);
+        return cuda_fail(e, "twiddles");
+    }
+    // ---- KB projectors
+    s->nproj = nproj;
+    if (nproj > 0) {
+        BetaArgs ba;
+        std::memcpy(ba.b, s->b, sizeof(ba.b));
+        std::memcpy(ba.k, k_frac, sizeof(ba.k));
+        ba.inv_sqrt_vol = 1.0 / std::sqrt(s->vol);
+        std::vector<double> d(nproj);
+        for (int p = 0; p < nproj; ++p) {
+            ba.width[p] = kb->width[p];
+            for (int x = 0; x < 3; ++x) ba.tau[p][x] = cell->tau[3 * kb->atom[p] + x];
+            d[p] = kb->D[p];
+        }
+        e = cudaMalloc(&s->d_beta, sizeof(double2) * (size_t)nproj * npw);
+        if (e == cudaSuccess) e = launch_beta(ba, nproj, s->d_miller, npw, s->d_beta, 0);
+        if (e != cudaSuccess) {
+            free_system(s);
+            return cuda_fail(e, "projector kernel");
+        }
+        if ((rs = upload(&s->d_dkb, d.data(), d.size(), "upload D")) != SGW_OK) {
+            free_system(s);
+            return rs;
+        }
+    }
+    // ---- Miller lookup table for Eq. 8 gathers into this basis's coefficients
+    {
+        int hi[3];
+        for (int x = 0; x < 3; ++x) {
+            s->lo[x] = 1 << 30;
+            hi[x] = -(1 << 30);
+        }
+        for (int g = 0; g < npw; ++g)
+            for (int x = 0; x < 3; ++x) {
+                s->lo[x] = std::min(s->lo[x], s->miller[3 * g + x]);
+                hi[x] = std::max(hi[x], s->miller[3 * g + x]);
+            }
+        for (int x = 0; x < 3; ++x) s->ext[x] = hi[x] - s->lo[x] + 1;
+        std::vector<int> lut((size_t)s->ext[0] * s->ext[1] * s->ext[2], -1);
+        for (int g = 0; g < npw; ++g) {
+            const int i0 = s->miller[3 * g] - s->lo[0], i1 = s->miller[3 * g + 1] - s->lo[1],
+                      i2 = s->miller[3 * g + 2] - s->lo[2];
+            lut[((size_t)i0 * s->ext[1] + i1) * s->ext[2] + i2] = g;
+        }
+        if ((rs = upload(&s->d_lut, lut.data(), lut.size(), "upload lookup")) != SGW_OK) {
+            free_system(s);
+            return rs;
+        }
+    }
+    // ---- plan
+    Plan& P = s->plan;
+    P.n1 = n1;
+    P.n2 = n2;
+    P.n3 = n3;
+    P.npw = npw;
+    P.nstick = s->nstick;
+    P.nxcol = s->nxcol;
+    P.g2s = s->d_g2s;
+    P.stick_xy = s->d_stick_xy;
+    P.xbase = s->d_xbase;
+    P.vloc = s->d_vloc;
+    P.kin = s->d_kin;
+    P.twid = s->d_twid;
+    P.nproj = nproj;
+    P.beta = s->d_beta;
+    P.dkb = s->d_dkb;
+    P.nocc = 0;
+    P.psi = nullptr;
+    P.inv_nbox = 1.0 / (double)nbox;
+    if (apply_smem_bytes(P) > max_optin_smem()) {
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "the pruned FFT box (%d sticks x %d) needs %d B of shared memory per CTA, more than the %d B "
+                      "this build keeps on chip",
+                      s->nstick, n3, apply_smem_bytes(P), max_optin_smem());
+        free_system(s);
+        return fail(SGW_EUNSUPPORTED, buf);
+    }
+    SGW_CUDA(cudaDeviceSynchronize(), "create_system");
+    *out = s;
+    return SGW_OK;
+}
+
+sgw_status sgw_get_gvectors(const sgw_system* s, int* n_pw, int* miller, double* kin) {
+    if (!s) return fail(SGW_EINVAL, "NULL system");
+    if (n_pw) *n_pw = s->npw;
+    if (miller) std::memcpy(miller, s->miller.data(), sizeof(int) * 3 * s->npw);
+    if (kin) std::memcpy(kin, s->kin.data(), sizeof(double) * s->npw);
+    return SGW_OK;
+}
+
+sgw_status sgw_get_box_map(const sgw_system* s, int* map) {
+    if (!s || !map) return fail(SGW_EINVAL, "NULL argument");
+    std::memcpy(map, s->map.data(), sizeof(int) * s->npw);
+    return SGW_OK;
+}
+
+sgw_status sgw_set_occupied(sgw_system* s, int n_occ, const void* psi_v, const double* eps_v) {
+    g_err.clear();
+    if (!s) return fail(SGW_EINVAL, "NULL system");
+    if (n_occ < 0 || n_occ > 4096) return fail(SGW_EINVAL, "n_occ out of range");
+    if (n_occ > 0 && (!psi_v || !eps_v)) return fail(SGW_EINVAL, "NULL psi_v or eps_v");
+    if (n_occ > 0 && !finite_all(eps_v, n_occ)) return fail(SGW_EINVAL, "non-finite eps_v");
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    const size_t bytes = sizeof(double2) * (size_t)n_occ * s->npw;
+    double2* d_new = nullptr;
+    if (n_occ > 0) {
+        SGW_CUDA(cudaMalloc(&d_new, bytes), "psi_v allocation");
+        cudaError_t e = cudaMemcpy(d_new, psi_v, bytes, cudaMemcpyDefault);
+        if (e != cudaSuccess) {
+            cudaFree(d_new);
+            return cuda_fail(e, "psi_v copy");
+        }
+        // orthonormality: max |psi^H psi - I| <= 1e-10 (also catches NaN/Inf)
+        double2* d_S = nullptr;
+        std::vector<double2> S((size_t)n_occ * n_occ);
+        e = cudaMalloc(&d_S, sizeof(double2) * S.size());
+        if (e == cudaSuccess) e = launch_gram(d_new, n_occ, s->npw, d_S, 0);
+        if (e == cudaSuccess) e = cudaMemcpy(S.data(), d_S, sizeof(double2) * S.size(), cudaMemcpyDeviceToHost);
+        cudaFree(d_S);
+        if (e != cudaSuccess) {
+            cudaFree(d_new);
+            return cuda_fail(e, "overlap kernel");
+        }
+        double worst = 0.0;
+        for (int v = 0; v < n_occ; ++v)
+            for (int w = 0; w < n_occ; ++w) {
+                const double2 q = S[(size_t)v * n_occ + w];
+                const double dr = q.x - (v == w ? 1.0 : 0.0);
+                const double d = std::sqrt(dr * dr + q.y * q.y);
+                if (!(d <= worst)) worst = d;   // NaN-propagating max
+            }
+        if (!(worst <= 1e-10)) {
+            cudaFree(d_new);
+            char buf[120];
+            std::snprintf(buf, sizeof buf, "psi_v not orthonormal: max |psi^H psi - I| = %.3e > 1e-10", worst);
+            return fail(SGW_EINVAL, buf);
+        }
+    }
+    cudaFree(s->d_psi);
+    s->d_psi = d_new;
+    s->nocc = n_occ;
+    s->eps.assign(eps_v, eps_v + n_occ);
+    s->plan.nocc = n_occ;
+    s->plan.psi = d_new;
+    if (apply_smem_bytes(s->plan) > max_optin_smem()) return fail(SGW_EUNSUPPORTED, "too many occupied states");
+    return SGW_OK;
+}
+
+sgw_status sgw_make_rhs(const sgw_system* kq, const sgw_system* k, int n_v, const void* psi_k, int n_pert,
+                        const int* gp_miller, void* rhs, void* stream) {
+    g_err.clear();
+    if (!kq || !k || !rhs || (n_v > 0 && !psi_k) || (n_pert > 0 && !gp_miller))
+        return fail(SGW_EINVAL, "NULL argument");
+    if (n_v < 0 || n_pert < 0) return fail(SGW_EINVAL, "negative size");
+    if (n_v == 0 || n_pert == 0) return SGW_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    Staged in, out;
+    sgw_status r;
+    if ((r = stage_in(psi_k, sizeof(double2) * (size_t)n_v * k->npw, in, st, "psi_k")) != SGW_OK) return r;
+    if ((r = stage_out(rhs, sizeof(double2) * (size_t)n_v * n_pert * kq->npw, out, "rhs")) != SGW_OK) return r;
+    int* d_gp = nullptr;
+    SGW_CUDA(cudaMalloc(&d_gp, sizeof(int) * 3 * n_pert), "gp allocation");
+    cudaError_t e = cudaMemcpyAsync(d_gp, gp_miller, sizeof(int) * 3 * n_pert, cudaMemcpyHostToDevice, st);
+    RhsArgs ra;
+    for (int x = 0; x < 3; ++x) {
+        ra.lo[x] = k->lo[x];
+        ra.ext[x] = k->ext[x];
+    }
+    if (e == cudaSuccess)
+        e = launch_rhs(ra, kq->d_miller, kq->npw, k->d_lut, (const double2*)in.dev, k->npw, d_gp, n_v, n_pert,
+                       (double2*)out.dev, st);
+    if (e == cudaSuccess && (r = finish_out(out, st, "rhs copy")) != SGW_OK) {
+        cudaFree(d_gp);
+        return r;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_gp);
+    if (e != cudaSuccess) return cuda_fail(e, "rhs kernel");
+    return SGW_OK;
+}
+
+static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const double* z, void* y, void* stream,
+                               int project) {
+    g_err.clear();
+    if (!s || !x || !y) return fail(SGW_EINVAL, "NULL argument");
+    if (nvec < 0) return fail(SGW_EINVAL, "negative nvec");
+    if (nvec == 0) return SGW_OK;
+    if (project && s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+    if (project && (!z || !finite_all(z, 2 * (size_t)nvec))) return fail(SGW_EINVAL, "bad shifts");
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vb = sizeof(double2) * (size_t)nvec * s->npw;
+    Staged in, out;
+    sgw_status r;
+    if ((r = stage_in(x, vb, in, st, "x")) != SGW_OK) return r;
+    if ((r = stage_out(y, vb, out, "y")) != SGW_OK) return r;
+    int grid = 0;
+    SGW_CUDA(resident_grid(apply_kernel_ptr(), apply_smem_bytes(s->plan), &grid), "apply occupancy");
+    grid = std::min(grid, nvec);
+    const size_t scratch = sizeof(double2) * (size_t)grid * s->npw;
+    const size_t zb = project ? sizeof(double2) * nvec : 0;
+    if ((r = ensure_ws(s, scratch + zb + 256)) != SGW_OK) return r;
+    double2* d_scr = (double2*)s->d_ws;
+    double2* d_z = (double2*)((char*)s->d_ws + ((scratch + 255) / 256) * 256);
+    if (project) SGW_CUDA(cudaMemcpyAsync(d_z, z, zb, cudaMemcpyHostToDevice, st), "z copy");
+    SGW_CUDA(launch_apply(s->plan, nvec, (const double2*)in.dev, (double2*)out.dev, d_z, project, d_scr, grid, st),
+             "apply kernel");
+    if ((r = finish_out(out, st, "y copy")) != SGW_OK) return r;
+    SGW_CUDA(cudaStreamSynchronize(st), "apply");
+    return SGW_OK;
+}
+
+sgw_status sgw_apply_h(sgw_system* s, int nvec, const void* x, void* y, void* stream) {
+    return apply_common(s, nvec, x, nullptr, y, stream, 0);
+}
+
+sgw_status sgw_apply_shifted(sgw_system* s, int nvec, const void* x, const double* z, void* y, void* stream) {
+    return apply_common(s, nvec, x, z, y, stream, 1);
+}
+
+namespace {
+
+// Bump allocator over the system's workspace.
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t b) {
+        const size_t o = off;
+        off += (b + 255) / 256 * 256;
+        return o;
+    }
+};
+
+}  // namespace
+
+sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const double* e_ref, int nomega,
+                             const double* omega, double eta, double tol, const sgw_solve_opts* opts, void* dpsi,
+                             sgw_report* report) {
+    g_err.clear();
+    if (!s || !rhs || !e_ref || !omega || !dpsi) return fail(SGW_EINVAL, "NULL argument");
+    if (nrhs < 0 || nomega < 1) return fail(SGW_EINVAL, "need nrhs >= 0 and nomega >= 1");
+    if (nomega > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nomega above 512");
+    if (!(eta > 0.0) || !std::isfinite(eta))
+        return fail(SGW_EINVAL, "eta must be positive (the shifted systems are singular at eta = 0)");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
+    if (!finite_all(e_ref, nrhs) || !finite_all(omega, nomega)) return fail(SGW_EINVAL, "non-finite e_ref or omega");
+    if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+    const int ell = opts && opts->ell ? opts->ell : 4;
+    if (ell < 1 || ell > kMaxEll) return fail(SGW_EINVAL, "ell must be 1, 2, 3 or 4");
+    int seed = opts ? opts->seed_index : -1;
+    if (seed < 0) {
+        seed = 0;
+        for (int j = 1; j < nomega; ++j)
+            if (omega[j] > omega[seed]) seed = j;
+    }
+    if (seed >= nomega) return fail(SGW_EINVAL, "seed_index out of range");
+    const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : 40000;
+    const int max_refine = !opts || opts->max_refine == 0 ? 3 : std::max(0, opts->max_refine);
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+    if (nrhs == 0) return SGW_OK;
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    if (solve_smem_bytes(s->plan, nomega) > max_optin_smem())
+        return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
+    const size_t vb = sizeof(double2) * (size_t)s->npw;
+    const size_t np = (size_t)nrhs * nomega;
+    Staged in, out;
+    sgw_status r;
+    if ((r = stage_in(rhs, vb * nrhs, in, st, "rhs")) != SGW_OK) return r;
+    if ((r = stage_out(dpsi, vb * np, out, "dpsi")) != SGW_OK) return r;
+    int grid = 0, grid1 = 0, grid_r = 0;
+    SGW_CUDA(solve_grid(s->plan, nomega, nrhs, &grid), "solver occupancy");
+    const int chunk = (int)std::min<size_t>(np, 4096);
+    SGW_CUDA(solve_grid(s->plan, 1, chunk, &grid1), "solver occupancy");
+    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r), "residual occupancy");
+    grid_r = (int)std::min<size_t>(grid_r, np);
+    // workspace
+    Carve c;
+    const size_t o_seed = c.take(vb * (2 * ell + 3) * grid);
+    const size_t o_uw = c.take(vb * (size_t)nomega * grid);
+    const size_t o_eref = c.take(sizeof(double) * nrhs);
+    const size_t o_om = c.take(sizeof(double) * nomega);
+    const size_t o_sig = c.take(sizeof(double) * nomega);
+    const size_t o_cnt = c.take(sizeof(int));
+    const size_t o_mv = c.take(sizeof(int) * np);
+    const size_t o_est = c.take(sizeof(double) * np);
+    const size_t o_st = c.take(sizeof(int) * np);
+    const size_t o_rscr = c.take(2 * vb * grid_r);
+    const size_t o_rel = c.take(sizeof(double) * np);
+    const size_t o_cert = c.take(sizeof(double) * np);
+    const size_t o_list = c.take(sizeof(int) * chunk);
+    const size_t o_rvec = c.take(vb * chunk);
+    const size_t o_dbuf = c.take(vb * chunk);
+    const size_t o_eref1 = c.take(sizeof(double) * chunk);
+    const size_t o_seed1 = c.take(vb * (2 * ell + 3) * grid1);
+    const size_t o_uw1 = c.take(vb * grid1);
+    const size_t o_zero = c.take(sizeof(double));
+    const size_t o_mv1 = c.take(sizeof(int) * chunk);
+    const size_t o_est1 = c.take(sizeof(double) * chunk);
+    const size_t o_st1 = c.take(sizeof(int) * chunk);
+    if ((r = ensure_ws(s, c.off)) != SGW_OK) return r;
+    char* w = (char*)s->d_ws;
+    std::vector<double> sig(nomega);
+    for (int j = 0; j < nomega; ++j) sig[j] = omega[seed] - omega[j];
+    SGW_CUDA(cudaMemcpyAsync(w + o_eref, e_ref, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st), "e_ref copy");
+    SGW_CUDA(cudaMemcpyAsync(w + o_om, omega, sizeof(double) * nomega, cudaMemcpyHostToDevice, st), "omega copy");
+    SGW_CUDA(cudaMemcpyAsync(w + o_sig, sig.data(), sizeof(double) * nomega, cudaMemcpyHostToDevice, st), "sig copy");
+    SGW_CUDA(cudaMemsetAsync(w + o_zero, 0, sizeof(double), st), "memset");
+
+    // 1. multishift pass
+    SolveArgs A;
+    A.nrhs = nrhs;
+    A.nshift = nomega;
+    A.ell = ell;
+    A.max_mv = max_mv;
+    A.rhs = (const double2*)in.dev;
+    A.e_ref = (const double*)(w + o_eref);
+    A.sig = (const double*)(w + o_sig);
+    A.omega_seed = omega[seed];
+    A.eta = eta;
+    A.tol = tol;
+    A.x = (double2*)out.dev;
+    A.uw = (double2*)(w + o_uw);
+    A.seedw = (double2*)(w + o_seed);
+    A.counter = (int*)(w + o_cnt);
+    A.out_mv = (int*)(w + o_mv);
+    A.out_res = (double*)(w + o_est);
+    A.out_status = (int*)(w + o_st);
+    SGW_CUDA(launch_solve(s->plan, A, grid, st), "solver kernel");
+    int launches = 1;
+
+    // 2. true residual of every pair
+    double* d_rel = (double*)(w + o_rel);
+    double* d_cert = (double*)(w + o_cert);
+    SGW_CUDA(launch_residual(s->plan, nrhs, nomega, nullptr, 0, (const double2*)in.dev, A.e_ref,
+                             (const double*)(w + o_om), eta, A.x, (double2*)(w + o_rscr), d_rel, d_cert, nullptr,
+                             grid_r, st),
+             "residual kernel");
+    ++launches;
+    std::vector<int> stv(np), mvv(np);
+    std::vector<double> estv(np), relv(np), certv(np);
+    SGW_CUDA(cudaMemcpyAsync(stv.data(), A.out_status, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(mvv.data(), A.out_mv, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(estv.data(), A.out_res, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(relv.data(), d_rel, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaStreamSynchronize(st), "solve");
+
+    // 3. per-shift correction solves for pairs above tol
+    std::vector<int> list, mv1(chunk);
+    std::vector<double> eref1(chunk);
+    for (int round = 0; round < max_refine; ++round) {
+        list.clear();
+        for (size_t q = 0; q < np; ++q)
+            if (std::isfinite(relv[q]) && relv[q] > tol && stv[q] != SGW_PAIR_NONFINITE) list.push_back((int)q);
+        if (list.empty()) break;
+        for (size_t c0 = 0; c0 < list.size(); c0 += chunk) {
+            const int nc = (int)std::min<size_t>(chunk, list.size() - c0);
+            double worst = 0.0;
+            for (int i = 0; i < nc; ++i) {
+                const int q = list[c0 + i];
+                eref1[i] = e_ref[q / nomega] + omega[q % nomega];
+                worst = std::max(worst, relv[q]);
+            }
+            SGW_CUDA(cudaMemcpyAsync(w + o_list, list.data() + c0, sizeof(int) * nc, cudaMemcpyHostToDevice, st),
+                     "list copy");
+            SGW_CUDA(cudaMemcpyAsync(w + o_eref1, eref1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st),
+                     "list copy");
+            const int* d_list = (const int*)(w + o_list);
+            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, A.e_ref,
+                                     (const double*)(w + o_om), eta, A.x, (double2*)(w + o_rscr), d_rel, d_cert,
+                                     (double2*)(w + o_rvec), std::min(grid_r, nc), st),
+                     "residual kernel");
+            SolveArgs B = A;
+            B.nrhs = nc;
+            B.nshift = 1;
+            B.rhs = (const double2*)(w + o_rvec);
+            B.e_ref = (const double*)(w + o_eref1);
+            B.sig = (const double*)(w + o_zero);
+            B.omega_seed = 0.0;
+            B.tol = std::min(0.5, std::max(1e-13, 0.3 * tol / worst));
+            B.x = (double2*)(w + o_dbuf);
+            B.uw = (double2*)(w + o_uw1);
+            B.seedw = (double2*)(w + o_seed1);
+            B.out_mv = (int*)(w + o_mv1);
+            B.out_res = (double*)(w + o_est1);
+            B.out_status = (int*)(w + o_st1);
+            SGW_CUDA(launch_solve(s->plan, B, std::min(grid1, nc), st), "correction solve");
+            SGW_CUDA(launch_pair_axpy(nc, d_list, s->npw, B.x, A.x, st), "refinement update");
+            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, A.e_ref,
+                                     (const double*)(w + o_om), eta, A.x, (double2*)(w + o_rscr), d_rel, d_cert,
+                                     nullptr, std::min(grid_r, nc), st),
+                     "residual kernel");
+            launches += 4;
+            SGW_CUDA(cudaMemcpyAsync(mv1.data(), B.out_mv, sizeof(int) * nc, cudaMemcpyDeviceToHost, st), "report");
+            SGW_CUDA(cudaStreamSynchronize(st), "refinement");
+            for (int i = 0; i < nc; ++i) mvv[list[c0 + i]] += mv1[i];
+        }
+        SGW_CUDA(cudaMemcpyAsync(relv.data(), d_rel, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
+        SGW_CUDA(cudaStreamSynchronize(st), "refinement");
+    }
+    if ((r = finish_out(out, st, "dpsi copy")) != SGW_OK) return r;
+    SGW_CUDA(cudaMemcpyAsync(certv.data(), d_cert, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaStreamSynchronize(st), "solve");
+    bool all = true;
+    for (size_t q = 0; q < np; ++q) {
+        if (relv[q] <= tol) stv[q] = SGW_PAIR_CONVERGED;
+        else if (stv[q] == SGW_PAIR_CONVERGED) stv[q] = SGW_PAIR_MAXITER;
+        all = all && stv[q] == SGW_PAIR_CONVERGED;
+    }
+    if (report) {
+        if (report->status) std::memcpy(report->status, stv.data(), sizeof(int) * np);
+        if (report->matvecs) std::memcpy(report->matvecs, mvv.data(), sizeof(int) * np);
+        if (report->est_res) std::memcpy(report->est_res, estv.data(), sizeof(double) * np);
+        if (report->rel_res) std::memcpy(report->rel_res, relv.data(), sizeof(double) * np);
+        if (report->cert) std::memcpy(report->cert, certv.data(), sizeof(double) * np);
+        if (report->launches) *report->launches = launches;
+    }
+    if (!all) return fail(SGW_ENOCONV, "some (rhs, omega) pairs did not reach the tolerance");
+    return SGW_OK;
+}
+
+sgw_status sgw_residual(sgw_system* s, int nrhs, const void* rhs, const double* e_ref, int nomega, const double* omega,
+                        double eta, const void* dpsi, double* rel_res, double* cert, void* stream) {
+    g_err.clear();
+    if (!s || !rhs || !e_ref || !omega || !dpsi) return fail(SGW_EINVAL, "NULL argument");
+    if (nrhs < 0 || nomega < 0) return fail(SGW_EINVAL, "negative size");
+    if (!(eta > 0.0)) return fail(SGW_EINVAL, "eta must be positive");
+    if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+    const size_t np = (size_t)nrhs * nomega;
+    if (np == 0) return SGW_OK;
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vb = sizeof(double2) * (size_t)s->npw;
+    Staged in_r, in_x;
+    sgw_status r;
+    if ((r = stage_in(rhs, vb * nrhs, in_r, st, "rhs")) != SGW_OK) return r;
+    if ((r = stage_in(dpsi, vb * np, in_x, st, "dpsi")) != SGW_OK) return r;
+    int grid = 0;
+    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid), "residual occupancy");
+    grid = (int)std::min<size_t>(grid, np);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t off_er = al(2 * vb * grid);
+    const size_t off_om = off_er + al(sizeof(double) * nrhs);
+    const size_t off_rel = off_om + al(sizeof(double) * nomega);
+    const size_t off_cert = off_rel + al(sizeof(double) * np);
+    const size_t total = off_cert + al(sizeof(double) * np);
+    if ((r = ensure_ws(s, total)) != SGW_OK) return r;
+    char* w = (char*)s->d_ws;
+    SGW_CUDA(cudaMemcpyAsync(w + off_er, e_ref, sizeof(double) * nrhs, cudaMemcpyHostToDevice, st), "e_ref copy");
+    SGW_CUDA(cudaMemcpyAsync(w + off_om, omega, sizeof(double) * nomega, cudaMemcpyHostToDevice, st), "omega copy");
+    SGW_CUDA(launch_residual(s->plan, nrhs, nomega, nullptr, 0, (const double2*)in_r.dev, (const double*)(w + off_er),
+                             (const double*)(w + off_om), eta, (const double2*)in_x.dev, (double2*)w,
+                             (double*)(w + off_rel), (double*)(w + off_cert), nullptr, grid, st),
+             "residual kernel");
+    std::vector<double> relv(np), certv(np);
+    SGW_CUDA(cudaMemcpyAsync(relv.data(), w + off_rel, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "copy");
+    SGW_CUDA(cudaMemcpyAsync(certv.data(), w + off_cert, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "copy");
+    SGW_CUDA(cudaStreamSynchronize(st), "residual");
+    if (rel_res) std::memcpy(rel_res, relv.data(), sizeof(double) * np);
+    if (cert) std::memcpy(cert, certv.data(), sizeof(double) * np);
+    return SGW_OK;
+}
+
+void sgw_destroy_system(sgw_system* s) {
+    if (!s) return;
+    cudaSetDevice(s->dev);
+    cudaDeviceSynchronize();
+    free_system(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,634 @@
+// Hot kernels: the multishift BiCGstab(ell) solve of the Sternheimer equation (Eq. 6 with
+// the operator of Eq. 7), the H application test hook and the true-residual certificate.
+//
+// Solver organisation.  One CTA owns one right-hand side at a time (a work queue hands
+// them out) and runs its whole Krylov iteration: every H application, dot product,
+// recurrence scalar and shift update of that right-hand side happens inside the CTA, so
+// the iteration needs no grid-wide synchronisation and no host round trips.  Seed vectors
+// live in a per-CTA slice of global memory (L2-resident), shift vectors x_j and u_j in
+// the caller's output and in a per-CTA workspace.
+//
+// Method (shifted BiCGstab(ell) for families of shifted systems, the Krylov solver the
+// paper cites for "all frequencies at the cost of one", Sec. 2.2).  The seed system is
+// A_0 = P_c H P_c - z_s; shift j solves (A_0 + sigma_j) x_j = b with sigma_j = z_s - z_j.
+// With phi_n the BiCG residual polynomials of the seed and zeta_n^j = phi_n(-sigma_j),
+//   zeta_{n+1} = (1 + alpha_n beta_{n-1}/alpha_{n-1} + alpha_n sigma) zeta_n
+//                - (alpha_n beta_{n-1}/alpha_{n-1}) zeta_{n-1},
+//   alpha_n^j = alpha_n zeta_n / zeta_{n+1},   beta_{n-1}^j = beta_{n-1} (zeta_{n-1}/zeta_n)^2,
+// and every minimal-residual polynomial q(l) = 1 - sum_i gamma_i l^i of the seed becomes
+// q^j(mu) = q(mu - sigma_j) / q(-sigma_j) for shift j.  Residuals of all shifts stay
+// collinear with the seed's, r^j = r / (Psi^j zeta^j) with Psi^j the product of the
+// q(-sigma_j); each shift keeps only x_j and its direction u_j, and the powers
+// A_j^t r^j, A_j^t u_j it needs are expanded binomially in the seed's R_t = A_0^t r and
+// U_t = A_0^t u.
+#include <cuda_runtime.h>
+
+#include "setup.h"
+#include "sgw_internal.cuh"
+
+namespace sgw {
+
+namespace {
+
+// Per-shift state in shared memory.
+struct ShiftSmem {
+    int zp, zc, psi, zn, as, bs, cr, las, cx, ca, cb, sig, est, st, mv, act, end;
+};
+
+__host__ __device__ inline ShiftSmem shift_layout(int base, int ns) {
+    ShiftSmem s;
+    int off = base;
+    s.zp = off;  off = align16(off + ns * 16);
+    s.zc = off;  off = align16(off + ns * 16);
+    s.psi = off; off = align16(off + ns * 16);
+    s.zn = off;  off = align16(off + ns * 16);
+    s.as = off;  off = align16(off + ns * 16);
+    s.bs = off;  off = align16(off + ns * 16);
+    s.cr = off;  off = align16(off + ns * 16);
+    s.las = off; off = align16(off + ns * 16);
+    s.cx = off;  off = align16(off + ns * kMaxEll * 16);
+    s.ca = off;  off = align16(off + ns * kMaxEll * 16);
+    s.cb = off;  off = align16(off + ns * kMaxEll * 16);
+    s.sig = off; off = align16(off + ns * 8);
+    s.est = off; off = align16(off + ns * 8);
+    s.st = off;  off = align16(off + ns * 4);
+    s.mv = off;  off = align16(off + ns * 4);
+    s.act = off; off = align16(off + ns * 4);
+    s.end = off;
+    return s;
+}
+
+struct SeedScalars {
+    double2 rho0, alpha, omega, alpha_prev, beta;
+    double2 gam[kMaxEll];
+    double bnorm, rnorm;
+    int first, nact, fail;
+};
+
+__device__ __forceinline__ int binom(int n, int k) {
+    // n <= 4
+    const int t[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+    return t[n][k];
+}
+
+// Solves the ell x ell Hermitian system M g = v (complex, FP64) by Gaussian elimination
+// with partial pivoting.  Returns false on a zero pivot.
+__device__ bool small_solve(double2 (&M)[kMaxEll][kMaxEll], double2 (&v)[kMaxEll], int n, double2 (&g)[kMaxEll]) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        double best = cabs2(M[c][c]);
+        for (int r = c + 1; r < n; ++r)
+            if (cabs2(M[r][c]) > best) { best = cabs2(M[r][c]); piv = r; }
+        if (!(best > 0.0)) return false;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) { double2 t = M[c][k]; M[c][k] = M[piv][k]; M[piv][k] = t; }
+            double2 t = v[c]; v[c] = v[piv]; v[piv] = t;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            const double2 f = cdiv(M[r][c], M[c][c]);
+            for (int k = c; k < n; ++k) M[r][k] = csub(M[r][k], cmul(f, M[c][k]));
+            v[r] = csub(v[r], cmul(f, v[c]));
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double2 s = v[r];
+        for (int k = r + 1; k < n; ++k) s = csub(s, cmul(M[r][k], g[k]));
+        g[r] = cdiv(s, M[r][r]);
+    }
+    return true;
+}
+
+__device__ __forceinline__ double2 cpowr(double2 a, int e) {
+    double2 r = make_double2(1.0, 0.0);
+    for (int i = 0; i < e; ++i) r = cmul(r, a);
+    return r;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SeedScalars S;
+    __shared__ int s_r;
+    __shared__ double2 s_dot[kRedSlots];
+
+    load_twiddles(P, smem);
+    const ApplySmem L = apply_smem_layout(P);
+    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const int ns = A.nshift, ell = A.ell, npw = P.npw;
+    const ShiftSmem Q = shift_layout(L.end, ns);
+    double2* zp = reinterpret_cast<double2*>(smem + Q.zp);
+    double2* zc = reinterpret_cast<double2*>(smem + Q.zc);
+    double2* Psi = reinterpret_cast<double2*>(smem + Q.psi);
+    double2* zn = reinterpret_cast<double2*>(smem + Q.zn);
+    double2* as = reinterpret_cast<double2*>(smem + Q.as);
+    double2* bs = reinterpret_cast<double2*>(smem + Q.bs);
+    double2* cr = reinterpret_cast<double2*>(smem + Q.cr);
+    double2* las = reinterpret_cast<double2*>(smem + Q.las);
+    double2* cx = reinterpret_cast<double2*>(smem + Q.cx);
+    double2* ca = reinterpret_cast<double2*>(smem + Q.ca);
+    double2* cb = reinterpret_cast<double2*>(smem + Q.cb);
+    double* sig = reinterpret_cast<double*>(smem + Q.sig);
+    double* est = reinterpret_cast<double*>(smem + Q.est);
+    int* st = reinterpret_cast<int*>(smem + Q.st);
+    int* mv = reinterpret_cast<int*>(smem + Q.mv);
+    int* act = reinterpret_cast<int*>(smem + Q.act);
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double2* W = A.seedw + (size_t)blockIdx.x * (2 * ell + 3) * npw;
+    double2* R[kMaxEll + 1];
+    double2* U[kMaxEll + 1];
+    for (int i = 0; i <= kMaxEll; ++i) {
+        R[i] = W + (size_t)min(i, ell) * npw;
+        U[i] = W + (size_t)(ell + 1 + min(i, ell)) * npw;
+    }
+    double2* RT = W + (size_t)(2 * ell + 2) * npw;
+    double2* UW = A.uw + (size_t)blockIdx.x * ns * npw;
+    for (int j = tid; j < ns; j += nt) sig[j] = A.sig[j];
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_r = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const int r = s_r;
+        if (r >= A.nrhs) break;
+        const double2* rhs = A.rhs + (size_t)r * npw;
+        double2* X = A.x + (size_t)r * ns * npw;
+        const double2 zs = make_double2(A.e_ref[r] + A.omega_seed, A.eta);
+
+        // b = -P_c rhs (Eq. 8 with the sign of the problem statement)
+        block_dots(P.psi, P.nocc, npw, rhs, npw, red, coef);
+        {
+            double2 acc[1] = {cz()};
+            for (int g = tid; g < npw; g += nt) {
+                double2 h = rhs[g];
+                for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
+                const double2 b = make_double2(-h.x, -h.y);
+                R[0][g] = b;
+                RT[g] = b;
+                U[0][g] = cz();
+                acc[0].x += cabs2(b);
+            }
+            block_sum<1>(acc, red, s_dot);
+        }
+        for (size_t i = tid; i < (size_t)ns * npw; i += nt) {
+            X[i] = cz();
+            UW[i] = cz();
+        }
+        if (tid == 0) {
+            S.bnorm = sqrt(s_dot[0].x);
+            S.rho0 = make_double2(1.0, 0.0);
+            S.alpha = cz();
+            S.omega = make_double2(1.0, 0.0);
+            S.alpha_prev = make_double2(1.0, 0.0);
+            S.first = 1;
+            S.fail = isfinite(S.bnorm) ? 0 : SGW_PAIR_NONFINITE;
+            S.nact = (S.bnorm > 0.0 && S.fail == 0) ? ns : 0;
+        }
+        for (int j = tid; j < ns; j += nt) {
+            zp[j] = zc[j] = Psi[j] = make_double2(1.0, 0.0);
+            las[j] = make_double2(1.0, 0.0);
+            st[j] = -1;
+            mv[j] = 0;
+            est[j] = 1.0;
+            act[j] = j;
+        }
+        __syncthreads();
+        if (S.nact == 0) {
+            // zero right-hand side: dpsi = 0 exactly; a non-finite one is reported as such
+            for (int j = tid; j < ns; j += nt) {
+                st[j] = S.fail ? S.fail : SGW_PAIR_CONVERGED;
+                est[j] = S.fail ? NAN : 0.0;
+            }
+        }
+        int mvc = 0;
+
+        while (S.nact > 0 && S.fail == 0 && mvc + 2 * ell <= A.max_mv) {
+            if (tid == 0) S.rho0 = make_double2(-(S.omega.x * S.rho0.x - S.omega.y * S.rho0.y),
+                                                -(S.omega.x * S.rho0.y + S.omega.y * S.rho0.x));
+            __syncthreads();
+            // ---------------------------------------------------------------- BiCG part
+            for (int j = 0; j < ell; ++j) {
+                block_dots(RT, 1, 0, R[j], npw, red, s_dot);
+                if (tid == 0) {
+                    const double2 rho1 = s_dot[0];
+                    S.beta = cdiv(cmul(S.alpha, rho1), S.rho0);
+                    S.rho0 = rho1;
+                    if (!cfinite(S.beta) || (rho1.x == 0.0 && rho1.y == 0.0)) S.fail = SGW_PAIR_BREAKDOWN;
+                }
+                __syncthreads();
+                if (S.fail) break;
+                {
+                    const double2 be = S.beta;
+                    for (int g = tid; g < npw; g += nt)
+                        for (int i = 0; i <= j; ++i) U[i][g] = csub(R[i][g], cmul(be, U[i][g]));
+                }
+                __syncthreads();
+                apply_h_block(P, smem, U[j], U[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+                block_dots(RT, 1, 0, U[j + 1], npw, red, s_dot);
+                if (tid == 0) {
+                    const double2 gam = s_dot[0];
+                    if (gam.x == 0.0 && gam.y == 0.0) S.fail = SGW_PAIR_BREAKDOWN;
+                    else S.alpha = cdiv(S.rho0, gam);
+                    if (!cfinite(S.alpha)) S.fail = SGW_PAIR_NONFINITE;
+                }
+                __syncthreads();
+                if (S.fail) break;
+                // shift scalars of this BiCG step
+                {
+                    const double2 al = S.alpha;
+                    const double2 bb = S.first ? cz() : make_double2(-S.beta.x, -S.beta.y);
+                    const double2 cf = S.first ? cz() : cdiv(cmul(al, bb), S.alpha_prev);
+                    for (int a = tid; a < S.nact; a += nt) {
+                        const int k = act[a];
+                        const double2 one_c = make_double2(1.0 + cf.x + al.x * sig[k], cf.y + al.y * sig[k]);
+                        const double2 znk = csub(cmul(one_c, zc[k]), cmul(cf, zp[k]));
+                        zn[k] = znk;
+                        as[k] = cdiv(cmul(al, zc[k]), znk);
+                        const double2 q = cdiv(zp[k], zc[k]);
+                        bs[k] = S.first ? cz() : cmul(bb, cmul(q, q));
+                        cr[k] = cdiv(make_double2(1.0, 0.0), cmul(Psi[k], zc[k]));
+                        if (!cfinite(as[k]) || !cfinite(bs[k]) || !cfinite(cr[k])) st[k] = SGW_PAIR_NONFINITE;
+                    }
+                }
+                __syncthreads();
+                // shift pass: u_j <- cr r + bs u_j ;  x_j <- x_j + as u_j
+                {
+                    const int na = S.nact;
+                    for (int g = tid; g < npw; g += nt) {
+                        const double2 r0 = R[0][g];
+                        for (int a = 0; a < na; ++a) {
+                            const int k = act[a];
+                            if (st[k] >= 0) continue;
+                            double2* up = UW + (size_t)k * npw + g;
+                            double2* xp = X + (size_t)k * npw + g;
+                            const double2 u = cfma(cr[k], r0, cmul(bs[k], *up));
+                            *up = u;
+                            *xp = cfma(as[k], u, *xp);
+                        }
+                    }
+                }
+                __syncthreads();
+                {
+                    const double2 al = S.alpha;
+                    for (int g = tid; g < npw; g += nt)
+                        for (int i = 0; i <= j; ++i) R[i][g] = csub(R[i][g], cmul(al, U[i + 1][g]));
+                }
+                __syncthreads();
+                apply_h_block(P, smem, R[j], R[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+                for (int a = tid; a < S.nact; a += nt) {
+                    const int k = act[a];
+                    zp[k] = zc[k];
+                    zc[k] = zn[k];
+                    las[k] = as[k];
+                }
+                if (tid == 0) {
+                    S.alpha_prev = S.alpha;
+                    S.first = 0;
+                }
+                mvc += 2;
+                __syncthreads();
+            }
+            if (S.fail) break;
+
+            // ------------------------------------------------------------------ MR part
+            {
+                // Gram entries <R_i, R_k>, 1 <= i <= k <= ell, and <R_i, R_0>
+                double2 acc[14];
+#pragma unroll
+                for (int i = 0; i < 14; ++i) acc[i] = cz();
+                for (int g = tid; g < npw; g += nt) {
+                    double2 rv[kMaxEll + 1];
+#pragma unroll
+                    for (int t = 0; t <= kMaxEll; ++t) rv[t] = t <= ell ? R[t][g] : cz();
+                    int q = 0;
+#pragma unroll
+                    for (int i = 1; i <= kMaxEll; ++i) {
+#pragma unroll
+                        for (int k = i; k <= kMaxEll; ++k) {
+                            acc[q] = cadd(acc[q], cmulc(rv[i], rv[k]));
+                            ++q;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 1; i <= kMaxEll; ++i) acc[9 + i] = cadd(acc[9 + i], cmulc(rv[i], rv[0]));
+                }
+                // 10 Gram entries (indices 0..9) + 4 projections (10..13)
+                block_sum<14>(acc, red, s_dot);
+                if (tid == 0) {
+                    double2 M[kMaxEll][kMaxEll], v[kMaxEll], g[kMaxEll];
+                    int q = 0;
+                    for (int i = 1; i <= kMaxEll; ++i)
+                        for (int k = i; k <= kMaxEll; ++k) {
+                            const double2 e = s_dot[q++];
+                            if (i <= ell && k <= ell) {
+                                M[i - 1][k - 1] = e;
+                                M[k - 1][i - 1] = make_double2(e.x, -e.y);
+                            }
+                        }
+                    for (int i = 1; i <= ell; ++i) v[i - 1] = s_dot[9 + i];
+                    if (!small_solve(M, v, ell, g)) {
+                        S.fail = SGW_PAIR_BREAKDOWN;
+                    } else {
+                        for (int i = 0; i < ell; ++i) S.gam[i] = g[i];
+                        S.omega = g[ell - 1];
+                        if (!cfinite(S.omega) || (S.omega.x == 0.0 && S.omega.y == 0.0)) S.fail = SGW_PAIR_BREAKDOWN;
+                    }
+                }
+                __syncthreads();
+                if (S.fail) break;
+            }
+            // per-shift coefficients of the MR update
+            for (int a = tid; a < S.nact; a += nt) {
+                const int k = act[a];
+                const double2 sg = make_double2(sig[k], 0.0);
+                const double2 msg = make_double2(-sig[k], 0.0);
+                // c_m: coefficients of q(mu - sigma) = 1 - sum_i gamma_i (mu - sigma)^i
+                double2 c[kMaxEll + 1];
+                c[0] = make_double2(1.0, 0.0);
+                for (int m = 1; m <= ell; ++m) c[m] = cz();
+                for (int i = 1; i <= ell; ++i)
+                    for (int m = 0; m <= i; ++m)
+                        c[m] = csub(c[m], cscal(cmul(S.gam[i - 1], cpowr(msg, i - m)), (double)binom(i, m)));
+                const double2 q0 = c[0];
+                double2 gs[kMaxEll];
+                for (int i = 1; i <= ell; ++i) gs[i - 1] = cdiv(make_double2(-c[i].x, -c[i].y), q0);
+                const double2 rsc = cdiv(make_double2(1.0, 0.0), cmul(Psi[k], zc[k]));
+                const double2 rpre = cdiv(make_double2(1.0, 0.0), cmul(Psi[k], zp[k]));
+                const double2 aa = cdiv(csub(rpre, rsc), las[k]);
+                const double2 bc = cdiv(cmul(rpre, S.alpha_prev), las[k]);
+                for (int t = 0; t < ell; ++t) {
+                    double2 d = cz();
+                    for (int i = t + 1; i <= ell; ++i)
+                        d = cadd(d, cscal(cmul(gs[i - 1], cpowr(sg, i - 1 - t)), (double)binom(i - 1, t)));
+                    cx[k * kMaxEll + t] = cmul(rsc, d);
+                    ca[k * kMaxEll + t] = cmul(d, aa);
+                    cb[k * kMaxEll + t] = cmul(d, bc);
+                }
+                Psi[k] = cmul(Psi[k], q0);
+                if (!cfinite(q0) || !cfinite(aa) || !cfinite(bc)) st[k] = SGW_PAIR_NONFINITE;
+            }
+            __syncthreads();
+            // MR pass: shifts, then the seed's R_0 and U_0
+            {
+                const int na = S.nact;
+                double2 acc[1] = {cz()};
+                for (int g = tid; g < npw; g += nt) {
+                    double2 rv[kMaxEll + 1], uv[kMaxEll + 1];
+#pragma unroll
+                    for (int t = 0; t <= kMaxEll; ++t) {
+                        rv[t] = t <= ell ? R[t][g] : cz();
+                        uv[t] = t <= ell ? U[t][g] : cz();
+                    }
+                    for (int a = 0; a < na; ++a) {
+                        const int k = act[a];
+                        if (st[k] >= 0) continue;
+                        double2* up = UW + (size_t)k * npw + g;
+                        double2* xp = X + (size_t)k * npw + g;
+                        double2 xv = *xp, u = *up;
+#pragma unroll
+                        for (int t = 0; t < kMaxEll; ++t) {
+                            if (t < ell) {
+                                xv = cfma(cx[k * kMaxEll + t], rv[t], xv);
+                                u = csub(u, cadd(cmul(ca[k * kMaxEll + t], rv[t]), cmul(cb[k * kMaxEll + t], uv[t + 1])));
+                            }
+                        }
+                        *xp = xv;
+                        *up = u;
+                    }
+                    double2 r0 = rv[0], u0 = uv[0];
+#pragma unroll
+                    for (int i = 1; i <= kMaxEll; ++i) {
+                        if (i <= ell) {
+                            r0 = csub(r0, cmul(S.gam[i - 1], rv[i]));
+                            u0 = csub(u0, cmul(S.gam[i - 1], uv[i]));
+                        }
+                    }
+                    R[0][g] = r0;
+                    U[0][g] = u0;
+                    acc[0].x += cabs2(r0);
+                }
+                block_sum<1>(acc, red, s_dot);
+            }
+            if (tid == 0) S.rnorm = sqrt(s_dot[0].x);
+            __syncthreads();
+            // convergence of each shift from the collinear residual; renormalise zeta
+            for (int a = tid; a < S.nact; a += nt) {
+                const int k = act[a];
+                if (st[k] >= 0) { mv[k] = mvc; continue; }
+                const double2 sc = cmul(Psi[k], zc[k]);
+                const double e = S.rnorm / (sqrt(cabs2(sc)) * S.bnorm);
+                est[k] = e;
+                if (!isfinite(e)) {
+                    st[k] = SGW_PAIR_NONFINITE;
+                    mv[k] = mvc;
+                } else if (e <= A.tol) {
+                    st[k] = SGW_PAIR_CONVERGED;
+                    mv[k] = mvc;
+                }
+                const double2 f = zc[k];
+                zc[k] = make_double2(1.0, 0.0);
+                zp[k] = cdiv(zp[k], f);
+                Psi[k] = cmul(Psi[k], f);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int n = 0;
+                for (int a = 0; a < S.nact; ++a)
+                    if (st[act[a]] < 0) act[n++] = act[a];
+                S.nact = n;
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        for (int j = tid; j < ns; j += nt) {
+            int s = st[j];
+            if (s < 0) {
+                s = S.fail ? S.fail : SGW_PAIR_MAXITER;
+                mv[j] = mvc;
+            }
+            A.out_status[(size_t)r * ns + j] = s;
+            A.out_mv[(size_t)r * ns + j] = mv[j];
+            A.out_res[(size_t)r * ns + j] = est[j];
+        }
+    }
+}
+
+// y_i = H x_i, or (P_c H P_c - z_i) x_i when `project` is set.  One CTA per vector
+// (persistent over the batch); scratch holds P_c x per CTA.
+__global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, const double2* __restrict__ x,
+                                                            double2* __restrict__ y, const double2* __restrict__ z,
+                                                            int project, double2* __restrict__ scratch) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    load_twiddles(P, smem);
+    const ApplySmem L = apply_smem_layout(P);
+    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
+    double2* xs = scratch + (size_t)blockIdx.x * npw;
+    for (int v = blockIdx.x; v < nvec; v += gridDim.x) {
+        const double2* xv = x + (size_t)v * npw;
+        double2* yv = y + (size_t)v * npw;
+        if (!project) {
+            apply_h_block(P, smem, xv, yv, cz(), 0);
+            continue;
+        }
+        block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
+        for (int g = tid; g < npw; g += nt) {
+            double2 h = xv[g];
+            for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
+            xs[g] = h;
+        }
+        __syncthreads();
+        apply_h_block(P, smem, xs, yv, cz(), APPLY_PROJ_OUT);
+        const double2 zz = z[v];
+        for (int g = tid; g < npw; g += nt) yv[g] = csub(yv[g], cmul(zz, xv[g]));
+        __syncthreads();
+    }
+}
+
+// For every listed pair q = r * ns + j (all pairs when list is NULL):
+//   res = -P_c rhs_r - (P_c H P_c - z_rj) x_rj  in FP64,
+//   rel[q] = |res| / |P_c rhs_r|,  cert[q] = |res| / (eta |x_rj|),
+// and, when store is given, store[i] = -res (the right-hand side of the correction
+// equation in the solver's convention b = -P_c rhs).
+__global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs, int ns, const int* __restrict__ list,
+                                                               int nlist, const double2* __restrict__ rhs,
+                                                               const double* __restrict__ e_ref,
+                                                               const double* __restrict__ omega, double eta,
+                                                               const double2* __restrict__ x,
+                                                               double2* __restrict__ scratch, double* __restrict__ rel,
+                                                               double* __restrict__ cert, double2* __restrict__ store) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double2 s_dot[kRedSlots];
+    load_twiddles(P, smem);
+    const ApplySmem L = apply_smem_layout(P);
+    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
+    double2* xs = scratch + (size_t)blockIdx.x * 2 * npw;
+    double2* ys = xs + npw;
+    const int count = list ? nlist : nrhs * ns;
+    for (int i = blockIdx.x; i < count; i += gridDim.x) {
+        const int q = list ? list[i] : i;
+        const int r = q / ns, j = q % ns;
+        const double2* xv = x + (size_t)q * npw;
+        const double2* rv = rhs + (size_t)r * npw;
+        const double2 z = make_double2(e_ref[r] + omega[j], eta);
+        block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
+        for (int g = tid; g < npw; g += nt) {
+            double2 h = xv[g];
+            for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
+            xs[g] = h;
+        }
+        __syncthreads();
+        apply_h_block(P, smem, xs, ys, cz(), APPLY_PROJ_OUT);
+        block_dots(P.psi, P.nocc, npw, rv, npw, red, coef);
+        double2 acc[3] = {cz(), cz(), cz()};
+        for (int g = tid; g < npw; g += nt) {
+            double2 h = rv[g];
+            for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
+            const double2 b = make_double2(-h.x, -h.y);
+            const double2 ax = csub(ys[g], cmul(z, xv[g]));
+            const double2 res = csub(b, ax);
+            if (store) store[(size_t)i * npw + g] = make_double2(-res.x, -res.y);
+            acc[0].x += cabs2(res);
+            acc[1].x += cabs2(b);
+            acc[2].x += cabs2(xv[g]);
+        }
+        block_sum<3>(acc, red, s_dot);
+        if (tid == 0) {
+            const double rn = sqrt(s_dot[0].x), bn = sqrt(s_dot[1].x), xn = sqrt(s_dot[2].x);
+            rel[q] = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
+            cert[q] = xn > 0.0 ? rn / (eta * xn) : (rn > 0.0 ? INFINITY : 0.0);
+        }
+        __syncthreads();
+    }
+}
+
+// x[list[i]] += d[i] for the listed pairs (refinement update).
+__global__ void pair_axpy_kernel(int nlist, const int* __restrict__ list, int npw, const double2* __restrict__ d,
+                                 double2* __restrict__ x) {
+    const size_t n = (size_t)nlist * npw;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = t / npw, g = t % npw;
+        double2* xp = x + (size_t)list[i] * npw + g;
+        *xp = cadd(*xp, d[t]);
+    }
+}
+
+// ------------------------------------------------------------------------ host launchers
+
+int apply_smem_bytes(const Plan& P) { return apply_smem_layout(P).end; }
+
+int solve_smem_bytes(const Plan& P, int nshift) {
+    const ApplySmem L = apply_smem_layout(P);
+    return shift_layout(L.end, nshift).end;
+}
+
+cudaError_t resident_grid(const void* kernel, int smem, int* grid) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    *grid = nsm * per;
+    return cudaSuccess;
+}
+
+cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid) {
+    int g = 0;
+    cudaError_t e = resident_grid((const void*)ms_solve_kernel, solve_smem_bytes(P, nshift), &g);
+    if (e != cudaSuccess) return e;
+    *grid = g < nrhs ? g : nrhs;
+    if (*grid < 1) *grid = 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream_t st) {
+    const int smem = solve_smem_bytes(P, a.nshift);
+    cudaError_t e = cudaFuncSetAttribute((const void*)ms_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    ms_solve_kernel<<<grid, kThreads, smem, st>>>(P, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
+                         double2* scratch, int grid, cudaStream_t st) {
+    const int smem = apply_smem_bytes(P);
+    cudaError_t e = cudaFuncSetAttribute((const void*)apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    apply_kernel<<<grid, kThreads, smem, st>>>(P, nvec, x, y, z, project, scratch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
+                            const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
+                            double* rel, double* cert, double2* store, int grid, cudaStream_t st) {
+    const int smem = apply_smem_bytes(P);
+    cudaError_t e = cudaFuncSetAttribute((const void*)residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    residual_kernel<<<grid, kThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
+                                                  cert, store);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st) {
+    if (nlist == 0) return cudaSuccess;
+    pair_axpy_kernel<<<1024, 256, 0, st>>>(nlist, list, npw, d, x);
+    return cudaGetLastError();
+}
+
+const void* solve_kernel_ptr() { return (const void*)ms_solve_kernel; }
+const void* apply_kernel_ptr() { return (const void*)apply_kernel; }
+const void* residual_kernel_ptr() { return (const void*)residual_kernel; }
+
+}  // namespace sgw

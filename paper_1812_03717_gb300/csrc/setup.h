@@ -1,0 +1,71 @@
+// Host-side launchers of the set-up kernels (setup.cu) and the hot kernels (kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sgw_internal.cuh"
+
+namespace sgw {
+
+struct SphereArgs {
+    double b[3][3];   // reciprocal lattice rows (bohr^-1)
+    double k[3];      // fractional k
+    double ecut;      // Ry == bohr^-2
+    int M[3];         // Miller bounds
+    int cap;          // capacity of the output arrays
+};
+
+struct BetaArgs {
+    double b[3][3];
+    double k[3];
+    double inv_sqrt_vol;
+    double width[64];
+    double tau[64][3];
+};
+constexpr int kMaxProj = 64;
+
+struct RhsArgs {
+    int lo[3];
+    int ext[3];
+};
+
+cudaError_t launch_sphere(const SphereArgs& a, int* miller, double* kin, int* count, cudaStream_t st);
+cudaError_t launch_boxmap(const int* miller, int npw, const int dims[3], int* map, cudaStream_t st);
+cudaError_t launch_beta(const BetaArgs& a, int nproj, const int* miller, int npw, double2* beta, cudaStream_t st);
+cudaError_t launch_twiddles(const int dims[3], double2* tw, cudaStream_t st);
+cudaError_t launch_rhs(const RhsArgs& a, const int* miller_kq, int npw_kq, const int* lut_k, const double2* psi_k,
+                       int npw_k, const int* gp, int n_v, int n_pert, double2* rhs, cudaStream_t st);
+cudaError_t launch_gram(const double2* psi, int nocc, int npw, double2* S, cudaStream_t st);
+
+// --- hot path (kernels.cu)
+
+struct SolveArgs {
+    int nrhs, nshift, ell, max_mv;
+    const double2* rhs;       // [nrhs][npw]
+    const double* e_ref;      // [nrhs]
+    const double* sig;        // [nshift]  z_seed - z_j (real: omega_seed - omega_j)
+    double omega_seed, eta, tol;
+    double2* x;               // [nrhs][nshift][npw]   (the caller's dpsi)
+    double2* uw;              // [grid][nshift][npw]   per-CTA shift directions
+    double2* seedw;           // [grid][2 ell + 3][npw] per-CTA seed vectors
+    int* counter;             // work queue (zeroed by the launcher)
+    int* out_mv;              // [nrhs][nshift]
+    double* out_res;          // [nrhs][nshift]
+    int* out_status;          // [nrhs][nshift]
+};
+
+// Shared memory (bytes) the solver needs beyond the H application, for nshift shifts.
+int solve_extra_smem(int nshift);
+int solve_smem_bytes(const Plan& P, int nshift);
+int apply_smem_bytes(const Plan& P);
+cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid);
+cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
+                         double2* scratch, int grid, cudaStream_t st);
+cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
+                            const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
+                            double* rel, double* cert, double2* store, int grid, cudaStream_t st);
+cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st);
+cudaError_t resident_grid(const void* kernel, int smem, int* grid);
+
+}  // namespace sgw

@@ -1,0 +1,336 @@
+// Internal declarations of the GB300 shifted-Sternheimer library.
+//
+// Data layout in device memory (all complex values are FP64 pairs, double2):
+//   plane-wave vectors      [nvec][npw]              canonical G order (Miller lexicographic)
+//   local potential         [N3][N1][N2]             one contiguous xy-plane per z
+//   stick buffer (on chip)  [nstick][N3]             z-columns of the box that hold a G
+//   plane buffer (on chip)  [N1][N2]                 one xy-plane of the box
+//   KB projectors           [nproj][npw]             <k+G|beta_p>
+//   occupied states         [nocc][npw]              psi_v of the basis (Eq. 7-8)
+//
+// One CTA owns one whole vector during an H application (Sec. 2.1: kinetic and non-local
+// parts in reciprocal space, V_loc in real space through the FFT).  The whole pruned box
+// of that vector -- only the z-columns ("sticks") through the sphere, plus one xy-plane
+// at a time -- lives in shared memory, so an application reads x once and writes y once.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "sgw.h"
+
+namespace sgw {
+
+constexpr int kThreads = 256;          // threads per CTA of every library kernel
+constexpr int kMaxStages = 12;         // radix stages per axis (N <= 5^12)
+constexpr int kMaxShifts = 512;        // frequencies per solve
+constexpr int kMaxEll = 4;             // BiCGstab(ell)
+constexpr int kRedSlots = 16;          // complex values reduced per block reduction
+
+struct AxisPlan {
+    int n;
+    int nst;
+    int rad[kMaxStages];
+};
+
+// Everything an H application needs; passed by value to kernels.
+struct Plan {
+    int n1, n2, n3, npw, nstick, nxcol;
+    AxisPlan ax[3];
+    const int* g2s;          // [npw]    stick * n3 + (m3 mod n3)
+    const int* stick_xy;     // [nstick] (m1 mod n1) * n2 + (m2 mod n2)
+    const int* xbase;        // [nxcol]  x * n2 for every x that has a stick
+    const double* vloc;      // [n3][n1][n2]
+    const double* kin;       // [npw]
+    const double2* twid;     // [n1 + n2 + n3]  exp(-2 pi i m / n_axis)
+    int nproj;
+    const double2* beta;     // [nproj][npw]
+    const double* dkb;       // [nproj]
+    int nocc;
+    const double2* psi;      // [nocc][npw]
+    double inv_nbox;         // 1 / (n1 n2 n3)
+};
+
+// Shared-memory carve-up of an H application (byte offsets from the dynamic base).
+struct ApplySmem {
+    int tw, sticks, plane, red, coef, end;
+};
+
+inline __host__ __device__ int align16(int b) { return (b + 15) & ~15; }
+
+inline __host__ __device__ ApplySmem apply_smem_layout(const Plan& p) {
+    ApplySmem s;
+    int off = 0;
+    s.tw = off;     off = align16(off + (p.n1 + p.n2 + p.n3) * 16);
+    s.sticks = off; off = align16(off + p.nstick * p.n3 * 16);
+    s.plane = off;  off = align16(off + p.n1 * p.n2 * 16);
+    s.red = off;    off = align16(off + (kThreads / 32) * kRedSlots * 16);
+    int nc = p.nocc > p.nproj ? p.nocc : p.nproj;
+    s.coef = off;   off = align16(off + ((nc + 7) / 8 * 8 + 8) * 16);
+    s.end = off;
+    return s;
+}
+
+// ----------------------------------------------------------------------- complex helpers
+
+__device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cscal(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// a * b + c
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    // scaled division (Smith's method) to avoid overflow in |b|^2
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.y + b.x * r;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// ------------------------------------------------------------------- block reductions
+
+// Sums NV complex values over the CTA; the totals land in out[0..NV).  All threads call.
+template <int NV>
+__device__ __forceinline__ void block_sum(double2 (&v)[NV], double2* red, double2* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[i].x += __shfl_down_sync(0xffffffffu, v[i].x, o);
+            v[i].y += __shfl_down_sync(0xffffffffu, v[i].y, o);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[warp * kRedSlots + i] = v[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double2 s = cz();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[w * kRedSlots + threadIdx.x]);
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// out[v] = sum_g conj(V[v*ld + g]) x[g] for v < nv (out must hold nv rounded up to 8).
+__device__ __forceinline__ void block_dots(const double2* V, int nv, int ld,
+                                           const double2* x, int n, double2* red, double2* out) {
+    for (int v0 = 0; v0 < nv; v0 += 8) {
+        double2 acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = cz();
+        const int cnt = min(8, nv - v0);
+        for (int g = threadIdx.x; g < n; g += blockDim.x) {
+            const double2 xv = x[g];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < cnt) acc[i] = cadd(acc[i], cmulc(V[(size_t)(v0 + i) * ld + g], xv));
+        }
+        block_sum<8>(acc, red, out + v0);
+    }
+}
+
+// -------------------------------------------------------------- shared-memory FFT lines
+
+// Small DFTs of radix 2, 3, 4, 5 with exponent sign SIGN (-1 forward, +1 inverse).
+template <int SIGN>
+__device__ __forceinline__ void dft_small(double2 (&v)[5], int R) {
+    if (R == 4) {
+        double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        double2 t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        // d * (SIGN i)
+        double2 t3 = make_double2(-SIGN * d.y, SIGN * d.x);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else if (R == 2) {
+        double2 a = v[0];
+        v[0] = cadd(a, v[1]);
+        v[1] = csub(a, v[1]);
+    } else if (R == 3) {
+        const double s3 = 0.86602540378443864676;   // sin(2 pi / 3)
+        double2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+        double2 m1 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
+        double2 m2 = make_double2(-SIGN * s3 * t2.y, SIGN * s3 * t2.x);
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(m1, m2);
+        v[2] = csub(m1, m2);
+    } else {  // R == 5
+        const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2pi/5), cos(4pi/5)
+        const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2pi/5), sin(4pi/5)
+        double2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+        double2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        double2 a1 = make_double2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+        double2 a2 = make_double2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+        double2 b1 = make_double2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
+        double2 b2 = make_double2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
+        // i * SIGN * b
+        double2 ib1 = make_double2(-SIGN * b1.y, SIGN * b1.x);
+        double2 ib2 = make_double2(-SIGN * b2.y, SIGN * b2.x);
+        v[0] = make_double2(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
+        v[1] = cadd(a1, ib1);
+        v[4] = csub(a1, ib1);
+        v[2] = cadd(a2, ib2);
+        v[3] = csub(a2, ib2);
+    }
+}
+
+// In-place batched FFT of `nlines` lines of length ax.n held in shared memory.  Line l
+// starts at base(l) = line_base ? line_base[l] : l * ls, element i at base + i * es.
+// Stockham autosort, decimation in time: stage with radix R and span Ns reads
+// x[j + k N/R], twiddles by w^(k (j mod Ns) N/(Ns R)), and writes the R outputs to
+// (j / Ns) Ns R + (j mod Ns) + k Ns.  Each stage reads all of a group of lines into
+// registers before any thread writes, so no second buffer is needed.
+// tw[m] = exp(-2 pi i m / n).  All threads of the CTA must call.
+template <int SIGN>
+__device__ void fft_lines(double2* data, int nlines, const int* __restrict__ line_base, int ls, int es,
+                          const AxisPlan& ax, const double2* tw) {
+    const int N = ax.n;
+    int Ns = 1;
+    for (int st = 0; st < ax.nst; ++st) {
+        const int R = ax.rad[st];
+        const int nb = N / R;
+        const int lpg = max(1, (int)blockDim.x / nb);
+        const int stride = N / (Ns * R);
+        for (int l0 = 0; l0 < nlines; l0 += lpg) {
+            const int t = threadIdx.x;
+            const int l = l0 + t / nb;
+            const int j = t % nb;
+            const bool act = (t < lpg * nb) && (l < nlines);
+            double2 v[5];
+            int base = 0;
+            const int jm = j % Ns;
+            if (act) {
+                base = line_base ? line_base[l] : l * ls;
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    if (k < R) v[k] = data[base + (j + k * nb) * es];
+#pragma unroll
+                for (int k = 1; k < 5; ++k) {
+                    if (k < R) {
+                        double2 w = tw[jm * k * stride];
+                        if (SIGN > 0) w.y = -w.y;
+                        v[k] = cmul(v[k], w);
+                    }
+                }
+                dft_small<SIGN>(v, R);
+            }
+            __syncthreads();
+            if (act) {
+                const int d0 = (j / Ns) * Ns * R + jm;
+#pragma unroll
+                for (int k = 0; k < 5; ++k)
+                    if (k < R) data[base + (d0 + k * Ns) * es] = v[k];
+            }
+            __syncthreads();
+        }
+        Ns *= R;
+    }
+}
+
+// ------------------------------------------------------------------------- H application
+
+enum : int {
+    APPLY_PROJ_OUT = 1,   // y <- P_c y
+    APPLY_SUB_Z = 2       // y <- y - z x
+};
+
+// Loads the twiddle tables of the plan into shared memory (call once per kernel).
+__device__ __forceinline__ void load_twiddles(const Plan& P, unsigned char* smem) {
+    const ApplySmem L = apply_smem_layout(P);
+    double2* tw = reinterpret_cast<double2*>(smem + L.tw);
+    for (int i = threadIdx.x; i < P.n1 + P.n2 + P.n3; i += blockDim.x) tw[i] = P.twid[i];
+    __syncthreads();
+}
+
+// y = H x  (+ options) for one vector, by the whole CTA.  x and y are global and must not
+// alias.  Steps: KB coefficients c_p = D_p <beta_p|x>; scatter x into the sticks; inverse
+// FFT along z on the sticks; per z-plane: scatter the plane, inverse FFT along y (only
+// the x-columns that hold sticks) and x, multiply by V(r), forward FFT along x and y,
+// gather back into the sticks; forward FFT along z; gather the sphere, scale by 1/N^3 and
+// add T_G x_G + sum_p c_p beta_p(G).
+// x and y may have been written earlier in the same kernel, so they are read through the
+// coherent path (no __restrict__ / read-only cache).
+static __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, const double2* x,
+                                                  double2* y, double2 zsh, int mode) {
+    const ApplySmem L = apply_smem_layout(P);
+    const double2* tw = reinterpret_cast<const double2*>(smem + L.tw);
+    double2* sticks = reinterpret_cast<double2*>(smem + L.sticks);
+    double2* plane = reinterpret_cast<double2*>(smem + L.plane);
+    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n1 = P.n1, n2 = P.n2, n3 = P.n3, npw = P.npw, nst = P.nstick;
+    const double2* tw1 = tw;
+    const double2* tw2 = tw + n1;
+    const double2* tw3 = tw + n1 + n2;
+
+    // non-local: c_p = <beta_p|x>
+    if (P.nproj > 0) block_dots(P.beta, P.nproj, npw, x, npw, red, coef);
+
+    // sphere -> sticks
+    for (int i = tid; i < nst * n3; i += nt) sticks[i] = cz();
+    __syncthreads();
+    for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = x[g];
+    __syncthreads();
+    fft_lines<+1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
+
+    for (int iz = 0; iz < n3; ++iz) {
+        for (int i = tid; i < n1 * n2; i += nt) plane[i] = cz();
+        __syncthreads();
+        for (int s = tid; s < nst; s += nt) plane[P.stick_xy[s]] = sticks[s * n3 + iz];
+        __syncthreads();
+        fft_lines<+1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);     // along y, occupied x only
+        fft_lines<+1>(plane, n2, nullptr, 1, n2, P.ax[0], tw1);          // along x, every y
+        const double* vz = P.vloc + (size_t)iz * n1 * n2;
+        for (int i = tid; i < n1 * n2; i += nt) plane[i] = cscal(plane[i], vz[i]);
+        __syncthreads();
+        fft_lines<-1>(plane, n2, nullptr, 1, n2, P.ax[0], tw1);
+        fft_lines<-1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);
+        for (int s = tid; s < nst; s += nt) sticks[s * n3 + iz] = plane[P.stick_xy[s]];
+        __syncthreads();
+    }
+    fft_lines<-1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
+
+    // gather + kinetic + non-local
+    for (int g = tid; g < npw; g += nt) {
+        const double2 xv = x[g];
+        double2 h = cscal(sticks[P.g2s[g]], P.inv_nbox);
+        h = make_double2(fma(P.kin[g], xv.x, h.x), fma(P.kin[g], xv.y, h.y));
+        for (int p = 0; p < P.nproj; ++p) h = cfma(cscal(coef[p], P.dkb[p]), P.beta[(size_t)p * npw + g], h);
+        y[g] = h;
+    }
+    __syncthreads();
+
+    if (mode & APPLY_PROJ_OUT) {
+        block_dots(P.psi, P.nocc, npw, y, npw, red, coef);
+        for (int g = tid; g < npw; g += nt) {
+            double2 h = y[g];
+            for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
+            if (mode & APPLY_SUB_Z) h = csub(h, cmul(zsh, x[g]));
+            y[g] = h;
+        }
+    } else if (mode & APPLY_SUB_Z) {
+        for (int g = tid; g < npw; g += nt) y[g] = csub(y[g], cmul(zsh, x[g]));
+    }
+    __syncthreads();
+}
+
+}  // namespace sgw

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of libsgw.so (include/sgw.h): argument marshalling only.
+
+Vectors may be numpy arrays (host) or torch tensors (host or CUDA); the library detects
+device pointers itself.  Outputs are allocated like the main input (numpy -> numpy,
+CUDA tensor -> CUDA tensor).  Every compute step runs in the library's CUDA kernels; if
+the library is missing this module raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsgw.so")
+
+SGW_OK, SGW_EINVAL, SGW_ENOMEM, SGW_ECUDA, SGW_ENOCONV, SGW_EALIAS, SGW_ESTATE, SGW_EUNSUPPORTED = range(8)
+PAIR_CONVERGED, PAIR_MAXITER, PAIR_BREAKDOWN, PAIR_NONFINITE = range(4)
+STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV", "SGW_EALIAS", "SGW_ESTATE",
+                "SGW_EUNSUPPORTED"]
+
+EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
+           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_residual", "sgw_destroy_system",
+           "sgw_last_error"]
+
+
+class SgwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class _Cell(ctypes.Structure):
+    _fields_ = [("a", (ctypes.c_double * 3) * 3), ("n_atoms", ctypes.c_int), ("tau", ctypes.c_void_p)]
+
+
+class _KB(ctypes.Structure):
+    _fields_ = [("n_proj", ctypes.c_int), ("atom", ctypes.c_void_p), ("width", ctypes.c_void_p),
+                ("D", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("ell", ctypes.c_int), ("seed_index", ctypes.c_int), ("max_matvec", ctypes.c_int),
+                ("max_refine", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("matvecs", ctypes.c_void_p), ("est_res", ctypes.c_void_p), ("rel_res", ctypes.c_void_p),
+                ("cert", ctypes.c_void_p), ("status", ctypes.c_void_p), ("launches", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1812_03717_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.sgw_create_system.argtypes = [ctypes.POINTER(_Cell), dp, vp, vp, vp, ctypes.POINTER(_KB), ctypes.POINTER(vp)]
+    lib.sgw_get_gvectors.argtypes = [vp, vp, vp, vp]
+    lib.sgw_get_box_map.argtypes = [vp, vp]
+    lib.sgw_set_occupied.argtypes = [vp, ip, vp, vp]
+    lib.sgw_make_rhs.argtypes = [vp, vp, ip, vp, ip, vp, vp, vp]
+    lib.sgw_apply_h.argtypes = [vp, ip, vp, vp, vp]
+    lib.sgw_apply_shifted.argtypes = [vp, ip, vp, vp, vp, vp]
+    lib.sgw_solve_shifted.argtypes = [vp, ip, vp, vp, ip, vp, dp, dp, ctypes.POINTER(_Opts), vp,
+                                      ctypes.POINTER(_Report)]
+    lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
+    lib.sgw_destroy_system.argtypes = [vp]
+    lib.sgw_destroy_system.restype = None
+    lib.sgw_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS[:-2]:
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, allow=()):
+    if status != SGW_OK and status not in allow:
+        raise SgwError(status, load().sgw_last_error().decode())
+    return status
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data
+
+
+def _c128(x):
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.complex128:
+            raise TypeError("complex128 tensor required")
+        return x.contiguous()
+    return np.ascontiguousarray(x, dtype=np.complex128)
+
+
+def _like(x, shape):
+    if _is_torch(x):
+        import torch
+        return torch.empty(shape, dtype=torch.complex128, device=x.device)
+    return np.empty(shape, dtype=np.complex128)
+
+
+def _stream_of(x, stream):
+    if stream is not None:
+        return stream
+    if _is_torch(x) and x.is_cuda:
+        import torch
+        return torch.cuda.current_stream(x.device).cuda_stream
+    return None
+
+
+class System:
+    """One plane-wave basis with its Hamiltonian (sgw_create_system) and occupied states."""
+
+    def __init__(self, a, tau, ecut_ry, k_frac, fft_dims, vloc_r, kb_atom=(), kb_width=(), kb_d=()):
+        lib = load()
+        cell = _Cell()
+        a = np.asarray(a, dtype=np.float64)
+        for i in range(3):
+            for j in range(3):
+                cell.a[i][j] = float(a[i, j])
+        self._tau = np.ascontiguousarray(tau, dtype=np.float64).reshape(-1, 3)
+        cell.n_atoms = len(self._tau)
+        cell.tau = self._tau.ctypes.data
+        self._kb_atom = np.ascontiguousarray(kb_atom, dtype=np.int32)
+        self._kb_width = np.ascontiguousarray(kb_width, dtype=np.float64)
+        self._kb_d = np.ascontiguousarray(kb_d, dtype=np.float64)
+        kb = _KB(len(self._kb_atom), self._kb_atom.ctypes.data, self._kb_width.ctypes.data, self._kb_d.ctypes.data)
+        k = np.ascontiguousarray(k_frac, dtype=np.float64)
+        dims = np.ascontiguousarray(fft_dims, dtype=np.int32)
+        v = np.ascontiguousarray(vloc_r, dtype=np.float64)
+        if v.size != int(np.prod(dims)):
+            raise ValueError("vloc_r size does not match fft_dims")
+        h = ctypes.c_void_p()
+        _check(lib.sgw_create_system(ctypes.byref(cell), float(ecut_ry), k.ctypes.data, dims.ctypes.data,
+                                     v.ctypes.data, ctypes.byref(kb), ctypes.byref(h)))
+        self._h = h
+        n = ctypes.c_int()
+        _check(lib.sgw_get_gvectors(self._h, ctypes.byref(n), None, None))
+        self.n_pw = n.value
+        self.nocc = 0
+
+    @classmethod
+    def from_instance(cls, inst, k_frac):
+        return cls(inst.a, inst.tau, inst.ecut_ry, k_frac, inst.fft_dims, inst.vloc_r, inst.kb_atom,
+                   inst.kb_width, inst.kb_d)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sgw_destroy_system(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def gvectors(self):
+        mil = np.empty((self.n_pw, 3), dtype=np.int32)
+        kin = np.empty(self.n_pw, dtype=np.float64)
+        _check(load().sgw_get_gvectors(self._h, None, mil.ctypes.data, kin.ctypes.data))
+        return mil, kin
+
+    def box_map(self):
+        m = np.empty(self.n_pw, dtype=np.int32)
+        _check(load().sgw_get_box_map(self._h, m.ctypes.data))
+        return m
+
+    def set_occupied(self, psi_v, eps_v):
+        psi = _c128(psi_v)
+        eps = np.ascontiguousarray(eps_v, dtype=np.float64)
+        _check(load().sgw_set_occupied(self._h, len(eps), _ptr(psi), eps.ctypes.data))
+        self.nocc = len(eps)
+
+    def make_rhs(self, sys_k, psi_k, gp_miller, out=None, stream=None):
+        psi = _c128(psi_k)
+        gp = np.ascontiguousarray(gp_miller, dtype=np.int32).reshape(-1, 3)
+        n_v = psi.shape[0]
+        if out is None:
+            out = _like(psi, (n_v * len(gp), self.n_pw))
+        _check(load().sgw_make_rhs(self._h, sys_k._h, n_v, _ptr(psi), len(gp), gp.ctypes.data, _ptr(out),
+                                   _stream_of(psi, stream)))
+        return out
+
+    def apply_h(self, x, out=None, stream=None):
+        x = _c128(x)
+        nvec = x.shape[0] if x.ndim == 2 else 1
+        if out is None:
+            out = _like(x, x.shape)
+        _check(load().sgw_apply_h(self._h, nvec, _ptr(x), _ptr(out), _stream_of(x, stream)))
+        return out
+
+    def apply_shifted(self, x, z, out=None, stream=None):
+        x = _c128(x)
+        nvec = x.shape[0] if x.ndim == 2 else 1
+        zz = np.ascontiguousarray(np.broadcast_to(np.asarray(z, dtype=np.complex128), (nvec,)))
+        if out is None:
+            out = _like(x, x.shape)
+        _check(load().sgw_apply_shifted(self._h, nvec, _ptr(x), zz.ctypes.data, _ptr(out), _stream_of(x, stream)))
+        return out
+
+    def solve_shifted(self, rhs, e_ref, omega, eta, tol=1e-10, ell=4, seed_index=-1, max_matvec=0, max_refine=0,
+                      out=None, stream=None, raise_on_noconv=False):
+        """Returns (dpsi [nrhs][nomega][n_pw], report dict, converged flag)."""
+        rhs = _c128(rhs)
+        nrhs = rhs.shape[0]
+        e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        nw = len(omega)
+        if out is None:
+            out = _like(rhs, (nrhs, nw, self.n_pw))
+        rep = {"matvecs": np.zeros((nrhs, nw), dtype=np.int32), "est_res": np.zeros((nrhs, nw)),
+               "rel_res": np.zeros((nrhs, nw)), "cert": np.zeros((nrhs, nw)),
+               "status": np.zeros((nrhs, nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32)}
+        opts = _Opts(int(ell), int(seed_index), int(max_matvec), int(max_refine), _stream_of(rhs, stream))
+        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches")))
+        s = load().sgw_solve_shifted(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data,
+                                     float(eta), float(tol), ctypes.byref(opts), _ptr(out), ctypes.byref(crep))
+        _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
+        return out, rep, s == SGW_OK
+
+    def residual(self, rhs, e_ref, omega, eta, dpsi, stream=None):
+        rhs = _c128(rhs)
+        dpsi = _c128(dpsi)
+        e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        nrhs, nw = rhs.shape[0], len(omega)
+        rel = np.zeros((nrhs, nw))
+        cert = np.zeros((nrhs, nw))
+        _check(load().sgw_residual(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data, float(eta),
+                                   _ptr(dpsi), rel.ctypes.data, cert.ctypes.data, _stream_of(rhs, stream)))
+        return rel, cert

@@ -1,0 +1,252 @@
+"""Parity of the CUDA path with the FP64 oracle, through the C ABI.
+
+Index work (sphere, maps, Eq. 8 gather) must be bit-exact; FP64 H applications agree
+with the oracle's dense H to 1e-12 relative (FFT rounding at N^3 <= 36^3); solutions
+agree with the oracle's LU to 1e-8 relative per (rhs, omega) pair -- the stated accuracy
+target -- and their true residual certificate is checked on every pair.
+"""
+import numpy as np
+import pytest
+
+import instances as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_SOLVE = 1e-8       # max over pairs of |dpsi - dpsi_ref| / |dpsi_ref|
+TOL_APPLY = 1e-12      # relative, FP64 FFT apply vs dense H
+
+
+@pytest.fixture(scope="module")
+def sgw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1812_03717_gb300 as P
+    from paper_1812_03717_gb300 import build as B
+    import os
+    if not os.path.exists(B.LIB):
+        B.build()
+    return P
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return I.config1()
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return I.config2(k_subset=[0])
+
+
+def _systems(P, inst, ik=0):
+    kp = inst.kpoints[ik]
+    skq = P.System.from_instance(inst, kp.kq_frac)
+    sk = P.System.from_instance(inst, kp.k_frac)
+    skq.set_occupied(kp.psi_kq, kp.eps_kq)
+    return skq, sk
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+# ------------------------------------------------------------------------ index work
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_sphere_and_box_map_bit_exact(sgw, which, request):
+    inst = request.getfixturevalue(which)
+    kp = inst.kpoints[0]
+    for kf in (kp.k_frac, kp.kq_frac, np.zeros(3)):
+        s = sgw.System.from_instance(inst, kf)
+        mil, kin = s.gvectors
+        ref_m, ref_k = O.gsphere(inst.a, kf, inst.ecut_ry)
+        assert np.array_equal(mil, ref_m)
+        np.testing.assert_allclose(kin, ref_k, rtol=1e-14, atol=0)
+        assert np.array_equal(s.box_map(), O.box_map(ref_m, inst.fft_dims))
+
+
+def test_make_rhs_bit_exact(sgw, cfg2):
+    kp = cfg2.kpoints[0]
+    skq, sk = _systems(sgw, cfg2)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg2.gp_miller)
+    ref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, cfg2.gp_miller)
+    assert rhs.shape == ref.shape
+    assert np.array_equal(rhs, ref)
+
+
+# ---------------------------------------------------------------------- H application
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_apply_h_matches_dense(sgw, which, request):
+    inst = request.getfixturevalue(which)
+    kp = inst.kpoints[0]
+    h, mil, _ = O.dense_h_inst(inst, kp.kq_frac)
+    s = sgw.System.from_instance(inst, kp.kq_frac)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((5, len(mil))) + 1j * rng.standard_normal((5, len(mil)))
+    y = s.apply_h(x)
+    ref = x @ h.T
+    assert _relerr(y, ref).max() < TOL_APPLY
+
+
+def test_apply_shifted_matches_dense(sgw, cfg1):
+    kp = cfg1.kpoints[0]
+    h, mil, _ = O.dense_h_inst(cfg1, kp.kq_frac)
+    skq, _ = _systems(sgw, cfg1)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((4, len(mil))) + 1j * rng.standard_normal((4, len(mil)))
+    z = np.array([0.1 + 0.01j, -0.3 + 0.2j, 1.5 + 0.0037j, 0.0 + 1.0j])
+    y = skq.apply_shifted(x, z)
+    ref = np.stack([O.shifted_operator(h, kp.psi_kq, z[i]) @ x[i] for i in range(4)])
+    assert _relerr(y, ref).max() < TOL_APPLY
+
+
+def test_apply_device_pointers_equal_host(sgw, cfg1):
+    import torch
+    kp = cfg1.kpoints[0]
+    s = sgw.System.from_instance(cfg1, kp.kq_frac)
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((3, s.n_pw)) + 1j * rng.standard_normal((3, s.n_pw))
+    y_host = s.apply_h(x)
+    y_dev = s.apply_h(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(y_dev.cpu().numpy(), y_host)
+
+
+# ------------------------------------------------------------------------- the solve
+
+def test_solve_config1_all_pairs(sgw, cfg1):
+    """Full config 1 (32 rhs x 16 omega) against the oracle's LU, every pair."""
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)
+    e_ref = cfg1.e_ref(0)
+    dpsi, rep, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, tol=1e-10)
+    h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
+    ref = O.solve_shifted(h, kp.psi_kq, rhs, e_ref, cfg1.omega, cfg1.eta)
+    err = _relerr(dpsi, ref)
+    assert ok, rep["status"]
+    assert err.max() < TOL_SOLVE, err.max()
+    assert rep["rel_res"].max() <= 1e-10
+    rel, cert = skq.residual(rhs, e_ref, cfg1.omega, cfg1.eta, dpsi)
+    np.testing.assert_allclose(rel, rep["rel_res"], rtol=1e-6, atol=1e-16)
+    ref_rel, _ = O.residual(h, kp.psi_kq, rhs[:4], e_ref[:4], cfg1.omega, cfg1.eta, dpsi[:4])
+    np.testing.assert_allclose(rel[:4], ref_rel, rtol=1e-3, atol=1e-14)
+    assert np.all(err <= cert * (1 + 1e-6) + 1e-15)
+
+
+def test_solve_config2_sampled(sgw, cfg2):
+    """Config-2 size (N_pw ~ 1640, 36^3 box, 64 omega): all 512 right-hand sides of one
+    k-point in the launch configuration the benchmark times; 2 bands x 4 frequencies x all
+    32 perturbations compared with the oracle's LU; the residual certificate on every pair."""
+    kp = cfg2.kpoints[0]
+    skq, sk = _systems(sgw, cfg2)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg2.gp_miller)
+    e_ref = cfg2.e_ref(0)
+    dpsi, rep, ok = skq.solve_shifted(rhs, e_ref, cfg2.omega, cfg2.eta, tol=1e-10)
+    assert ok, np.unique(rep["status"], return_counts=True)
+    h, _, _ = O.dense_h_inst(cfg2, kp.kq_frac)
+    npert = cfg2.n_pert
+    for v in (0, 15):
+        rows = np.arange(v * npert, (v + 1) * npert)
+        for j in (0, 21, 42, 63):
+            ref = O.solve_shifted(h, kp.psi_kq, rhs[rows], e_ref[rows], cfg2.omega[j:j + 1], cfg2.eta)[:, 0]
+            err = _relerr(dpsi[rows, j], ref)
+            assert err.max() < TOL_SOLVE, (v, j, err.max())
+    assert rep["rel_res"].max() <= 1e-10
+
+
+def test_solve_device_buffers_and_single_shift(sgw, cfg1):
+    """Device-resident inputs give the host result; a single shift (the seed alone) works."""
+    import torch
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[:5]
+    e_ref = cfg1.e_ref(0)[:5]
+    d_host, _, ok1 = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta)
+    d_dev, _, ok2 = skq.solve_shifted(torch.from_numpy(rhs).cuda(), e_ref, cfg1.omega, cfg1.eta)
+    torch.cuda.synchronize()
+    assert ok1 and ok2
+    assert np.array_equal(d_dev.cpu().numpy(), d_host)
+    d1, _, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega[7:8], cfg1.eta)
+    assert ok
+    assert _relerr(d1[:, 0], d_host[:, 7]).max() < 1e-8
+
+
+@pytest.mark.parametrize("ell", [2, 4])
+def test_solution_independent_of_ell(sgw, cfg1, ell):
+    """BiCGstab(ell) changes the route, not the answer (where it converges)."""
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[:8]
+    e_ref = cfg1.e_ref(0)[:8]
+    d, rep, _ = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, ell=ell)
+    h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
+    ref = O.solve_shifted(h, kp.psi_kq, rhs, e_ref, cfg1.omega, cfg1.eta)
+    conv = rep["status"] == 0
+    assert conv.sum() >= conv.size // 2
+    assert _relerr(d, ref)[conv].max() < TOL_SOLVE
+
+
+# ------------------------------------------------------------------- edge cases, errors
+
+def test_zero_rhs_gives_zero(sgw, cfg1):
+    kp = cfg1.kpoints[0]
+    skq, _ = _systems(sgw, cfg1)
+    rhs = np.zeros((3, skq.n_pw), complex)
+    d, rep, ok = skq.solve_shifted(rhs, np.zeros(3), cfg1.omega, cfg1.eta)
+    assert ok and not np.any(d)
+    assert np.all(rep["matvecs"] == 0)
+
+
+def test_occupied_only_rhs_is_zero_after_projection(sgw, cfg1):
+    """rhs in range(P_v): b = -P_c rhs = 0 up to rounding -> tiny solution."""
+    kp = cfg1.kpoints[0]
+    skq, _ = _systems(sgw, cfg1)
+    d, rep, ok = skq.solve_shifted(kp.psi_kq[:2].copy(), kp.eps_k[:2], cfg1.omega, cfg1.eta)
+    assert np.abs(d).max() < 1e-10
+
+
+def test_nonfinite_rhs_reported(sgw, cfg1):
+    kp = cfg1.kpoints[0]
+    skq, _ = _systems(sgw, cfg1)
+    rhs = np.ones((2, skq.n_pw), complex)
+    rhs[1, 3] = np.nan
+    d, rep, ok = skq.solve_shifted(rhs, np.zeros(2), cfg1.omega, cfg1.eta)
+    assert not ok
+    assert np.all(rep["status"][1] == sgw.PAIR_NONFINITE)
+
+
+def test_argument_errors(sgw, cfg1):
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = np.ones((1, skq.n_pw), complex)
+    with pytest.raises(sgw.SgwError) as e:
+        skq.solve_shifted(rhs, [0.0], cfg1.omega, 0.0)
+    assert e.value.status == 1
+    bad = kp.psi_kq.copy()
+    bad[1] = bad[0]
+    with pytest.raises(sgw.SgwError) as e:
+        skq.set_occupied(bad, kp.eps_kq)
+    assert e.value.status == 1
+    fresh = sgw.System.from_instance(cfg1, kp.kq_frac)
+    with pytest.raises(sgw.SgwError) as e:
+        fresh.solve_shifted(rhs, [0.0], cfg1.omega, cfg1.eta)
+    assert e.value.status == 6
+    with pytest.raises(sgw.SgwError) as e:
+        sgw.System(cfg1.a, cfg1.tau, cfg1.ecut_ry, kp.kq_frac, (12, 12, 12), np.zeros(12 ** 3))
+    assert e.value.status == 5
+    with pytest.raises(sgw.SgwError) as e:
+        sgw.System(cfg1.a, cfg1.tau, cfg1.ecut_ry, kp.kq_frac, (16, 16, 14), np.zeros(16 * 16 * 14))
+    assert e.value.status == 1
+
+
+def test_maxiter_reported(sgw, cfg1):
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[20:22]
+    d, rep, ok = skq.solve_shifted(rhs, cfg1.e_ref(0)[20:22], cfg1.omega, cfg1.eta, max_matvec=8)
+    assert not ok
+    assert np.any(rep["status"] == sgw.PAIR_MAXITER)
