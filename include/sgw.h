@@ -110,19 +110,38 @@ sgw_status sgw_set_occupied(sgw_system* sys, int n_occ, const void* psi_v, const
 sgw_status sgw_make_rhs(const sgw_system* sys_kq, const sgw_system* sys_k, int n_v, const void* psi_k,
                         int n_pert, const int* gp_miller, void* rhs, void* stream);
 
+/* Arithmetic of the FFT part of an H application (the reciprocal-space parts, the
+ * projections, the Krylov recurrences and the true residual are FP64 in every mode). */
+enum {
+    SGW_PREC_FP64 = 0,   /* FP64 FFT (the FP64 pipe) */
+    SGW_PREC_DF32 = 1    /* float-float FFT: value = hi + lo in two FP32 numbers (~48-bit
+                            significand) on the FP32 pipes */
+};
+
 /* y = H x for nvec vectors [nvec][n_pw] (host or device): kinetic + non-local in
- * reciprocal space, local through the FFT box (Sec. 2.1).  Test hook. */
-sgw_status sgw_apply_h(sgw_system* sys, int nvec, const void* x, void* y, void* stream);
+ * reciprocal space, local through the FFT box (Sec. 2.1).  precision: SGW_PREC_*.  Test hook. */
+sgw_status sgw_apply_h(sgw_system* sys, int nvec, const void* x, void* y, int precision, void* stream);
 
 /* y_i = (P_c H P_c - z_i) x_i, z complex [nvec] as (re, im) pairs (host).  Requires
  * sgw_set_occupied.  Test hook for the operator the solver iterates with. */
 sgw_status sgw_apply_shifted(sgw_system* sys, int nvec, const void* x, const double* z, void* y,
-                             void* stream);
+                             int precision, void* stream);
+
+/* Multishift methods. */
+enum {
+    SGW_METHOD_LANCZOS = 0,   /* shifted Lanczos (FOM) on the Hermitian P_c H P_c: one H application per
+                                 Krylov step, every shift's Galerkin solution from T_k - z_j (default) */
+    SGW_METHOD_BICGSTAB = 1   /* shifted BiCGstab(ell) (Frommer 2003) */
+};
 
 typedef struct {
-    int ell;          /* degree of the minimal-residual polynomial of BiCGstab(ell): 1..4 (0 -> 4) */
-    int seed_index;   /* shift that carries the Krylov space; -1 -> the largest omega */
-    int max_matvec;   /* matrix-vector budget per right-hand side and per correction solve (0 -> 40000) */
+    int method;       /* SGW_METHOD_* */
+    int precision;    /* SGW_PREC_* of the multishift pass (Lanczos only; corrections and the
+                         true residual are FP64) */
+    int ell;          /* BiCGstab(ell) degree 1..4 (0 -> 4); unused by Lanczos */
+    int seed_index;   /* BiCGstab seed shift; -1 -> the largest omega; unused by Lanczos */
+    int max_matvec;   /* H applications per right-hand side and per correction solve (0 -> 40000); the
+                         Lanczos basis is also capped by free device memory */
     int max_refine;   /* rounds of per-shift correction solves (0 -> 3, negative -> none) */
     void* stream;     /* cudaStream_t, NULL = default stream */
 } sgw_solve_opts;
@@ -136,14 +155,18 @@ typedef struct {
     double* cert;       /* error certificate |b - A x| / (eta |x|) >= |x - x*| / |x| */
     int* status;        /* SGW_PAIR_*: CONVERGED iff rel_res <= tol */
     int* launches;      /* one int: library kernels launched by this call */
+    double* kernel_ms;  /* one double: CUDA-event time of the multishift kernel launch on the stream */
 } sgw_report;
 
 /* Multishift solve (the hot path).  For every r < nrhs and j < nomega solves
  *   (P_c H P_c - z_rj) dpsi[r][j] = -P_c rhs[r],   z_rj = e_ref[r] + omega[j] + i eta.
- * 1. Multishift pass: a shifted BiCGstab(ell) (Frommer 2003, the solver the paper cites in
- *    Sec. 2.2): one seed system per right-hand side builds the Krylov space, every shift
- *    is advanced from the seed's vectors through scalar recurrences, and a shift stops
- *    updating once its residual estimate drops to tol |b|.
+ * 1. Multishift pass (Sec. 2.2: shifted systems share one Krylov space).  Default: the
+ *    Lanczos process on the Hermitian P_c H P_c with b as start vector; each shift's
+ *    Galerkin solution x_j = V_k (T_k - z_j)^{-1} |b| e_1 and its residual norm follow from
+ *    the tridiagonal T_k alone, a shift is done when its residual reaches tol |b|, and the
+ *    solutions are formed from the stored basis at the end.  Alternative: shifted
+ *    BiCGstab(ell) (Frommer 2003, the solver the paper cites), one seed system carrying
+ *    all shifts through scalar recurrences.
  * 2. True FP64 residual and certificate of every pair (as sgw_residual).
  * 3. Pairs whose true residual exceeds tol (recursive/true residual gap, budget exhausted)
  *    get per-shift correction solves A_j d = r_j, x_j += d, then step 2 again; up to

@@ -48,6 +48,7 @@ struct sgw_system {
     int* d_stick_xy = nullptr;
     int* d_xbase = nullptr;
     double* d_vloc = nullptr;
+    float2* d_vloc_dd = nullptr;
     double2* d_twid = nullptr;
     double2* d_beta = nullptr;
     double* d_dkb = nullptr;
@@ -174,6 +175,7 @@ void free_system(sgw_system* s) {
     cudaFree(s->d_stick_xy);
     cudaFree(s->d_xbase);
     cudaFree(s->d_vloc);
+    cudaFree(s->d_vloc_dd);
     cudaFree(s->d_twid);
     cudaFree(s->d_beta);
     cudaFree(s->d_dkb);
@@ -374,17 +376,29 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     }
     std::vector<int> g2s(npw);
     for (int g = 0; g < npw; ++g) g2s[g] = stick_of[s->map[g] / n3] * n3 + s->map[g] % n3;
+    const int n2p = n2 | 1;   // odd row stride: strided (x-direction) FFT lines spread over all banks
+    for (auto& xy : stick_xy) xy = (xy / n2) * n2p + xy % n2;
     std::vector<int> xbase;
     for (int x = 0; x < n1; ++x)
-        if (xs_used[x]) xbase.push_back(x * n2);
+        if (xs_used[x]) xbase.push_back(x * n2p);
     s->nstick = (int)stick_xy.size();
     s->nxcol = (int)xbase.size();
-    // potential, one contiguous plane per z: [z][x][y]
-    std::vector<double> vz(nbox);
+    // potential, one contiguous (padded) plane per z: [z][x][y < n2p]
+    const size_t nboxp = (size_t)n1 * n2p * n3;
+    std::vector<double> vz(nboxp, 0.0);
     for (int x = 0; x < n1; ++x)
         for (int y = 0; y < n2; ++y)
-            for (int z = 0; z < n3; ++z) vz[((size_t)z * n1 + x) * n2 + y] = vloc_r[((size_t)x * n2 + y) * n3 + z];
+            for (int z = 0; z < n3; ++z) vz[((size_t)z * n1 + x) * n2p + y] = vloc_r[((size_t)x * n2 + y) * n3 + z];
+    std::vector<float2> vzdd(nboxp);
+    for (size_t i = 0; i < nboxp; ++i) {
+        const float h = (float)vz[i];
+        vzdd[i] = make_float2(h, (float)(vz[i] - (double)h));
+    }
     sgw_status rs;
+    if ((rs = upload(&s->d_vloc_dd, vzdd.data(), vzdd.size(), "upload V_loc")) != SGW_OK) {
+        free_system(s);
+        return rs;
+    }
     if ((rs = upload(&s->d_g2s, g2s.data(), g2s.size(), "upload g2s")) != SGW_OK ||
         (rs = upload(&s->d_stick_xy, stick_xy.data(), stick_xy.size(), "upload sticks")) != SGW_OK ||
         (rs = upload(&s->d_xbase, xbase.data(), xbase.size(), "upload xbase")) != SGW_OK ||
@@ -451,6 +465,7 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     P.n1 = n1;
     P.n2 = n2;
     P.n3 = n3;
+    P.n2p = n2p;
     P.npw = npw;
     P.nstick = s->nstick;
     P.nxcol = s->nxcol;
@@ -458,6 +473,7 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     P.stick_xy = s->d_stick_xy;
     P.xbase = s->d_xbase;
     P.vloc = s->d_vloc;
+    P.vloc_dd = s->d_vloc_dd;
     P.kin = s->d_kin;
     P.twid = s->d_twid;
     P.nproj = nproj;
@@ -580,7 +596,7 @@ sgw_status sgw_make_rhs(const sgw_system* kq, const sgw_system* k, int n_v, cons
 }
 
 static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const double* z, void* y, void* stream,
-                               int project) {
+                               int project, int precision) {
     g_err.clear();
     if (!s || !x || !y) return fail(SGW_EINVAL, "NULL argument");
     if (nvec < 0) return fail(SGW_EINVAL, "negative nvec");
@@ -603,19 +619,22 @@ static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const dou
     double2* d_scr = (double2*)s->d_ws;
     double2* d_z = (double2*)((char*)s->d_ws + ((scratch + 255) / 256) * 256);
     if (project) SGW_CUDA(cudaMemcpyAsync(d_z, z, zb, cudaMemcpyHostToDevice, st), "z copy");
-    SGW_CUDA(launch_apply(s->plan, nvec, (const double2*)in.dev, (double2*)out.dev, d_z, project, d_scr, grid, st),
+    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32) return fail(SGW_EINVAL, "unknown precision");
+    SGW_CUDA(launch_apply(s->plan, nvec, (const double2*)in.dev, (double2*)out.dev, d_z, project, d_scr, grid,
+                          precision, st),
              "apply kernel");
     if ((r = finish_out(out, st, "y copy")) != SGW_OK) return r;
     SGW_CUDA(cudaStreamSynchronize(st), "apply");
     return SGW_OK;
 }
 
-sgw_status sgw_apply_h(sgw_system* s, int nvec, const void* x, void* y, void* stream) {
-    return apply_common(s, nvec, x, nullptr, y, stream, 0);
+sgw_status sgw_apply_h(sgw_system* s, int nvec, const void* x, void* y, int precision, void* stream) {
+    return apply_common(s, nvec, x, nullptr, y, stream, 0, precision);
 }
 
-sgw_status sgw_apply_shifted(sgw_system* s, int nvec, const void* x, const double* z, void* y, void* stream) {
-    return apply_common(s, nvec, x, z, y, stream, 1);
+sgw_status sgw_apply_shifted(sgw_system* s, int nvec, const void* x, const double* z, void* y, int precision,
+                             void* stream) {
+    return apply_common(s, nvec, x, z, y, stream, 1, precision);
 }
 
 namespace {
@@ -644,6 +663,10 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
     if (!finite_all(e_ref, nrhs) || !finite_all(omega, nomega)) return fail(SGW_EINVAL, "non-finite e_ref or omega");
     if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+    const int method = opts ? opts->method : SGW_METHOD_LANCZOS;
+    const int precision = opts ? opts->precision : SGW_PREC_FP64;
+    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32) return fail(SGW_EINVAL, "unknown precision");
+    if (method != SGW_METHOD_LANCZOS && method != SGW_METHOD_BICGSTAB) return fail(SGW_EINVAL, "unknown method");
     const int ell = opts && opts->ell ? opts->ell : 4;
     if (ell < 1 || ell > kMaxEll) return fail(SGW_EINVAL, "ell must be 1, 2, 3 or 4");
     int seed = opts ? opts->seed_index : -1;
@@ -658,24 +681,46 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     if (nrhs == 0) return SGW_OK;
     SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
-    if (solve_smem_bytes(s->plan, nomega) > max_optin_smem())
-        return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
+    const bool lanczos = method == SGW_METHOD_LANCZOS;
+    const int smem_main = lanczos ? lanczos_smem_bytes(s->plan, nomega) : solve_smem_bytes(s->plan, nomega);
+    if (smem_main > max_optin_smem()) return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     const size_t np = (size_t)nrhs * nomega;
     Staged in, out;
     sgw_status r;
     if ((r = stage_in(rhs, vb * nrhs, in, st, "rhs")) != SGW_OK) return r;
     if ((r = stage_out(dpsi, vb * np, out, "dpsi")) != SGW_OK) return r;
-    int grid = 0, grid1 = 0, grid_r = 0;
-    SGW_CUDA(solve_grid(s->plan, nomega, nrhs, &grid), "solver occupancy");
     const int chunk = (int)std::min<size_t>(np, 4096);
-    SGW_CUDA(solve_grid(s->plan, 1, chunk, &grid1), "solver occupancy");
+    int grid = 0, grid1 = 0, grid_r = 0;
+    if (lanczos) {
+        SGW_CUDA(lanczos_grid(s->plan, nomega, nrhs, &grid), "solver occupancy");
+        SGW_CUDA(lanczos_grid(s->plan, 1, chunk, &grid1), "solver occupancy");
+    } else {
+        SGW_CUDA(solve_grid(s->plan, nomega, nrhs, &grid), "solver occupancy");
+        SGW_CUDA(solve_grid(s->plan, 1, chunk, &grid1), "solver occupancy");
+    }
     SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r), "residual occupancy");
     grid_r = (int)std::min<size_t>(grid_r, np);
-    // workspace
+    // Krylov workspace of one launch (reused by the correction solves)
+    int maxk = max_mv;
+    auto solver_bytes = [&](int g, int ns, int mk) -> size_t {
+        if (lanczos)
+            return (size_t)g * ((size_t)(mk + 1) * vb + 2 * (size_t)(mk + 1) * 8 + 2 * (size_t)mk * ns * 16) + 4096;
+        return (size_t)g * (vb * (2 * ell + 3) + vb * (size_t)ns) + 4096;
+    };
+    if (lanczos) {
+        size_t free_b = 0, total_b = 0;
+        SGW_CUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+        const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+        const size_t per_k = std::max<size_t>((size_t)grid * (vb + 16 + 32 * (size_t)nomega),
+                                              (size_t)grid1 * (vb + 16 + 32));
+        const size_t cap = budget / std::max<size_t>(per_k, 1);
+        if (cap < 8) return fail(SGW_ENOMEM, "not enough device memory for a Lanczos basis");
+        maxk = (int)std::min<size_t>((size_t)max_mv, cap - 2);
+    }
+    const size_t wsb = std::max(solver_bytes(grid, nomega, maxk), solver_bytes(grid1, 1, maxk));
     Carve c;
-    const size_t o_seed = c.take(vb * (2 * ell + 3) * grid);
-    const size_t o_uw = c.take(vb * (size_t)nomega * grid);
+    const size_t o_solver = c.take(wsb);
     const size_t o_eref = c.take(sizeof(double) * nrhs);
     const size_t o_om = c.take(sizeof(double) * nomega);
     const size_t o_sig = c.take(sizeof(double) * nomega);
@@ -690,8 +735,6 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     const size_t o_rvec = c.take(vb * chunk);
     const size_t o_dbuf = c.take(vb * chunk);
     const size_t o_eref1 = c.take(sizeof(double) * chunk);
-    const size_t o_seed1 = c.take(vb * (2 * ell + 3) * grid1);
-    const size_t o_uw1 = c.take(vb * grid1);
     const size_t o_zero = c.take(sizeof(double));
     const size_t o_mv1 = c.take(sizeof(int) * chunk);
     const size_t o_est1 = c.take(sizeof(double) * chunk);
@@ -705,45 +748,93 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     SGW_CUDA(cudaMemcpyAsync(w + o_sig, sig.data(), sizeof(double) * nomega, cudaMemcpyHostToDevice, st), "sig copy");
     SGW_CUDA(cudaMemsetAsync(w + o_zero, 0, sizeof(double), st), "memset");
 
+    // One multishift launch of the selected method.  e_ref_d / omega_d give z = e_ref + omega + i eta.
+    auto run = [&](bool corr, int nr, int ns, const double2* rhs_d, const double* e_ref_d, const double* omega_d,
+                   double omega_seed, const double* sig_d, double tl, double2* x_d, int* mv_d, double* est_d,
+                   int* st_d, int g) -> cudaError_t {
+        if (lanczos) {
+            LanczosArgs L;
+            L.nrhs = nr;
+            L.nshift = ns;
+            L.maxk = maxk;
+            L.rhs = rhs_d;
+            L.e_ref = e_ref_d;
+            L.omega = omega_d;
+            L.eta = eta;
+            L.tol = tl;
+            L.x = x_d;
+            char* base = w + o_solver;
+            L.basis = (double2*)base;
+            L.ab = (double*)(base + (size_t)g * (maxk + 1) * vb);
+            L.ysc = (double2*)(base + (size_t)g * ((maxk + 1) * vb + 2 * (size_t)(maxk + 1) * 8));
+            L.counter = (int*)(w + o_cnt);
+            L.out_mv = mv_d;
+            L.out_res = est_d;
+            L.out_status = st_d;
+            return launch_lanczos(s->plan, L, g, corr ? SGW_PREC_FP64 : precision, st);
+        }
+        SolveArgs A;
+        A.nrhs = nr;
+        A.nshift = ns;
+        A.ell = ell;
+        A.max_mv = max_mv;
+        A.rhs = rhs_d;
+        A.e_ref = e_ref_d;
+        A.sig = sig_d;
+        A.omega_seed = omega_seed;
+        A.eta = eta;
+        A.tol = tl;
+        A.x = x_d;
+        A.seedw = (double2*)(w + o_solver);
+        A.uw = (double2*)(w + o_solver + (size_t)g * vb * (2 * ell + 3));
+        A.counter = (int*)(w + o_cnt);
+        A.out_mv = mv_d;
+        A.out_res = est_d;
+        A.out_status = st_d;
+        return launch_solve(s->plan, A, g, st);
+    };
+
     // 1. multishift pass
-    SolveArgs A;
-    A.nrhs = nrhs;
-    A.nshift = nomega;
-    A.ell = ell;
-    A.max_mv = max_mv;
-    A.rhs = (const double2*)in.dev;
-    A.e_ref = (const double*)(w + o_eref);
-    A.sig = (const double*)(w + o_sig);
-    A.omega_seed = omega[seed];
-    A.eta = eta;
-    A.tol = tol;
-    A.x = (double2*)out.dev;
-    A.uw = (double2*)(w + o_uw);
-    A.seedw = (double2*)(w + o_seed);
-    A.counter = (int*)(w + o_cnt);
-    A.out_mv = (int*)(w + o_mv);
-    A.out_res = (double*)(w + o_est);
-    A.out_status = (int*)(w + o_st);
-    SGW_CUDA(launch_solve(s->plan, A, grid, st), "solver kernel");
+    double2* X = (double2*)out.dev;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const bool timed = report && report->kernel_ms;
+    if (timed) {
+        SGW_CUDA(cudaEventCreate(&ev0), "event");
+        SGW_CUDA(cudaEventCreate(&ev1), "event");
+        SGW_CUDA(cudaEventRecord(ev0, st), "event");
+    }
+    SGW_CUDA(run(false, nrhs, nomega, (const double2*)in.dev, (const double*)(w + o_eref), (const double*)(w + o_om),
+                 omega[seed], (const double*)(w + o_sig), tol, X, (int*)(w + o_mv), (double*)(w + o_est),
+                 (int*)(w + o_st), grid),
+             "solver kernel");
     int launches = 1;
+    if (timed) SGW_CUDA(cudaEventRecord(ev1, st), "event");
 
     // 2. true residual of every pair
     double* d_rel = (double*)(w + o_rel);
     double* d_cert = (double*)(w + o_cert);
-    SGW_CUDA(launch_residual(s->plan, nrhs, nomega, nullptr, 0, (const double2*)in.dev, A.e_ref,
-                             (const double*)(w + o_om), eta, A.x, (double2*)(w + o_rscr), d_rel, d_cert, nullptr,
-                             grid_r, st),
+    const double* d_eref = (const double*)(w + o_eref);
+    const double* d_om = (const double*)(w + o_om);
+    SGW_CUDA(launch_residual(s->plan, nrhs, nomega, nullptr, 0, (const double2*)in.dev, d_eref, d_om, eta, X,
+                             (double2*)(w + o_rscr), d_rel, d_cert, nullptr, grid_r, st),
              "residual kernel");
     ++launches;
     std::vector<int> stv(np), mvv(np);
     std::vector<double> estv(np), relv(np), certv(np);
-    SGW_CUDA(cudaMemcpyAsync(stv.data(), A.out_status, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
-    SGW_CUDA(cudaMemcpyAsync(mvv.data(), A.out_mv, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
-    SGW_CUDA(cudaMemcpyAsync(estv.data(), A.out_res, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(stv.data(), w + o_st, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(mvv.data(), w + o_mv, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(estv.data(), w + o_est, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
     SGW_CUDA(cudaMemcpyAsync(relv.data(), d_rel, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
     SGW_CUDA(cudaStreamSynchronize(st), "solve");
+    if (timed) {
+        float ms = 0.f;
+        SGW_CUDA(cudaEventElapsedTime(&ms, ev0, ev1), "event");
+        *report->kernel_ms = ms;
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+    }
 
-    // 3. per-shift correction solves for pairs above tol
+    // 3. per-shift correction solves for pairs above tol: A_j d = r_j, x_j += d
     std::vector<int> list, mv1(chunk);
     std::vector<double> eref1(chunk);
     for (int round = 0; round < max_refine; ++round) {
@@ -764,32 +855,21 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
             SGW_CUDA(cudaMemcpyAsync(w + o_eref1, eref1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st),
                      "list copy");
             const int* d_list = (const int*)(w + o_list);
-            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, A.e_ref,
-                                     (const double*)(w + o_om), eta, A.x, (double2*)(w + o_rscr), d_rel, d_cert,
-                                     (double2*)(w + o_rvec), std::min(grid_r, nc), st),
+            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, d_eref, d_om, eta, X,
+                                     (double2*)(w + o_rscr), d_rel, d_cert, (double2*)(w + o_rvec),
+                                     std::min(grid_r, nc), st),
                      "residual kernel");
-            SolveArgs B = A;
-            B.nrhs = nc;
-            B.nshift = 1;
-            B.rhs = (const double2*)(w + o_rvec);
-            B.e_ref = (const double*)(w + o_eref1);
-            B.sig = (const double*)(w + o_zero);
-            B.omega_seed = 0.0;
-            B.tol = std::min(0.5, std::max(1e-13, 0.3 * tol / worst));
-            B.x = (double2*)(w + o_dbuf);
-            B.uw = (double2*)(w + o_uw1);
-            B.seedw = (double2*)(w + o_seed1);
-            B.out_mv = (int*)(w + o_mv1);
-            B.out_res = (double*)(w + o_est1);
-            B.out_status = (int*)(w + o_st1);
-            SGW_CUDA(launch_solve(s->plan, B, std::min(grid1, nc), st), "correction solve");
-            SGW_CUDA(launch_pair_axpy(nc, d_list, s->npw, B.x, A.x, st), "refinement update");
-            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, A.e_ref,
-                                     (const double*)(w + o_om), eta, A.x, (double2*)(w + o_rscr), d_rel, d_cert,
-                                     nullptr, std::min(grid_r, nc), st),
+            const double tl = std::min(0.5, std::max(1e-13, 0.3 * tol / worst));
+            SGW_CUDA(run(true, nc, 1, (const double2*)(w + o_rvec), (const double*)(w + o_eref1), (const double*)(w + o_zero),
+                         0.0, (const double*)(w + o_zero), tl, (double2*)(w + o_dbuf), (int*)(w + o_mv1),
+                         (double*)(w + o_est1), (int*)(w + o_st1), std::min(grid1, nc)),
+                     "correction solve");
+            SGW_CUDA(launch_pair_axpy(nc, d_list, s->npw, (const double2*)(w + o_dbuf), X, st), "refinement update");
+            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, d_eref, d_om, eta, X,
+                                     (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(grid_r, nc), st),
                      "residual kernel");
             launches += 4;
-            SGW_CUDA(cudaMemcpyAsync(mv1.data(), B.out_mv, sizeof(int) * nc, cudaMemcpyDeviceToHost, st), "report");
+            SGW_CUDA(cudaMemcpyAsync(mv1.data(), w + o_mv1, sizeof(int) * nc, cudaMemcpyDeviceToHost, st), "report");
             SGW_CUDA(cudaStreamSynchronize(st), "refinement");
             for (int i = 0; i < nc; ++i) mvv[list[c0 + i]] += mv1[i];
         }

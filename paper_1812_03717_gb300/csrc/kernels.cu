@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
     __shared__ int s_r;
     __shared__ double2 s_dot[kRedSlots];
 
-    load_twiddles(P, smem);
+    load_twiddles<ArF64>(P, smem);
     const ApplySmem L = apply_smem_layout(P);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                         for (int i = 0; i <= j; ++i) U[i][g] = csub(R[i][g], cmul(be, U[i][g]));
                 }
                 __syncthreads();
-                apply_h_block(P, smem, U[j], U[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+                apply_h_block<ArF64>(P, smem, U[j], U[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
                 block_dots(RT, 1, 0, U[j + 1], npw, red, s_dot);
                 if (tid == 0) {
                     const double2 gam = s_dot[0];
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                         for (int i = 0; i <= j; ++i) R[i][g] = csub(R[i][g], cmul(al, U[i + 1][g]));
                 }
                 __syncthreads();
-                apply_h_block(P, smem, R[j], R[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+                apply_h_block<ArF64>(P, smem, R[j], R[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
                 for (int a = tid; a < S.nact; a += nt) {
                     const int k = act[a];
                     zp[k] = zc[k];
@@ -455,13 +455,226 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
     }
 }
 
+// ----------------------------------------------------------------- shifted Lanczos (FOM)
+//
+// Multishift solve by the Hermitian Lanczos process on A = P_c H P_c (Sec. 2.2: systems
+// that differ only in the frequency share one Krylov space).  With b = beta_1 v_1,
+//   A V_k = V_k T_k + beta_{k+1} v_{k+1} e_k^T,   T_k real symmetric tridiagonal (alpha, beta),
+// the Galerkin solution of shift j is x_j = V_k y_j with (T_k - z_j) y_j = beta_1 e_1.  The
+// LDL^T pivots of the complex-symmetric T_k - z_j,
+//   eta_1 = alpha_1 - z_j,  l_i = beta_i / eta_{i-1},  eta_i = alpha_i - z_j - l_i beta_i,
+// never vanish because Im z_j = eta > 0 and T_k has a real spectrum; the forward sweep
+// u_i = -l_i u_{i-1} (u_1 = beta_1) gives the residual norm |beta_{k+1} u_k / eta_k| of every
+// shift from scalars alone, and the residuals of all shifts stay collinear with v_{k+1}.
+// The basis is kept (one slice of global memory per CTA); when every shift has converged
+// (or the basis is full) each y_j is formed by the backward sweep y_i = u_i/eta_i - l_{i+1}
+// y_{i+1} and x_j = V y_j in one pass over the basis.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_ab[2];          // alpha_k, beta_{k+1}
+    __shared__ double2 s_dot[kRedSlots];
+    __shared__ int s_r, s_nact, s_kmax, s_fail;
+    load_twiddles<Ar>(P, smem);
+    const ApplySmem L = apply_smem_layout(P);
+    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const int ns = A.nshift, npw = P.npw, tid = threadIdx.x, nt = blockDim.x, maxk = A.maxk;
+    // per-shift state after the apply's shared memory
+    int off = L.end;
+    double2* zsh = reinterpret_cast<double2*>(smem + off); off = align16(off + ns * 16);
+    double2* eta = reinterpret_cast<double2*>(smem + off); off = align16(off + ns * 16);
+    double2* zeta = reinterpret_cast<double2*>(smem + off); off = align16(off + ns * 16);
+    double* est = reinterpret_cast<double*>(smem + off); off = align16(off + ns * 8);
+    int* kc = reinterpret_cast<int*>(smem + off); off = align16(off + ns * 4);
+    int* st = reinterpret_cast<int*>(smem + off);
+
+    double2* V = A.basis + (size_t)blockIdx.x * (maxk + 1) * npw;
+    double* ab = A.ab + (size_t)blockIdx.x * 2 * (maxk + 1);     // alpha[0..maxk), beta[0..maxk]
+    double* al = ab;
+    double* be = ab + (maxk + 1);
+    double2* Ysc = A.ysc + (size_t)blockIdx.x * 2 * maxk * ns;   // [maxk][ns] y, [maxk][ns] l
+    double2* Lsc = Ysc + (size_t)maxk * ns;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_r = atomicAdd(A.counter, 1);
+        __syncthreads();
+        const int r = s_r;
+        if (r >= A.nrhs) break;
+        const double2* rhs = A.rhs + (size_t)r * npw;
+        double2* X = A.x + (size_t)r * ns * npw;
+
+        // b = -P_c rhs into V[0], beta_1 = |b|
+        block_dots(P.psi, P.nocc, npw, rhs, npw, red, coef);
+        {
+            double2 acc[1] = {cz()};
+            for (int g = tid; g < npw; g += nt) {
+                double2 h = rhs[g];
+                for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
+                const double2 b = make_double2(-h.x, -h.y);
+                V[g] = b;
+                acc[0].x += cabs2(b);
+            }
+            block_sum<1>(acc, red, s_dot);
+        }
+        const double b1 = sqrt(s_dot[0].x);
+        const bool zero = !(b1 > 0.0), bad = !isfinite(b1);
+        {
+            const double inv = (zero || bad) ? 0.0 : 1.0 / b1;
+            for (int g = tid; g < npw; g += nt) V[g] = cscal(V[g], inv);
+        }
+        for (int j = tid; j < ns; j += nt) {
+            zsh[j] = make_double2(A.e_ref[r] + A.omega[j], A.eta);
+            est[j] = 1.0;
+            kc[j] = 0;
+            st[j] = bad ? SGW_PAIR_NONFINITE : (zero ? SGW_PAIR_CONVERGED : -1);
+            if (zero) est[j] = 0.0;
+        }
+        if (tid == 0) {
+            s_nact = (zero || bad) ? 0 : ns;
+            s_fail = 0;
+            be[0] = 0.0;
+        }
+        __syncthreads();
+        int k = 0;
+        while (s_nact > 0 && k < maxk) {
+            double2* vk = V + (size_t)k * npw;
+            double2* w = V + (size_t)(k + 1) * npw;
+            apply_h_block<Ar>(P, smem, vk, w, cz(), APPLY_PROJ_OUT);
+            const double bk = be[k];
+            const double2* vkm = k > 0 ? V + (size_t)(k - 1) * npw : nullptr;
+            {
+                double2 acc[1] = {cz()};
+                for (int g = tid; g < npw; g += nt) {
+                    double2 h = w[g];
+                    if (vkm) h = make_double2(h.x - bk * vkm[g].x, h.y - bk * vkm[g].y);
+                    w[g] = h;
+                    acc[0] = cadd(acc[0], cmulc(vk[g], h));
+                }
+                block_sum<1>(acc, red, s_dot);
+            }
+            const double a = s_dot[0].x;
+            {
+                double2 acc[1] = {cz()};
+                for (int g = tid; g < npw; g += nt) {
+                    const double2 h = make_double2(w[g].x - a * vk[g].x, w[g].y - a * vk[g].y);
+                    w[g] = h;
+                    acc[0].x += cabs2(h);
+                }
+                block_sum<1>(acc, red, s_dot);
+            }
+            const double bn = sqrt(s_dot[0].x);
+            {
+                const double inv = bn > 0.0 ? 1.0 / bn : 0.0;
+                for (int g = tid; g < npw; g += nt) w[g] = cscal(w[g], inv);
+            }
+            if (tid == 0) {
+                al[k] = a;
+                be[k + 1] = bn;
+                if (!isfinite(a) || !isfinite(bn)) s_fail = SGW_PAIR_NONFINITE;
+            }
+            // per-shift pivots and residual estimates
+            for (int j = tid; j < ns; j += nt) {
+                if (st[j] >= 0) continue;
+                const double2 d = make_double2(a - zsh[j].x, -zsh[j].y);
+                double2 e, u;
+                if (k == 0) {
+                    e = d;
+                    u = make_double2(b1, 0.0);
+                } else {
+                    const double2 l = cdiv(make_double2(bk, 0.0), eta[j]);
+                    e = csub(d, cscal(l, bk));
+                    u = cmul(make_double2(-l.x, -l.y), zeta[j]);
+                }
+                eta[j] = e;
+                zeta[j] = u;
+                const double2 q = cdiv(u, e);
+                const double rr = bn * sqrt(cabs2(q)) / b1;
+                est[j] = rr;
+                kc[j] = k + 1;
+                if (!isfinite(rr)) st[j] = SGW_PAIR_NONFINITE;
+                else if (rr <= A.tol || bn == 0.0) st[j] = SGW_PAIR_CONVERGED;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int n = 0;
+                for (int j = 0; j < ns; ++j) n += st[j] < 0 ? 1 : 0;
+                s_nact = s_fail ? 0 : n;
+            }
+            ++k;
+            __syncthreads();
+            if (bn == 0.0) break;
+        }
+        // budget exhausted / failure
+        for (int j = tid; j < ns; j += nt)
+            if (st[j] < 0) st[j] = s_fail ? s_fail : SGW_PAIR_MAXITER;
+        if (tid == 0) {
+            int m = 0;
+            for (int j = 0; j < ns; ++j) m = max(m, kc[j]);
+            s_kmax = m;
+        }
+        __syncthreads();
+        const int K = s_kmax;
+        // y_j = (T_kj - z_j)^{-1} beta_1 e_1 by forward / backward sweeps (one thread per shift)
+        for (int j = tid; j < ns; j += nt) {
+            const int kj = kc[j];
+            if (kj == 0 || st[j] == SGW_PAIR_NONFINITE) {
+                for (int i = 0; i < K; ++i) Ysc[(size_t)i * ns + j] = cz();
+                continue;
+            }
+            double2 e = make_double2(al[0] - zsh[j].x, -zsh[j].y);
+            double2 u = make_double2(b1, 0.0);
+            Ysc[j] = cdiv(u, e);
+            for (int i = 1; i < kj; ++i) {
+                const double2 l = cdiv(make_double2(be[i], 0.0), e);
+                e = csub(make_double2(al[i] - zsh[j].x, -zsh[j].y), cscal(l, be[i]));
+                u = cmul(make_double2(-l.x, -l.y), u);
+                Lsc[(size_t)i * ns + j] = l;
+                Ysc[(size_t)i * ns + j] = cdiv(u, e);
+            }
+            for (int i = kj - 2; i >= 0; --i)
+                Ysc[(size_t)i * ns + j] = csub(Ysc[(size_t)i * ns + j], cmul(Lsc[(size_t)(i + 1) * ns + j],
+                                                                         Ysc[(size_t)(i + 1) * ns + j]));
+            for (int i = kj; i < K; ++i) Ysc[(size_t)i * ns + j] = cz();
+        }
+        __syncthreads();
+        // x_j = V y_j, shifts in tiles of 8
+        for (int j0 = 0; j0 < ns; j0 += 8) {
+            const int cnt = min(8, ns - j0);
+            for (int g = tid; g < npw; g += nt) {
+                double2 acc[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[t] = cz();
+                for (int i = 0; i < K; ++i) {
+                    const double2 v = V[(size_t)i * npw + g];
+                    const double2* yr = Ysc + (size_t)i * ns + j0;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if (t < cnt) acc[t] = cfma(yr[t], v, acc[t]);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t)
+                    if (t < cnt) X[(size_t)(j0 + t) * npw + g] = acc[t];
+            }
+        }
+        for (int j = tid; j < ns; j += nt) {
+            A.out_status[(size_t)r * ns + j] = st[j];
+            A.out_mv[(size_t)r * ns + j] = kc[j];
+            A.out_res[(size_t)r * ns + j] = est[j];
+        }
+        __syncthreads();
+    }
+}
+
 // y_i = H x_i, or (P_c H P_c - z_i) x_i when `project` is set.  One CTA per vector
 // (persistent over the batch); scratch holds P_c x per CTA.
+template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, const double2* __restrict__ x,
                                                             double2* __restrict__ y, const double2* __restrict__ z,
                                                             int project, double2* __restrict__ scratch) {
     extern __shared__ __align__(16) unsigned char smem[];
-    load_twiddles(P, smem);
+    load_twiddles<Ar>(P, smem);
     const ApplySmem L = apply_smem_layout(P);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
@@ -471,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, co
         const double2* xv = x + (size_t)v * npw;
         double2* yv = y + (size_t)v * npw;
         if (!project) {
-            apply_h_block(P, smem, xv, yv, cz(), 0);
+            apply_h_block<Ar>(P, smem, xv, yv, cz(), 0);
             continue;
         }
         block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
@@ -481,7 +694,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, co
             xs[g] = h;
         }
         __syncthreads();
-        apply_h_block(P, smem, xs, yv, cz(), APPLY_PROJ_OUT);
+        apply_h_block<Ar>(P, smem, xs, yv, cz(), APPLY_PROJ_OUT);
         const double2 zz = z[v];
         for (int g = tid; g < npw; g += nt) yv[g] = csub(yv[g], cmul(zz, xv[g]));
         __syncthreads();
@@ -502,7 +715,7 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs,
                                                                double* __restrict__ cert, double2* __restrict__ store) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double2 s_dot[kRedSlots];
-    load_twiddles(P, smem);
+    load_twiddles<ArF64>(P, smem);
     const ApplySmem L = apply_smem_layout(P);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
@@ -523,7 +736,7 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs,
             xs[g] = h;
         }
         __syncthreads();
-        apply_h_block(P, smem, xs, ys, cz(), APPLY_PROJ_OUT);
+        apply_h_block<ArF64>(P, smem, xs, ys, cz(), APPLY_PROJ_OUT);
         block_dots(P.psi, P.nocc, npw, rv, npw, red, coef);
         double2 acc[3] = {cz(), cz(), cz()};
         for (int g = tid; g < npw; g += nt) {
@@ -540,8 +753,13 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs,
         block_sum<3>(acc, red, s_dot);
         if (tid == 0) {
             const double rn = sqrt(s_dot[0].x), bn = sqrt(s_dot[1].x), xn = sqrt(s_dot[2].x);
-            rel[q] = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
-            cert[q] = xn > 0.0 ? rn / (eta * xn) : (rn > 0.0 ? INFINITY : 0.0);
+            if (!isfinite(rn) || !isfinite(bn) || !isfinite(xn)) {
+                rel[q] = NAN;   // a non-finite input or solution is never reported converged
+                cert[q] = NAN;
+            } else {
+                rel[q] = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
+                cert[q] = xn > 0.0 ? rn / (eta * xn) : (rn > 0.0 ? INFINITY : 0.0);
+            }
         }
         __syncthreads();
     }
@@ -602,11 +820,15 @@ cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream
 }
 
 cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
-                         double2* scratch, int grid, cudaStream_t st) {
+                         double2* scratch, int grid, int precision, cudaStream_t st) {
     const int smem = apply_smem_bytes(P);
-    cudaError_t e = cudaFuncSetAttribute((const void*)apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const void* k = precision == SGW_PREC_DF32 ? (const void*)apply_kernel<ArDF> : (const void*)apply_kernel<ArF64>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    apply_kernel<<<grid, kThreads, smem, st>>>(P, nvec, x, y, z, project, scratch);
+    if (precision == SGW_PREC_DF32)
+        apply_kernel<ArDF><<<grid, kThreads, smem, st>>>(P, nvec, x, y, z, project, scratch);
+    else
+        apply_kernel<ArF64><<<grid, kThreads, smem, st>>>(P, nvec, x, y, z, project, scratch);
     return cudaGetLastError();
 }
 
@@ -627,8 +849,40 @@ cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2*
     return cudaGetLastError();
 }
 
+int lanczos_smem_bytes(const Plan& P, int nshift) {
+    return apply_smem_bytes(P) + 3 * align16(nshift * 16) + align16(nshift * 8) + 2 * align16(nshift * 4);
+}
+
+cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int* grid) {
+    int g = 0;
+    cudaError_t e = resident_grid((const void*)lanczos_solve_kernel<ArF64>, lanczos_smem_bytes(P, nshift), &g);
+    if (e != cudaSuccess) return e;
+    int g2 = 0;
+    e = resident_grid((const void*)lanczos_solve_kernel<ArDF>, lanczos_smem_bytes(P, nshift), &g2);
+    if (e != cudaSuccess) return e;
+    g = g < g2 ? g : g2;
+    *grid = g < nrhs ? g : nrhs;
+    if (*grid < 1) *grid = 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int grid, int precision, cudaStream_t st) {
+    const int smem = lanczos_smem_bytes(P, a.nshift);
+    const bool df = precision == SGW_PREC_DF32;
+    const void* k = df ? (const void*)lanczos_solve_kernel<ArDF> : (const void*)lanczos_solve_kernel<ArF64>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (df)
+        lanczos_solve_kernel<ArDF><<<grid, kThreads, smem, st>>>(P, a);
+    else
+        lanczos_solve_kernel<ArF64><<<grid, kThreads, smem, st>>>(P, a);
+    return cudaGetLastError();
+}
+
 const void* solve_kernel_ptr() { return (const void*)ms_solve_kernel; }
-const void* apply_kernel_ptr() { return (const void*)apply_kernel; }
+const void* apply_kernel_ptr() { return (const void*)apply_kernel<ArF64>; }
 const void* residual_kernel_ptr() { return (const void*)residual_kernel; }
 
 }  // namespace sgw

@@ -54,14 +54,31 @@ struct SolveArgs {
     int* out_status;          // [nrhs][nshift]
 };
 
-// Shared memory (bytes) the solver needs beyond the H application, for nshift shifts.
-int solve_extra_smem(int nshift);
+struct LanczosArgs {
+    int nrhs, nshift, maxk;
+    const double2* rhs;       // [nrhs][npw]
+    const double* e_ref;      // [nrhs]
+    const double* omega;      // [nshift]
+    double eta, tol;
+    double2* x;               // [nrhs][nshift][npw]
+    double2* basis;           // [grid][maxk + 1][npw]
+    double* ab;               // [grid][2][maxk + 1]
+    double2* ysc;             // [grid][2][maxk][nshift]
+    int* counter;
+    int* out_mv;              // [nrhs][nshift]  Lanczos steps when the pair converged
+    double* out_res;          // [nrhs][nshift]
+    int* out_status;          // [nrhs][nshift]
+};
+
+int lanczos_smem_bytes(const Plan& P, int nshift);
+cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int* grid);
+cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int grid, int precision, cudaStream_t st);
 int solve_smem_bytes(const Plan& P, int nshift);
 int apply_smem_bytes(const Plan& P);
 cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid);
 cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
-                         double2* scratch, int grid, cudaStream_t st);
+                         double2* scratch, int grid, int precision, cudaStream_t st);
 cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int grid, cudaStream_t st);

@@ -2,9 +2,9 @@
 //
 // Data layout in device memory (all complex values are FP64 pairs, double2):
 //   plane-wave vectors      [nvec][npw]              canonical G order (Miller lexicographic)
-//   local potential         [N3][N1][N2]             one contiguous xy-plane per z
+//   local potential         [N3][N1][N2p]            one contiguous (padded) xy-plane per z
 //   stick buffer (on chip)  [nstick][N3]             z-columns of the box that hold a G
-//   plane buffer (on chip)  [N1][N2]                 one xy-plane of the box
+//   plane buffer (on chip)  [N1][N2p]                one xy-plane of the box, rows padded to odd N2p
 //   KB projectors           [nproj][npw]             <k+G|beta_p>
 //   occupied states         [nocc][npw]              psi_v of the basis (Eq. 7-8)
 //
@@ -36,11 +36,13 @@ struct AxisPlan {
 // Everything an H application needs; passed by value to kernels.
 struct Plan {
     int n1, n2, n3, npw, nstick, nxcol;
+    int n2p;                 // row stride of the on-chip xy-plane: n2 rounded up to odd (bank spread)
     AxisPlan ax[3];
     const int* g2s;          // [npw]    stick * n3 + (m3 mod n3)
-    const int* stick_xy;     // [nstick] (m1 mod n1) * n2 + (m2 mod n2)
-    const int* xbase;        // [nxcol]  x * n2 for every x that has a stick
-    const double* vloc;      // [n3][n1][n2]
+    const int* stick_xy;     // [nstick] (m1 mod n1) * n2p + (m2 mod n2): the stick's place in the plane
+    const int* xbase;        // [nxcol]  x * n2p for every x that has a stick
+    const double* vloc;      // [n3][n1][n2p] (pad entries 0)
+    const float2* vloc_dd;   // [n3][n1][n2p] the same as float-float (hi, lo)
     const double* kin;       // [npw]
     const double2* twid;     // [n1 + n2 + n3]  exp(-2 pi i m / n_axis)
     int nproj;
@@ -63,7 +65,7 @@ inline __host__ __device__ ApplySmem apply_smem_layout(const Plan& p) {
     int off = 0;
     s.tw = off;     off = align16(off + (p.n1 + p.n2 + p.n3) * 16);
     s.sticks = off; off = align16(off + p.nstick * p.n3 * 16);
-    s.plane = off;  off = align16(off + p.n1 * p.n2 * 16);
+    s.plane = off;  off = align16(off + p.n1 * p.n2p * 16);
     s.red = off;    off = align16(off + (kThreads / 32) * kRedSlots * 16);
     int nc = p.nocc > p.nproj ? p.nocc : p.nproj;
     s.coef = off;   off = align16(off + ((nc + 7) / 8 * 8 + 8) * 16);
@@ -146,49 +148,146 @@ __device__ __forceinline__ void block_dots(const double2* V, int nv, int ld,
     }
 }
 
+// ------------------------------------------------------------------ arithmetic policies
+//
+// The FFT part of an H application is written once over a policy type Ar:
+//   Ar::C      complex value held in shared memory / registers (16 bytes for both policies)
+//   ArF64      native FP64 (the FP64 pipe: ~1/64 of the FP32 rate on this GPU)
+//   ArDF       float-float ("double-FP32") numbers hi + lo on the FP32 pipes, ~48-bit
+//              significand, from Dekker's and Knuth's error-free transformations:
+//              two_sum(a, b) = (s, e) with s = fl(a + b), e = a + b - s exactly;
+//              two_prod(a, b) = (p, e) with p = fl(a b), e = fma(a, b, -p) exactly.
+
+struct ArF64 {
+    using C = double2;
+    static __device__ __forceinline__ C add(C a, C b) { return cadd(a, b); }
+    static __device__ __forceinline__ C sub(C a, C b) { return csub(a, b); }
+    static __device__ __forceinline__ C mul(C a, C b) { return cmul(a, b); }
+    static __device__ __forceinline__ C conj(C a) { return make_double2(a.x, -a.y); }
+    // a * (sign i)
+    template <int SIGN>
+    static __device__ __forceinline__ C muli(C a) { return make_double2(-SIGN * a.y, SIGN * a.x); }
+    // a * c for a real constant c given as (hi, lo) float pair and its double value
+    static __device__ __forceinline__ C scal(C a, double c, float, float) { return cscal(a, c); }
+    static __device__ __forceinline__ C from_d(double2 a) { return a; }
+    static __device__ __forceinline__ double2 to_d(C a) { return a; }
+    static __device__ __forceinline__ C zero() { return cz(); }
+    // complex times real potential sample
+    static __device__ __forceinline__ C mulv(C a, const double* v, const float2*, size_t i) { return cscal(a, v[i]); }
+};
+
+struct dd {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return dd{h, e - (h - s)};
+}
+__device__ __forceinline__ dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float h = p + e;
+    return dd{h, e - (h - p)};
+}
+__device__ __forceinline__ dd dd_from(double x) {
+    const float h = __double2float_rn(x);
+    return dd{h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double dd_to(dd a) { return (double)a.hi + (double)a.lo; }
+
+struct ArDF {
+    using C = float4;   // (re.hi, re.lo, im.hi, im.lo)
+    static __device__ __forceinline__ dd re(C a) { return dd{a.x, a.y}; }
+    static __device__ __forceinline__ dd im(C a) { return dd{a.z, a.w}; }
+    static __device__ __forceinline__ C mk(dd r, dd i) { return make_float4(r.hi, r.lo, i.hi, i.lo); }
+    static __device__ __forceinline__ C add(C a, C b) { return mk(dd_add(re(a), re(b)), dd_add(im(a), im(b))); }
+    static __device__ __forceinline__ C sub(C a, C b) {
+        return mk(dd_add(re(a), dd_neg(re(b))), dd_add(im(a), dd_neg(im(b))));
+    }
+    static __device__ __forceinline__ C mul(C a, C b) {
+        const dd r = dd_add(dd_mul(re(a), re(b)), dd_neg(dd_mul(im(a), im(b))));
+        const dd i = dd_add(dd_mul(re(a), im(b)), dd_mul(im(a), re(b)));
+        return mk(r, i);
+    }
+    static __device__ __forceinline__ C conj(C a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+    template <int SIGN>
+    static __device__ __forceinline__ C muli(C a) {
+        return SIGN > 0 ? make_float4(-a.z, -a.w, a.x, a.y) : make_float4(a.z, a.w, -a.x, -a.y);
+    }
+    static __device__ __forceinline__ C scal(C a, double, float ch, float cl) {
+        const dd c{ch, cl};
+        return mk(dd_mul(re(a), c), dd_mul(im(a), c));
+    }
+    static __device__ __forceinline__ C from_d(double2 a) { return mk(dd_from(a.x), dd_from(a.y)); }
+    static __device__ __forceinline__ double2 to_d(C a) { return make_double2(dd_to(re(a)), dd_to(im(a))); }
+    static __device__ __forceinline__ C zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    static __device__ __forceinline__ C mulv(C a, const double*, const float2* v, size_t i) {
+        const float2 t = v[i];
+        const dd c{t.x, t.y};
+        return mk(dd_mul(re(a), c), dd_mul(im(a), c));
+    }
+};
+
+// Real constants of the small DFTs as (double, float hi, float lo).
+#define SGW_CONST(name, val)                                      \
+    constexpr double name##_d = val;                              \
+    constexpr float name##_h = (float)(val);                      \
+    constexpr float name##_l = (float)((val) - (double)(float)(val));
+SGW_CONST(kS3, 0.86602540378443864676)    // sin(2 pi / 3)
+SGW_CONST(kC51, 0.30901699437494742410)   // cos(2 pi / 5)
+SGW_CONST(kC52, -0.80901699437494742410)  // cos(4 pi / 5)
+SGW_CONST(kS51, 0.95105651629515357212)   // sin(2 pi / 5)
+SGW_CONST(kS52, 0.58778525229247312917)   // sin(4 pi / 5)
+SGW_CONST(kHalf, 0.5)
+#undef SGW_CONST
+
 // -------------------------------------------------------------- shared-memory FFT lines
 
 // Small DFTs of radix 2, 3, 4, 5 with exponent sign SIGN (-1 forward, +1 inverse).
-template <int SIGN>
-__device__ __forceinline__ void dft_small(double2 (&v)[5], int R) {
+template <class Ar, int SIGN>
+__device__ __forceinline__ void dft_small(typename Ar::C (&v)[5], int R) {
+    using C = typename Ar::C;
     if (R == 4) {
-        double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        double2 t2 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
-        // d * (SIGN i)
-        double2 t3 = make_double2(-SIGN * d.y, SIGN * d.x);
-        v[0] = cadd(t0, t2);
-        v[2] = csub(t0, t2);
-        v[1] = cadd(t1, t3);
-        v[3] = csub(t1, t3);
+        const C t0 = Ar::add(v[0], v[2]), t1 = Ar::sub(v[0], v[2]);
+        const C t2 = Ar::add(v[1], v[3]);
+        const C t3 = Ar::template muli<SIGN>(Ar::sub(v[1], v[3]));
+        v[0] = Ar::add(t0, t2);
+        v[2] = Ar::sub(t0, t2);
+        v[1] = Ar::add(t1, t3);
+        v[3] = Ar::sub(t1, t3);
     } else if (R == 2) {
-        double2 a = v[0];
-        v[0] = cadd(a, v[1]);
-        v[1] = csub(a, v[1]);
+        const C a = v[0];
+        v[0] = Ar::add(a, v[1]);
+        v[1] = Ar::sub(a, v[1]);
     } else if (R == 3) {
-        const double s3 = 0.86602540378443864676;   // sin(2 pi / 3)
-        double2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
-        double2 m1 = make_double2(v[0].x - 0.5 * t1.x, v[0].y - 0.5 * t1.y);
-        double2 m2 = make_double2(-SIGN * s3 * t2.y, SIGN * s3 * t2.x);
-        v[0] = cadd(v[0], t1);
-        v[1] = cadd(m1, m2);
-        v[2] = csub(m1, m2);
+        const C t1 = Ar::add(v[1], v[2]), t2 = Ar::sub(v[1], v[2]);
+        const C m1 = Ar::sub(v[0], Ar::scal(t1, kHalf_d, kHalf_h, kHalf_l));
+        const C m2 = Ar::template muli<SIGN>(Ar::scal(t2, kS3_d, kS3_h, kS3_l));
+        v[0] = Ar::add(v[0], t1);
+        v[1] = Ar::add(m1, m2);
+        v[2] = Ar::sub(m1, m2);
     } else {  // R == 5
-        const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2pi/5), cos(4pi/5)
-        const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2pi/5), sin(4pi/5)
-        double2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-        double2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-        double2 a1 = make_double2(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
-        double2 a2 = make_double2(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
-        double2 b1 = make_double2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
-        double2 b2 = make_double2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
-        // i * SIGN * b
-        double2 ib1 = make_double2(-SIGN * b1.y, SIGN * b1.x);
-        double2 ib2 = make_double2(-SIGN * b2.y, SIGN * b2.x);
-        v[0] = make_double2(v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y);
-        v[1] = cadd(a1, ib1);
-        v[4] = csub(a1, ib1);
-        v[2] = cadd(a2, ib2);
-        v[3] = csub(a2, ib2);
+        const C t1 = Ar::add(v[1], v[4]), t2 = Ar::add(v[2], v[3]);
+        const C t3 = Ar::sub(v[1], v[4]), t4 = Ar::sub(v[2], v[3]);
+        const C a1 = Ar::add(v[0], Ar::add(Ar::scal(t1, kC51_d, kC51_h, kC51_l), Ar::scal(t2, kC52_d, kC52_h, kC52_l)));
+        const C a2 = Ar::add(v[0], Ar::add(Ar::scal(t1, kC52_d, kC52_h, kC52_l), Ar::scal(t2, kC51_d, kC51_h, kC51_l)));
+        const C b1 = Ar::add(Ar::scal(t3, kS51_d, kS51_h, kS51_l), Ar::scal(t4, kS52_d, kS52_h, kS52_l));
+        const C b2 = Ar::sub(Ar::scal(t3, kS52_d, kS52_h, kS52_l), Ar::scal(t4, kS51_d, kS51_h, kS51_l));
+        const C ib1 = Ar::template muli<SIGN>(b1);
+        const C ib2 = Ar::template muli<SIGN>(b2);
+        v[0] = Ar::add(v[0], Ar::add(t1, t2));
+        v[1] = Ar::add(a1, ib1);
+        v[4] = Ar::sub(a1, ib1);
+        v[2] = Ar::add(a2, ib2);
+        v[3] = Ar::sub(a2, ib2);
     }
 }
 
@@ -199,9 +298,10 @@ __device__ __forceinline__ void dft_small(double2 (&v)[5], int R) {
 // (j / Ns) Ns R + (j mod Ns) + k Ns.  Each stage reads all of a group of lines into
 // registers before any thread writes, so no second buffer is needed.
 // tw[m] = exp(-2 pi i m / n).  All threads of the CTA must call.
-template <int SIGN>
-__device__ void fft_lines(double2* data, int nlines, const int* __restrict__ line_base, int ls, int es,
-                          const AxisPlan& ax, const double2* tw) {
+template <class Ar, int SIGN>
+__device__ void fft_lines(typename Ar::C* data, int nlines, const int* __restrict__ line_base, int ls, int es,
+                          const AxisPlan& ax, const typename Ar::C* tw) {
+    using C = typename Ar::C;
     const int N = ax.n;
     int Ns = 1;
     for (int st = 0; st < ax.nst; ++st) {
@@ -214,7 +314,7 @@ __device__ void fft_lines(double2* data, int nlines, const int* __restrict__ lin
             const int l = l0 + t / nb;
             const int j = t % nb;
             const bool act = (t < lpg * nb) && (l < nlines);
-            double2 v[5];
+            C v[5];
             int base = 0;
             const int jm = j % Ns;
             if (act) {
@@ -225,12 +325,12 @@ __device__ void fft_lines(double2* data, int nlines, const int* __restrict__ lin
 #pragma unroll
                 for (int k = 1; k < 5; ++k) {
                     if (k < R) {
-                        double2 w = tw[jm * k * stride];
-                        if (SIGN > 0) w.y = -w.y;
-                        v[k] = cmul(v[k], w);
+                        C w = tw[jm * k * stride];
+                        if (SIGN > 0) w = Ar::conj(w);
+                        v[k] = Ar::mul(v[k], w);
                     }
                 }
-                dft_small<SIGN>(v, R);
+                dft_small<Ar, SIGN>(v, R);
             }
             __syncthreads();
             if (act) {
@@ -253,10 +353,11 @@ enum : int {
 };
 
 // Loads the twiddle tables of the plan into shared memory (call once per kernel).
+template <class Ar>
 __device__ __forceinline__ void load_twiddles(const Plan& P, unsigned char* smem) {
     const ApplySmem L = apply_smem_layout(P);
-    double2* tw = reinterpret_cast<double2*>(smem + L.tw);
-    for (int i = threadIdx.x; i < P.n1 + P.n2 + P.n3; i += blockDim.x) tw[i] = P.twid[i];
+    typename Ar::C* tw = reinterpret_cast<typename Ar::C*>(smem + L.tw);
+    for (int i = threadIdx.x; i < P.n1 + P.n2 + P.n3; i += blockDim.x) tw[i] = Ar::from_d(P.twid[i]);
     __syncthreads();
 }
 
@@ -265,54 +366,58 @@ __device__ __forceinline__ void load_twiddles(const Plan& P, unsigned char* smem
 // FFT along z on the sticks; per z-plane: scatter the plane, inverse FFT along y (only
 // the x-columns that hold sticks) and x, multiply by V(r), forward FFT along x and y,
 // gather back into the sticks; forward FFT along z; gather the sphere, scale by 1/N^3 and
-// add T_G x_G + sum_p c_p beta_p(G).
+// add T_G x_G + sum_p c_p beta_p(G).  The FFT part runs in the arithmetic of Ar; the
+// reciprocal-space parts (kinetic, projectors, P_c) in FP64.
 // x and y may have been written earlier in the same kernel, so they are read through the
 // coherent path (no __restrict__ / read-only cache).
-static __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, const double2* x,
-                                                  double2* y, double2 zsh, int mode) {
+template <class Ar>
+__device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, const double2* x, double2* y,
+                                           double2 zsh, int mode) {
+    using C = typename Ar::C;
     const ApplySmem L = apply_smem_layout(P);
-    const double2* tw = reinterpret_cast<const double2*>(smem + L.tw);
-    double2* sticks = reinterpret_cast<double2*>(smem + L.sticks);
-    double2* plane = reinterpret_cast<double2*>(smem + L.plane);
+    const C* tw = reinterpret_cast<const C*>(smem + L.tw);
+    C* sticks = reinterpret_cast<C*>(smem + L.sticks);
+    C* plane = reinterpret_cast<C*>(smem + L.plane);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3, npw = P.npw, nst = P.nstick;
-    const double2* tw1 = tw;
-    const double2* tw2 = tw + n1;
-    const double2* tw3 = tw + n1 + n2;
+    const C* tw1 = tw;
+    const C* tw2 = tw + n1;
+    const C* tw3 = tw + n1 + n2;
 
     // non-local: c_p = <beta_p|x>
     if (P.nproj > 0) block_dots(P.beta, P.nproj, npw, x, npw, red, coef);
 
     // sphere -> sticks
-    for (int i = tid; i < nst * n3; i += nt) sticks[i] = cz();
+    for (int i = tid; i < nst * n3; i += nt) sticks[i] = Ar::zero();
     __syncthreads();
-    for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = x[g];
+    for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = Ar::from_d(x[g]);
     __syncthreads();
-    fft_lines<+1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
+    fft_lines<Ar, +1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
 
+    const int n2p = P.n2p;
     for (int iz = 0; iz < n3; ++iz) {
-        for (int i = tid; i < n1 * n2; i += nt) plane[i] = cz();
+        for (int i = tid; i < n1 * n2p; i += nt) plane[i] = Ar::zero();
         __syncthreads();
         for (int s = tid; s < nst; s += nt) plane[P.stick_xy[s]] = sticks[s * n3 + iz];
         __syncthreads();
-        fft_lines<+1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);     // along y, occupied x only
-        fft_lines<+1>(plane, n2, nullptr, 1, n2, P.ax[0], tw1);          // along x, every y
-        const double* vz = P.vloc + (size_t)iz * n1 * n2;
-        for (int i = tid; i < n1 * n2; i += nt) plane[i] = cscal(plane[i], vz[i]);
+        fft_lines<Ar, +1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);     // along y, occupied x only
+        fft_lines<Ar, +1>(plane, n2, nullptr, 1, n2p, P.ax[0], tw1);         // along x, every y
+        const size_t zo = (size_t)iz * n1 * n2p;
+        for (int i = tid; i < n1 * n2p; i += nt) plane[i] = Ar::mulv(plane[i], P.vloc, P.vloc_dd, zo + i);
         __syncthreads();
-        fft_lines<-1>(plane, n2, nullptr, 1, n2, P.ax[0], tw1);
-        fft_lines<-1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);
+        fft_lines<Ar, -1>(plane, n2, nullptr, 1, n2p, P.ax[0], tw1);
+        fft_lines<Ar, -1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);
         for (int s = tid; s < nst; s += nt) sticks[s * n3 + iz] = plane[P.stick_xy[s]];
         __syncthreads();
     }
-    fft_lines<-1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
+    fft_lines<Ar, -1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
 
     // gather + kinetic + non-local
     for (int g = tid; g < npw; g += nt) {
         const double2 xv = x[g];
-        double2 h = cscal(sticks[P.g2s[g]], P.inv_nbox);
+        double2 h = cscal(Ar::to_d(sticks[P.g2s[g]]), P.inv_nbox);
         h = make_double2(fma(P.kin[g], xv.x, h.x), fma(P.kin[g], xv.y, h.y));
         for (int p = 0; p < P.nproj; ++p) h = cfma(cscal(coef[p], P.dkb[p]), P.beta[(size_t)p * npw + g], h);
         y[g] = h;

@@ -17,6 +17,9 @@ LIB_PATH = os.path.join(_PKG, "libsgw.so")
 
 SGW_OK, SGW_EINVAL, SGW_ENOMEM, SGW_ECUDA, SGW_ENOCONV, SGW_EALIAS, SGW_ESTATE, SGW_EUNSUPPORTED = range(8)
 PAIR_CONVERGED, PAIR_MAXITER, PAIR_BREAKDOWN, PAIR_NONFINITE = range(4)
+METHOD_LANCZOS, METHOD_BICGSTAB = range(2)
+PREC_FP64, PREC_DF32 = range(2)
+_PREC = {"fp64": PREC_FP64, "df32": PREC_DF32}
 STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV", "SGW_EALIAS", "SGW_ESTATE",
                 "SGW_EUNSUPPORTED"]
 
@@ -41,13 +44,14 @@ class _KB(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("ell", ctypes.c_int), ("seed_index", ctypes.c_int), ("max_matvec", ctypes.c_int),
+    _fields_ = [("method", ctypes.c_int), ("precision", ctypes.c_int), ("ell", ctypes.c_int), ("seed_index", ctypes.c_int), ("max_matvec", ctypes.c_int),
                 ("max_refine", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _Report(ctypes.Structure):
     _fields_ = [("matvecs", ctypes.c_void_p), ("est_res", ctypes.c_void_p), ("rel_res", ctypes.c_void_p),
-                ("cert", ctypes.c_void_p), ("status", ctypes.c_void_p), ("launches", ctypes.c_void_p)]
+                ("cert", ctypes.c_void_p), ("status", ctypes.c_void_p), ("launches", ctypes.c_void_p),
+                ("kernel_ms", ctypes.c_void_p)]
 
 
 _lib = None
@@ -67,8 +71,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_get_box_map.argtypes = [vp, vp]
     lib.sgw_set_occupied.argtypes = [vp, ip, vp, vp]
     lib.sgw_make_rhs.argtypes = [vp, vp, ip, vp, ip, vp, vp, vp]
-    lib.sgw_apply_h.argtypes = [vp, ip, vp, vp, vp]
-    lib.sgw_apply_shifted.argtypes = [vp, ip, vp, vp, vp, vp]
+    lib.sgw_apply_h.argtypes = [vp, ip, vp, vp, ip, vp]
+    lib.sgw_apply_shifted.argtypes = [vp, ip, vp, vp, vp, ip, vp]
     lib.sgw_solve_shifted.argtypes = [vp, ip, vp, vp, ip, vp, dp, dp, ctypes.POINTER(_Opts), vp,
                                       ctypes.POINTER(_Report)]
     lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
@@ -203,25 +207,26 @@ class System:
                                    _stream_of(psi, stream)))
         return out
 
-    def apply_h(self, x, out=None, stream=None):
+    def apply_h(self, x, out=None, precision="fp64", stream=None):
         x = _c128(x)
         nvec = x.shape[0] if x.ndim == 2 else 1
         if out is None:
             out = _like(x, x.shape)
-        _check(load().sgw_apply_h(self._h, nvec, _ptr(x), _ptr(out), _stream_of(x, stream)))
+        _check(load().sgw_apply_h(self._h, nvec, _ptr(x), _ptr(out), _PREC[precision], _stream_of(x, stream)))
         return out
 
-    def apply_shifted(self, x, z, out=None, stream=None):
+    def apply_shifted(self, x, z, out=None, precision="fp64", stream=None):
         x = _c128(x)
         nvec = x.shape[0] if x.ndim == 2 else 1
         zz = np.ascontiguousarray(np.broadcast_to(np.asarray(z, dtype=np.complex128), (nvec,)))
         if out is None:
             out = _like(x, x.shape)
-        _check(load().sgw_apply_shifted(self._h, nvec, _ptr(x), zz.ctypes.data, _ptr(out), _stream_of(x, stream)))
+        _check(load().sgw_apply_shifted(self._h, nvec, _ptr(x), zz.ctypes.data, _ptr(out), _PREC[precision],
+                                        _stream_of(x, stream)))
         return out
 
-    def solve_shifted(self, rhs, e_ref, omega, eta, tol=1e-10, ell=4, seed_index=-1, max_matvec=0, max_refine=0,
-                      out=None, stream=None, raise_on_noconv=False):
+    def solve_shifted(self, rhs, e_ref, omega, eta, tol=1e-10, method="lanczos", precision="fp64", ell=4, seed_index=-1, max_matvec=0,
+                      max_refine=0, out=None, stream=None, raise_on_noconv=False):
         """Returns (dpsi [nrhs][nomega][n_pw], report dict, converged flag)."""
         rhs = _c128(rhs)
         nrhs = rhs.shape[0]
@@ -232,9 +237,12 @@ class System:
             out = _like(rhs, (nrhs, nw, self.n_pw))
         rep = {"matvecs": np.zeros((nrhs, nw), dtype=np.int32), "est_res": np.zeros((nrhs, nw)),
                "rel_res": np.zeros((nrhs, nw)), "cert": np.zeros((nrhs, nw)),
-               "status": np.zeros((nrhs, nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32)}
-        opts = _Opts(int(ell), int(seed_index), int(max_matvec), int(max_refine), _stream_of(rhs, stream))
-        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches")))
+               "status": np.zeros((nrhs, nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
+               "kernel_ms": np.zeros(1)}
+        m = {"lanczos": METHOD_LANCZOS, "bicgstab": METHOD_BICGSTAB}[method]
+        opts = _Opts(m, _PREC[precision], int(ell), int(seed_index), int(max_matvec), int(max_refine), _stream_of(rhs, stream))
+        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
+                                                        "kernel_ms")))
         s = load().sgw_solve_shifted(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data,
                                      float(eta), float(tol), ctypes.byref(opts), _ptr(out), ctypes.byref(crep))
         _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))

@@ -176,18 +176,32 @@ def test_solve_device_buffers_and_single_shift(sgw, cfg1):
 
 
 @pytest.mark.parametrize("ell", [2, 4])
-def test_solution_independent_of_ell(sgw, cfg1, ell):
-    """BiCGstab(ell) changes the route, not the answer (where it converges)."""
+def test_bicgstab_matches_oracle_where_converged(sgw, cfg1, ell):
+    """The paper-cited shifted BiCGstab(ell): same answer as the LU where it converges."""
     kp = cfg1.kpoints[0]
     skq, sk = _systems(sgw, cfg1)
     rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[:8]
     e_ref = cfg1.e_ref(0)[:8]
-    d, rep, _ = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, ell=ell)
+    d, rep, _ = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, method="bicgstab", ell=ell)
     h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
     ref = O.solve_shifted(h, kp.psi_kq, rhs, e_ref, cfg1.omega, cfg1.eta)
     conv = rep["status"] == 0
     assert conv.sum() >= conv.size // 2
     assert _relerr(d, ref)[conv].max() < TOL_SOLVE
+
+
+def test_lanczos_and_bicgstab_agree(sgw, cfg1):
+    """Two Krylov routes through the same Krylov space, one answer."""
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[:6]
+    e_ref = cfg1.e_ref(0)[:6]
+    d1, r1, ok1 = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, method="lanczos")
+    d2, r2, ok2 = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, method="bicgstab")
+    assert ok1 and ok2
+    assert _relerr(d1, d2).max() < 2 * TOL_SOLVE
+    # the Lanczos seed needs no more matrix-vector products than BiCGstab(4)
+    assert r1["matvecs"].max(axis=1).sum() <= r2["matvecs"].max(axis=1).sum()
 
 
 # ------------------------------------------------------------------- edge cases, errors
@@ -250,3 +264,50 @@ def test_maxiter_reported(sgw, cfg1):
     d, rep, ok = skq.solve_shifted(rhs, cfg1.e_ref(0)[20:22], cfg1.omega, cfg1.eta, max_matvec=8)
     assert not ok
     assert np.any(rep["status"] == sgw.PAIR_MAXITER)
+
+
+# ------------------------------------------------------- float-float (FP32-pipe) FFT mode
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_apply_h_df32_matches_dense(sgw, which, request):
+    """The float-float FFT (~48-bit significand on the FP32 pipes) keeps the H application at
+    FP64-level accuracy: relative error below 1e-11 against the oracle's dense FP64 H."""
+    inst = request.getfixturevalue(which)
+    kp = inst.kpoints[0]
+    h, mil, _ = O.dense_h_inst(inst, kp.kq_frac)
+    s = sgw.System.from_instance(inst, kp.kq_frac)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((5, len(mil))) + 1j * rng.standard_normal((5, len(mil)))
+    y = s.apply_h(x, precision="df32")
+    assert _relerr(y, x @ h.T).max() < 1e-11
+
+
+def test_solve_df32_config1_all_pairs(sgw, cfg1):
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)
+    e_ref = cfg1.e_ref(0)
+    dpsi, rep, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, tol=1e-10, precision="df32")
+    h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
+    ref = O.solve_shifted(h, kp.psi_kq, rhs, e_ref, cfg1.omega, cfg1.eta)
+    assert ok
+    assert rep["rel_res"].max() <= 1e-10
+    assert _relerr(dpsi, ref).max() < TOL_SOLVE
+
+
+def test_solve_df32_config2_sampled(sgw, cfg2):
+    """Config-2 size in the float-float mode: 64 right-hand sides (4 bands x 16 G_p) x 64
+    omega; FP64 true residual of every pair <= 1e-10; LU comparison on sampled pairs."""
+    kp = cfg2.kpoints[0]
+    skq, sk = _systems(sgw, cfg2)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg2.gp_miller)
+    npert = cfg2.n_pert
+    rows = np.concatenate([np.arange(v * npert, v * npert + 16) for v in (0, 5, 10, 15)])
+    e_ref = cfg2.e_ref(0)[rows]
+    dpsi, rep, ok = skq.solve_shifted(rhs[rows], e_ref, cfg2.omega, cfg2.eta, tol=1e-10, precision="df32")
+    assert ok
+    assert rep["rel_res"].max() <= 1e-10
+    h, _, _ = O.dense_h_inst(cfg2, kp.kq_frac)
+    for j in (0, 40, 63):
+        ref = O.solve_shifted(h, kp.psi_kq, rhs[rows[:16]], e_ref[:16], cfg2.omega[j:j + 1], cfg2.eta)[:, 0]
+        assert _relerr(dpsi[:16, j], ref).max() < TOL_SOLVE
