@@ -190,6 +190,26 @@ sgw_status sgw_residual(sgw_system* sys, int nrhs, const void* rhs, const double
                         const double* omega, double eta, const void* dpsi, double* rel_res,
                         double* cert, void* stream);
 
+/* Allocation-free variant of sgw_residual (the paper has no counterpart: this serves
+ * callers that cannot let a library allocate device memory, e.g. a framework whose caching
+ * allocator or fixed arena owns all device memory, or a code path that must not pay the
+ * device-wide synchronisation cudaFree can imply).  Same results as sgw_residual, but:
+ *   - every array argument (rhs, e_ref, omega, dpsi, rel_res, cert) must be a device pointer
+ *     of the system's device (else SGW_EINVAL); rel_res and cert are written on the device;
+ *   - it calls no cudaMalloc / cudaFree: its scratch (2 * n_pw complex values per CTA) is a
+ *     built-in device array of SGW_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the
+ *     library until the process exits; n_pw > SGW_NOALLOC_SCRATCH_BYTES / 32 gives
+ *     SGW_EUNSUPPORTED;
+ *   - the first call on a device looks up that array's device address, so make the first
+ *     call on each device before any stream capture;
+ *   - all calls share the array: calls that overlap on the GPU (other streams, other host
+ *     threads) race and must be serialised by the caller;
+ *   - it is asynchronous on `stream`: results are ready when the stream is. */
+#define SGW_NOALLOC_SCRATCH_BYTES ((size_t)4 << 20)
+sgw_status sgw_residual_noalloc(sgw_system* sys, int nrhs, const void* rhs, const double* e_ref, int nomega,
+                                const double* omega, double eta, const void* dpsi, double* rel_res,
+                                double* cert, void* stream);
+
 void sgw_destroy_system(sgw_system* sys);
 
 /* Message of the last failing call on this host thread ("" if none). */

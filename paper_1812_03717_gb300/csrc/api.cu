@@ -204,6 +204,20 @@ int max_optin_smem() {
 
 }  // namespace
 
+namespace sgw {
+
+sgw_status noalloc_fail(sgw_status s, const char* msg) { return fail(s, msg); }
+
+sgw_status noalloc_plan(const sgw_system* sys, const Plan** plan, int* dev) {
+    g_err.clear();
+    if (!sys) return fail(SGW_EINVAL, "NULL system");
+    *plan = &sys->plan;
+    *dev = sys->dev;
+    return SGW_OK;
+}
+
+}  // namespace sgw
+
 extern "C" {
 
 const char* sgw_last_error(void) { return g_err.c_str(); }

@@ -24,8 +24,8 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
                 "SGW_EUNSUPPORTED"]
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
-           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_residual", "sgw_destroy_system",
-           "sgw_last_error"]
+           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_residual", "sgw_residual_noalloc",
+           "sgw_destroy_system", "sgw_last_error"]
 
 
 class SgwError(RuntimeError):
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_solve_shifted.argtypes = [vp, ip, vp, vp, ip, vp, dp, dp, ctypes.POINTER(_Opts), vp,
                                       ctypes.POINTER(_Report)]
     lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
+    lib.sgw_residual_noalloc.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_destroy_system.argtypes = [vp]
     lib.sgw_destroy_system.restype = None
     lib.sgw_last_error.restype = ctypes.c_char_p
@@ -259,3 +260,14 @@ class System:
         _check(load().sgw_residual(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data, float(eta),
                                    _ptr(dpsi), rel.ctypes.data, cert.ctypes.data, _stream_of(rhs, stream)))
         return rel, cert
+
+    def residual_noalloc(self, rhs, e_ref, omega, eta, dpsi, rel_res, cert, stream=None):
+        """sgw_residual_noalloc: every argument a CUDA tensor (float64 e_ref / omega / rel_res /
+        cert, complex128 rhs / dpsi); writes rel_res and cert on the device; allocates nothing."""
+        for t in (rhs, e_ref, omega, dpsi, rel_res, cert):
+            if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+                raise ValueError("residual_noalloc takes contiguous CUDA tensors only")
+        nrhs, nw = rhs.shape[0], omega.shape[0]
+        _check(load().sgw_residual_noalloc(self._h, nrhs, rhs.data_ptr(), e_ref.data_ptr(), nw, omega.data_ptr(),
+                                           float(eta), dpsi.data_ptr(), rel_res.data_ptr(), cert.data_ptr(),
+                                           _stream_of(rhs, stream)))
