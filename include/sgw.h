@@ -143,6 +143,7 @@ typedef struct {
     int max_matvec;   /* H applications per right-hand side and per correction solve (0 -> 40000); the
                          Lanczos basis is also capped by free device memory */
     int max_refine;   /* rounds of per-shift correction solves (0 -> 3, negative -> none) */
+    int threads;      /* CTA size of the Lanczos kernel: 256, 384 or 512 (0 -> 256) */
     void* stream;     /* cudaStream_t, NULL = default stream */
 } sgw_solve_opts;
 

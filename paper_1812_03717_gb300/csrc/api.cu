@@ -388,8 +388,9 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
         kv.second = (int)stick_xy.size();
         stick_xy.push_back(kv.first);
     }
+    const int n3p = n3 | 1;   // odd stick stride
     std::vector<int> g2s(npw);
-    for (int g = 0; g < npw; ++g) g2s[g] = stick_of[s->map[g] / n3] * n3 + s->map[g] % n3;
+    for (int g = 0; g < npw; ++g) g2s[g] = stick_of[s->map[g] / n3] * n3p + s->map[g] % n3;
     const int n2p = n2 | 1;   // odd row stride: strided (x-direction) FFT lines spread over all banks
     for (auto& xy : stick_xy) xy = (xy / n2) * n2p + xy % n2;
     std::vector<int> xbase;
@@ -480,6 +481,8 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     P.n2 = n2;
     P.n3 = n3;
     P.n2p = n2p;
+    P.n3p = n3p;
+    P.nplanes = 1;
     P.npw = npw;
     P.nstick = s->nstick;
     P.nxcol = s->nxcol;
@@ -679,6 +682,7 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
     const int method = opts ? opts->method : SGW_METHOD_LANCZOS;
     const int precision = opts ? opts->precision : SGW_PREC_FP64;
+    const int threads = opts ? opts->threads : 0;
     if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32) return fail(SGW_EINVAL, "unknown precision");
     if (method != SGW_METHOD_LANCZOS && method != SGW_METHOD_BICGSTAB) return fail(SGW_EINVAL, "unknown method");
     const int ell = opts && opts->ell ? opts->ell : 4;
@@ -707,8 +711,8 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     const int chunk = (int)std::min<size_t>(np, 4096);
     int grid = 0, grid1 = 0, grid_r = 0;
     if (lanczos) {
-        SGW_CUDA(lanczos_grid(s->plan, nomega, nrhs, &grid), "solver occupancy");
-        SGW_CUDA(lanczos_grid(s->plan, 1, chunk, &grid1), "solver occupancy");
+        SGW_CUDA(lanczos_grid(s->plan, nomega, nrhs, threads, &grid), "solver occupancy");
+        SGW_CUDA(lanczos_grid(s->plan, 1, chunk, threads, &grid1), "solver occupancy");
     } else {
         SGW_CUDA(solve_grid(s->plan, nomega, nrhs, &grid), "solver occupancy");
         SGW_CUDA(solve_grid(s->plan, 1, chunk, &grid1), "solver occupancy");
@@ -785,7 +789,7 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
             L.out_mv = mv_d;
             L.out_res = est_d;
             L.out_status = st_d;
-            return launch_lanczos(s->plan, L, g, corr ? SGW_PREC_FP64 : precision, st);
+            return launch_lanczos(s->plan, L, g, corr ? SGW_PREC_FP64 : precision, threads, st);
         }
         SolveArgs A;
         A.nrhs = nr;

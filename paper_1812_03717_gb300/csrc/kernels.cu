@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
 // The basis is kept (one slice of global memory per CTA); when every shift has converged
 // (or the basis is full) each y_j is formed by the backward sweep y_i = u_i/eta_i - l_{i+1}
 // y_{i+1} and x_j = V y_j in one pass over the basis.
-template <class Ar>
-__global__ void __launch_bounds__(kThreads, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {
+template <class Ar, int NT>
+__global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_ab[2];          // alpha_k, beta_{k+1}
     __shared__ double2 s_dot[kRedSlots];
@@ -778,14 +778,37 @@ __global__ void pair_axpy_kernel(int nlist, const int* __restrict__ list, int np
 
 // ------------------------------------------------------------------------ host launchers
 
-int apply_smem_bytes(const Plan& P) { return apply_smem_layout(P).end; }
+namespace {
+int optin_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+int bicg_extra(int ns) { return shift_layout(0, ns).end; }
+int lanczos_extra(int ns) { return 3 * align16(ns * 16) + align16(ns * 8) + 2 * align16(ns * 4); }
+}  // namespace
 
-int solve_smem_bytes(const Plan& P, int nshift) {
-    const ApplySmem L = apply_smem_layout(P);
-    return shift_layout(L.end, nshift).end;
+// The plan with as many xy-planes per pass (4, 2 or 1) as fit next to `extra` bytes of
+// kernel-specific shared memory.
+Plan tuned_plan(const Plan& P, int extra) {
+    Plan Q = P;
+    const int cap = optin_smem() - 1024;   // static shared memory of the kernels
+    for (int np : {4, 2, 1}) {
+        Q.nplanes = np;
+        if (apply_smem_layout(Q).end + extra <= cap) return Q;
+    }
+    Q.nplanes = 1;
+    return Q;
 }
 
-cudaError_t resident_grid(const void* kernel, int smem, int* grid) {
+int apply_smem_bytes(const Plan& P) { return apply_smem_layout(tuned_plan(P, 0)).end; }
+
+int solve_smem_bytes(const Plan& P, int nshift) {
+    return apply_smem_layout(tuned_plan(P, bicg_extra(nshift))).end + bicg_extra(nshift);
+}
+
+cudaError_t resident_grid(const void* kernel, int smem, int* grid, int threads) {
     int dev = 0, nsm = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -793,7 +816,7 @@ cudaError_t resident_grid(const void* kernel, int smem, int* grid) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
     if (e != cudaSuccess) return e;
     if (per < 1) return cudaErrorInvalidConfiguration;
     *grid = nsm * per;
@@ -802,15 +825,16 @@ cudaError_t resident_grid(const void* kernel, int smem, int* grid) {
 
 cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid) {
     int g = 0;
-    cudaError_t e = resident_grid((const void*)ms_solve_kernel, solve_smem_bytes(P, nshift), &g);
+    cudaError_t e = resident_grid((const void*)ms_solve_kernel, solve_smem_bytes(P, nshift), &g, kThreads);
     if (e != cudaSuccess) return e;
     *grid = g < nrhs ? g : nrhs;
     if (*grid < 1) *grid = 1;
     return cudaSuccess;
 }
 
-cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream_t st) {
-    const int smem = solve_smem_bytes(P, a.nshift);
+cudaError_t launch_solve(const Plan& P0, const SolveArgs& a, int grid, cudaStream_t st) {
+    const Plan P = tuned_plan(P0, bicg_extra(a.nshift));
+    const int smem = solve_smem_bytes(P0, a.nshift);
     cudaError_t e = cudaFuncSetAttribute((const void*)ms_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
@@ -819,9 +843,10 @@ cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
+cudaError_t launch_apply(const Plan& P0, int nvec, const double2* x, double2* y, const double2* z, int project,
                          double2* scratch, int grid, int precision, cudaStream_t st) {
-    const int smem = apply_smem_bytes(P);
+    const Plan P = tuned_plan(P0, 0);
+    const int smem = apply_smem_bytes(P0);
     const void* k = precision == SGW_PREC_DF32 ? (const void*)apply_kernel<ArDF> : (const void*)apply_kernel<ArF64>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
@@ -832,10 +857,11 @@ cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
+cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int grid, cudaStream_t st) {
-    const int smem = apply_smem_bytes(P);
+    const Plan P = tuned_plan(P0, 0);
+    const int smem = apply_smem_bytes(P0);
     cudaError_t e = cudaFuncSetAttribute((const void*)residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     residual_kernel<<<grid, kThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
@@ -850,15 +876,25 @@ cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2*
 }
 
 int lanczos_smem_bytes(const Plan& P, int nshift) {
-    return apply_smem_bytes(P) + 3 * align16(nshift * 16) + align16(nshift * 8) + 2 * align16(nshift * 4);
+    return apply_smem_layout(tuned_plan(P, lanczos_extra(nshift))).end + lanczos_extra(nshift);
 }
 
-cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int* grid) {
-    int g = 0;
-    cudaError_t e = resident_grid((const void*)lanczos_solve_kernel<ArF64>, lanczos_smem_bytes(P, nshift), &g);
+namespace {
+template <class Ar>
+const void* lanczos_ptr(int nt) {
+    if (nt == 512) return (const void*)lanczos_solve_kernel<Ar, 512>;
+    if (nt == 384) return (const void*)lanczos_solve_kernel<Ar, 384>;
+    return (const void*)lanczos_solve_kernel<Ar, 256>;
+}
+int lanczos_threads(int requested) { return requested == 384 || requested == 512 ? requested : 256; }
+}  // namespace
+
+cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int threads, int* grid) {
+    const int nt = lanczos_threads(threads);
+    int g = 0, g2 = 0;
+    cudaError_t e = resident_grid(lanczos_ptr<ArF64>(nt), lanczos_smem_bytes(P, nshift), &g, nt);
     if (e != cudaSuccess) return e;
-    int g2 = 0;
-    e = resident_grid((const void*)lanczos_solve_kernel<ArDF>, lanczos_smem_bytes(P, nshift), &g2);
+    e = resident_grid(lanczos_ptr<ArDF>(nt), lanczos_smem_bytes(P, nshift), &g2, nt);
     if (e != cudaSuccess) return e;
     g = g < g2 ? g : g2;
     *grid = g < nrhs ? g : nrhs;
@@ -866,19 +902,19 @@ cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int* grid) {
     return cudaSuccess;
 }
 
-cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int grid, int precision, cudaStream_t st) {
-    const int smem = lanczos_smem_bytes(P, a.nshift);
+cudaError_t launch_lanczos(const Plan& P0, const LanczosArgs& a, int grid, int precision, int threads,
+                           cudaStream_t st) {
+    const Plan P = tuned_plan(P0, lanczos_extra(a.nshift));
+    const int smem = lanczos_smem_bytes(P0, a.nshift);
     const bool df = precision == SGW_PREC_DF32;
-    const void* k = df ? (const void*)lanczos_solve_kernel<ArDF> : (const void*)lanczos_solve_kernel<ArF64>;
+    const int nt = lanczos_threads(threads);
+    const void* k = df ? lanczos_ptr<ArDF>(nt) : lanczos_ptr<ArF64>(nt);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    if (df)
-        lanczos_solve_kernel<ArDF><<<grid, kThreads, smem, st>>>(P, a);
-    else
-        lanczos_solve_kernel<ArF64><<<grid, kThreads, smem, st>>>(P, a);
-    return cudaGetLastError();
+    void* args[] = {(void*)&P, (void*)&a};
+    return cudaLaunchKernel(k, dim3(grid), dim3(nt), args, smem, st);
 }
 
 const void* solve_kernel_ptr() { return (const void*)ms_solve_kernel; }

@@ -71,8 +71,9 @@ struct LanczosArgs {
 };
 
 int lanczos_smem_bytes(const Plan& P, int nshift);
-cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int* grid);
-cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int grid, int precision, cudaStream_t st);
+cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int threads, int* grid);
+cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int grid, int precision, int threads,
+                           cudaStream_t st);
 int solve_smem_bytes(const Plan& P, int nshift);
 int apply_smem_bytes(const Plan& P);
 cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid);
@@ -83,6 +84,6 @@ cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int grid, cudaStream_t st);
 cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st);
-cudaError_t resident_grid(const void* kernel, int smem, int* grid);
+cudaError_t resident_grid(const void* kernel, int smem, int* grid, int threads = kThreads);
 
 }  // namespace sgw

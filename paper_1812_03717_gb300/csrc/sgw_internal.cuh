@@ -3,8 +3,8 @@
 // Data layout in device memory (all complex values are FP64 pairs, double2):
 //   plane-wave vectors      [nvec][npw]              canonical G order (Miller lexicographic)
 //   local potential         [N3][N1][N2p]            one contiguous (padded) xy-plane per z
-//   stick buffer (on chip)  [nstick][N3]             z-columns of the box that hold a G
-//   plane buffer (on chip)  [N1][N2p]                one xy-plane of the box, rows padded to odd N2p
+//   stick buffer (on chip)  [nstick][N3p]            z-columns of the box that hold a G (N3p odd)
+//   plane buffer (on chip)  [nplanes][N1][N2p]       a few xy-planes of the box, rows padded to odd N2p
 //   KB projectors           [nproj][npw]             <k+G|beta_p>
 //   occupied states         [nocc][npw]              psi_v of the basis (Eq. 7-8)
 //
@@ -21,7 +21,8 @@
 
 namespace sgw {
 
-constexpr int kThreads = 256;          // threads per CTA of every library kernel
+constexpr int kThreads = 256;          // threads per CTA of the library kernels
+constexpr int kMaxThreads = 512;       // largest CTA any kernel launches (sizes the reduction scratch)
 constexpr int kMaxStages = 12;         // radix stages per axis (N <= 5^12)
 constexpr int kMaxShifts = 512;        // frequencies per solve
 constexpr int kMaxEll = 4;             // BiCGstab(ell)
@@ -37,8 +38,10 @@ struct AxisPlan {
 struct Plan {
     int n1, n2, n3, npw, nstick, nxcol;
     int n2p;                 // row stride of the on-chip xy-plane: n2 rounded up to odd (bank spread)
+    int n3p;                 // stride of the on-chip sticks: n3 rounded up to odd
+    int nplanes;             // xy-planes transformed together per barrier (chosen per launch)
     AxisPlan ax[3];
-    const int* g2s;          // [npw]    stick * n3 + (m3 mod n3)
+    const int* g2s;          // [npw]    stick * n3p + (m3 mod n3)
     const int* stick_xy;     // [nstick] (m1 mod n1) * n2p + (m2 mod n2): the stick's place in the plane
     const int* xbase;        // [nxcol]  x * n2p for every x that has a stick
     const double* vloc;      // [n3][n1][n2p] (pad entries 0)
@@ -64,9 +67,9 @@ inline __host__ __device__ ApplySmem apply_smem_layout(const Plan& p) {
     ApplySmem s;
     int off = 0;
     s.tw = off;     off = align16(off + (p.n1 + p.n2 + p.n3) * 16);
-    s.sticks = off; off = align16(off + p.nstick * p.n3 * 16);
-    s.plane = off;  off = align16(off + p.n1 * p.n2p * 16);
-    s.red = off;    off = align16(off + (kThreads / 32) * kRedSlots * 16);
+    s.sticks = off; off = align16(off + p.nstick * p.n3p * 16);
+    s.plane = off;  off = align16(off + p.nplanes * p.n1 * p.n2p * 16);
+    s.red = off;    off = align16(off + (kMaxThreads / 32) * kRedSlots * 16);
     int nc = p.nocc > p.nproj ? p.nocc : p.nproj;
     s.coef = off;   off = align16(off + ((nc + 7) / 8 * 8 + 8) * 16);
     s.end = off;
@@ -291,16 +294,17 @@ __device__ __forceinline__ void dft_small(typename Ar::C (&v)[5], int R) {
     }
 }
 
-// In-place batched FFT of `nlines` lines of length ax.n held in shared memory.  Line l
-// starts at base(l) = line_base ? line_base[l] : l * ls, element i at base + i * es.
+// In-place batched FFT of `nlines` lines of length ax.n held in shared memory, `lpp` lines
+// per plane, planes `pstride` elements apart.  Line l = p * lpp + q starts at
+// base(l) = p * pstride + (line_base ? line_base[q] : q * ls), element i at base + i * es.
 // Stockham autosort, decimation in time: stage with radix R and span Ns reads
 // x[j + k N/R], twiddles by w^(k (j mod Ns) N/(Ns R)), and writes the R outputs to
 // (j / Ns) Ns R + (j mod Ns) + k Ns.  Each stage reads all of a group of lines into
 // registers before any thread writes, so no second buffer is needed.
 // tw[m] = exp(-2 pi i m / n).  All threads of the CTA must call.
 template <class Ar, int SIGN>
-__device__ void fft_lines(typename Ar::C* data, int nlines, const int* __restrict__ line_base, int ls, int es,
-                          const AxisPlan& ax, const typename Ar::C* tw) {
+__device__ void fft_lines(typename Ar::C* data, int nlines, int lpp, int pstride, const int* __restrict__ line_base,
+                          int ls, int es, const AxisPlan& ax, const typename Ar::C* tw) {
     using C = typename Ar::C;
     const int N = ax.n;
     int Ns = 1;
@@ -318,7 +322,8 @@ __device__ void fft_lines(typename Ar::C* data, int nlines, const int* __restric
             int base = 0;
             const int jm = j % Ns;
             if (act) {
-                base = line_base ? line_base[l] : l * ls;
+                const int pl = l / lpp, q = l - pl * lpp;
+                base = pl * pstride + (line_base ? line_base[q] : q * ls);
 #pragma unroll
                 for (int k = 0; k < 5; ++k)
                     if (k < R) v[k] = data[base + (j + k * nb) * es];
@@ -390,29 +395,38 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
     if (P.nproj > 0) block_dots(P.beta, P.nproj, npw, x, npw, red, coef);
 
     // sphere -> sticks
-    for (int i = tid; i < nst * n3; i += nt) sticks[i] = Ar::zero();
+    const int n3p = P.n3p;
+    for (int i = tid; i < nst * n3p; i += nt) sticks[i] = Ar::zero();
     __syncthreads();
     for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = Ar::from_d(x[g]);
     __syncthreads();
-    fft_lines<Ar, +1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
+    fft_lines<Ar, +1>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
 
-    const int n2p = P.n2p;
-    for (int iz = 0; iz < n3; ++iz) {
-        for (int i = tid; i < n1 * n2p; i += nt) plane[i] = Ar::zero();
+    // nplanes xy-planes per pass: one set of barriers serves all of them
+    const int n2p = P.n2p, psz = n1 * n2p;
+    for (int iz0 = 0; iz0 < n3; iz0 += P.nplanes) {
+        const int npl = min(P.nplanes, n3 - iz0);
+        for (int i = tid; i < npl * psz; i += nt) plane[i] = Ar::zero();
         __syncthreads();
-        for (int s = tid; s < nst; s += nt) plane[P.stick_xy[s]] = sticks[s * n3 + iz];
+        for (int i = tid; i < npl * nst; i += nt) {
+            const int pl = i / nst, s = i - pl * nst;
+            plane[pl * psz + P.stick_xy[s]] = sticks[s * n3p + iz0 + pl];
+        }
         __syncthreads();
-        fft_lines<Ar, +1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);     // along y, occupied x only
-        fft_lines<Ar, +1>(plane, n2, nullptr, 1, n2p, P.ax[0], tw1);         // along x, every y
-        const size_t zo = (size_t)iz * n1 * n2p;
-        for (int i = tid; i < n1 * n2p; i += nt) plane[i] = Ar::mulv(plane[i], P.vloc, P.vloc_dd, zo + i);
+        fft_lines<Ar, +1>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);  // y, occupied x only
+        fft_lines<Ar, +1>(plane, npl * n2, n2, psz, nullptr, 1, n2p, P.ax[0], tw1);          // x, every y
+        const size_t zo = (size_t)iz0 * psz;
+        for (int i = tid; i < npl * psz; i += nt) plane[i] = Ar::mulv(plane[i], P.vloc, P.vloc_dd, zo + i);
         __syncthreads();
-        fft_lines<Ar, -1>(plane, n2, nullptr, 1, n2p, P.ax[0], tw1);
-        fft_lines<Ar, -1>(plane, P.nxcol, P.xbase, 0, 1, P.ax[1], tw2);
-        for (int s = tid; s < nst; s += nt) sticks[s * n3 + iz] = plane[P.stick_xy[s]];
+        fft_lines<Ar, -1>(plane, npl * n2, n2, psz, nullptr, 1, n2p, P.ax[0], tw1);
+        fft_lines<Ar, -1>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);
+        for (int i = tid; i < npl * nst; i += nt) {
+            const int pl = i / nst, s = i - pl * nst;
+            sticks[s * n3p + iz0 + pl] = plane[pl * psz + P.stick_xy[s]];
+        }
         __syncthreads();
     }
-    fft_lines<Ar, -1>(sticks, nst, nullptr, n3, 1, P.ax[2], tw3);
+    fft_lines<Ar, -1>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
 
     // gather + kinetic + non-local
     for (int g = tid; g < npw; g += nt) {

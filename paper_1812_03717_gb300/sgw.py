@@ -45,7 +45,7 @@ class _KB(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("precision", ctypes.c_int), ("ell", ctypes.c_int), ("seed_index", ctypes.c_int), ("max_matvec", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("max_refine", ctypes.c_int), ("threads", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _Report(ctypes.Structure):
@@ -227,7 +227,7 @@ class System:
         return out
 
     def solve_shifted(self, rhs, e_ref, omega, eta, tol=1e-10, method="lanczos", precision="fp64", ell=4, seed_index=-1, max_matvec=0,
-                      max_refine=0, out=None, stream=None, raise_on_noconv=False):
+                      max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False):
         """Returns (dpsi [nrhs][nomega][n_pw], report dict, converged flag)."""
         rhs = _c128(rhs)
         nrhs = rhs.shape[0]
@@ -241,7 +241,8 @@ class System:
                "status": np.zeros((nrhs, nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
                "kernel_ms": np.zeros(1)}
         m = {"lanczos": METHOD_LANCZOS, "bicgstab": METHOD_BICGSTAB}[method]
-        opts = _Opts(m, _PREC[precision], int(ell), int(seed_index), int(max_matvec), int(max_refine), _stream_of(rhs, stream))
+        opts = _Opts(m, _PREC[precision], int(ell), int(seed_index), int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(rhs, stream))
         crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
                                                         "kernel_ms")))
         s = load().sgw_solve_shifted(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data,

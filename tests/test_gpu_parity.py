@@ -311,3 +311,18 @@ def test_solve_df32_config2_sampled(sgw, cfg2):
     for j in (0, 40, 63):
         ref = O.solve_shifted(h, kp.psi_kq, rhs[rows[:16]], e_ref[:16], cfg2.omega[j:j + 1], cfg2.eta)[:, 0]
         assert _relerr(dpsi[:16, j], ref).max() < TOL_SOLVE
+
+
+@pytest.mark.parametrize("threads", [384, 512])
+@pytest.mark.parametrize("precision", ["fp64", "df32"])
+def test_solve_cta_size_variants(sgw, cfg1, threads, precision):
+    """The Lanczos kernel's CTA size is a tuning choice: same answers at every size."""
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[:12]
+    e_ref = cfg1.e_ref(0)[:12]
+    d0, _, ok0 = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, precision=precision)
+    d1, rep, ok1 = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, precision=precision, threads=threads)
+    assert ok0 and ok1
+    assert rep["rel_res"].max() <= 1e-10
+    assert _relerr(d1, d0).max() < 1e-9
