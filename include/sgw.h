@@ -211,6 +211,63 @@ sgw_status sgw_residual_noalloc(sgw_system* sys, int nrhs, const void* rhs, cons
                                 const double* omega, double eta, const void* dpsi, double* rel_res,
                                 double* cert, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Per-shift solves with a diagonal preconditioner.  The paper does not say how its linear
+ * systems are preconditioned; this part is an addition.  A preconditioner breaks the shift
+ * invariance the multishift pass relies on, so it acts on single-shift systems: pairs that
+ * are solved one by one (stragglers, correction equations).  Pair i solves
+ * (P_c H P_c - z_i) x_i = -P_c rhs_i, z_i = e_ref[i] + omega[i] + i eta, by BiCGstab(ell)
+ * right-preconditioned with a positive diagonal D:
+ *   SGW_PRECOND_PLAIN    M_G = 1 / max(1, T_G / e_prec), e_prec = 1.35 <r|T|r> / <r|r> of the
+ *                        pair's right-hand side r (a kinetic-energy scaling);
+ *   SGW_PRECOND_JACOBI   J_G = 1 / max(|H_GG - z_i|, delta_i), H_GG = T_G + <V_loc> +
+ *                        sum_p D_p |beta_p(G)|^2 (delta_i from the `delta` array);
+ *   SGW_PRECOND_LEARNED  M_G exp(f(phi_G)), phi_G = (T_G / (E_cut / 2), omega / 2.205 Ha, e_ref,
+ *                        <V_loc>), f the perceptron of an sgw_mlp trained to predict
+ *                        log(J_G / M_G) at the floor that solved training pairs fastest.
+ * The Krylov residual decides convergence, so D changes iteration counts, never the answer.
+ * --------------------------------------------------------------------------------------- */
+enum { SGW_PRECOND_NONE = 0, SGW_PRECOND_PLAIN = 1, SGW_PRECOND_LEARNED = 2, SGW_PRECOND_JACOBI = 3 };
+
+/* The perceptron 4 -> 64 -> 64 -> 1 with erf-GELU activations (4545 FP32 master parameters,
+ * packed w1[64][4], b1[64], w2[64][64], b2[64], w3[64], b3), evaluated with bfloat16 weights
+ * and FP32 accumulation; trained with Adam (beta 0.9 / 0.999, eps 1e-8) on a mean squared
+ * error.  Row arrays (feats [n][4], targets [n], weight [n], out [n]) are FP32 device buffers. */
+typedef struct sgw_mlp sgw_mlp;
+#define SGW_MLP_PARAMS 4545
+sgw_status sgw_mlp_create(const float* params /* host [4545] */, sgw_mlp** out);
+sgw_status sgw_mlp_get_params(const sgw_mlp* mlp, float* params /* host [4545] */);
+sgw_status sgw_mlp_forward(const sgw_mlp* mlp, int n, const float* feats, float* out, void* stream);
+/* Loss mean_i weight_i (f_i - target_i)^2 (weight NULL -> 1) and its gradient (host [4545]). */
+sgw_status sgw_mlp_grad(sgw_mlp* mlp, int n, const float* feats, const float* targets, const float* weight,
+                        float* grad, float* loss, void* stream);
+/* One Adam step on that loss; *loss receives the loss before the step. */
+sgw_status sgw_mlp_train_step(sgw_mlp* mlp, int n, const float* feats, const float* targets,
+                              const float* weight, float lr, float* loss, void* stream);
+void sgw_mlp_destroy(sgw_mlp* mlp);
+
+/* Per-shift preconditioned solves of npairs independent pairs.  rhs, x: complex
+ * [npairs][n_pw] (host or device); e_ref, omega (and delta for JACOBI): host [npairs];
+ * precond SGW_PRECOND_*; mlp required for SGW_PRECOND_LEARNED.  opts: ell, max_matvec and
+ * stream are used.  report arrays are [npairs]; rel_res and cert are the FP64 true residual
+ * and certificate. */
+sgw_status sgw_solve_pershift(sgw_system* sys, int npairs, const void* rhs, const double* e_ref,
+                              const double* omega, double eta, double tol, int precond, const double* delta,
+                              const sgw_mlp* mlp, const sgw_solve_opts* opts, void* x, sgw_report* report);
+
+/* The diagonal D of each pair (test hook): d [npairs][n_pw] FP64 (host or device). */
+sgw_status sgw_precond_diag(sgw_system* sys, int npairs, const void* rhs, const double* e_ref,
+                            const double* omega, double eta, int precond, const double* delta,
+                            const sgw_mlp* mlp, double* d, void* stream);
+
+/* Training rows of the learned preconditioner, one row per plane wave of each pair: features
+ * phi_G and target log(clip(J_G / M_G, e^-3, e^3)) at the pair's best Jacobi floor delta[i]
+ * (host [npairs]; delta <= 0 means the plain scaling was best: target 0).  rhs complex
+ * [npairs][n_pw] device; feats [npairs * n_pw][4] and targets [npairs * n_pw] FP32 device. */
+sgw_status sgw_training_rows(sgw_system* sys, int npairs, const void* rhs, const double* e_ref,
+                             const double* omega, double eta, const double* delta, float* feats,
+                             float* targets, void* stream);
+
 void sgw_destroy_system(sgw_system* sys);
 
 /* Message of the last failing call on this host thread ("" if none). */

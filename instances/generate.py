@@ -282,3 +282,19 @@ def config2(seed: int = 0, n_k: int = 4, ecut_ry: float = 20.0, dims=(36, 36, 36
     omega = np.linspace(0.0, 60.0, n_omega) / HA_EV
     return make_instance("cubic8-ecut%g" % ecut_ry, seed, a, tau, ecut_ry, dims, n_occ,
                          pairs, shortest_g(a, n_pert, True), omega, 0.1 / HA_EV)
+
+
+def fcc_perturbed(seed: int, ecut_ry: float = 10.0, dims=(16, 16, 16), n_occ: int = 4, n_pert: int = 8,
+                  n_omega: int = 16):
+    """Config-1 cell with seeded disorder, for training the learned preconditioner.
+    Draws: rng = default_rng(seed); atom displacements N(0, 0.05 bohr) (2 x 3), then k uniform
+    in [-1/2, 1/2)^3 (fractional); q = (0.1, 0, 0) 2pi/a, 8 shortest G, omega in [0, 50] eV."""
+    alat = 10.26
+    a, tau = fcc_cell(alat)
+    rng = np.random.default_rng(seed)
+    tau = tau + rng.normal(0.0, 0.05, size=tau.shape)
+    k = rng.uniform(-0.5, 0.5, size=3)
+    q = _frac_of_cart(a, np.array([0.1, 0.0, 0.0]) * 2 * math.pi / alat)
+    omega = np.linspace(0.0, 50.0, n_omega) / HA_EV
+    return make_instance("fcc2-disordered-%d" % seed, seed, a, tau, ecut_ry, dims, n_occ,
+                         [(k, k + q)], shortest_g(a, n_pert, True), omega, 0.1 / HA_EV)

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsgw.so")
-SOURCES = ["setup.cu", "kernels.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "kernels.cu", "api.cu", "noalloc.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

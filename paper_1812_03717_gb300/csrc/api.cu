@@ -41,6 +41,7 @@ struct sgw_system {
     std::vector<int> map;        // [npw]
     std::vector<double> eps;
     int lo[3], ext[3];           // Miller bounding box of the sphere (for Eq. 8 lookups)
+    double v_mean = 0.0;         // <V_loc> over the box (preconditioner feature)
     // device
     int* d_miller = nullptr;
     double* d_kin = nullptr;
@@ -278,6 +279,11 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     if (!finite_all(vloc_r, nbox)) {
         free_system(s);
         return fail(SGW_EINVAL, "non-finite V_loc");
+    }
+    {
+        double acc = 0.0;
+        for (size_t i = 0; i < nbox; ++i) acc += vloc_r[i];
+        s->v_mean = acc / (double)nbox;
     }
     double len[3];
     for (int i = 0; i < 3; ++i)
@@ -912,6 +918,235 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
         if (report->launches) *report->launches = launches;
     }
     if (!all) return fail(SGW_ENOCONV, "some (rhs, omega) pairs did not reach the tolerance");
+    return SGW_OK;
+}
+
+static sgw_status precond_common(sgw_system* s, int npairs, const double2* rhs_d, const double* eref_d,
+                                 const double* om_d, const double* delta_d, double eta, int precond,
+                                 const sgw_mlp* mlp, double* d_d, cudaStream_t st) {
+    PrecondArgs a;
+    a.n = npairs;
+    a.mode = precond;
+    a.rhs = rhs_d;
+    a.e_ref = eref_d;
+    a.omega = om_d;
+    a.delta = delta_d;
+    a.eta = eta;
+    a.half_ecut = 0.5 * s->ecut;
+    a.v_mean = s->v_mean;
+    a.mlp = precond == SGW_PRECOND_LEARNED ? mlp_weights(mlp) : nullptr;
+    a.d = d_d;
+    SGW_CUDA(launch_precond(s->plan, a, st), "preconditioner kernel");
+    return SGW_OK;
+}
+
+static sgw_status check_precond(int precond, const double* delta, int n, const sgw_mlp* mlp) {
+    if (precond < SGW_PRECOND_NONE || precond > SGW_PRECOND_JACOBI) return fail(SGW_EINVAL, "bad precond");
+    if (precond == SGW_PRECOND_LEARNED && !mlp) return fail(SGW_EINVAL, "learned preconditioner needs an sgw_mlp");
+    if (precond == SGW_PRECOND_JACOBI) {
+        if (!delta) return fail(SGW_EINVAL, "Jacobi preconditioner needs delta");
+        for (int i = 0; i < n; ++i)
+            if (!(delta[i] > 0.0) || !std::isfinite(delta[i])) return fail(SGW_EINVAL, "delta must be positive");
+    }
+    return SGW_OK;
+}
+
+sgw_status sgw_precond_diag(sgw_system* s, int npairs, const void* rhs, const double* e_ref, const double* omega,
+                            double eta, int precond, const double* delta, const sgw_mlp* mlp, double* d, void* stream) {
+    g_err.clear();
+    if (!s || !rhs || !e_ref || !omega || !d) return fail(SGW_EINVAL, "NULL argument");
+    sgw_status r;
+    if ((r = check_precond(precond, delta, npairs, mlp)) != SGW_OK) return r;
+    if (precond == SGW_PRECOND_NONE) return fail(SGW_EINVAL, "no diagonal for SGW_PRECOND_NONE");
+    if (npairs <= 0) return SGW_OK;
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vb = sizeof(double2) * (size_t)s->npw;
+    Staged in, out;
+    if ((r = stage_in(rhs, vb * npairs, in, st, "rhs")) != SGW_OK) return r;
+    if ((r = stage_out(d, sizeof(double) * s->npw * (size_t)npairs, out, "d")) != SGW_OK) return r;
+    Carve c;
+    const size_t o_e = c.take(sizeof(double) * npairs), o_o = c.take(sizeof(double) * npairs),
+                 o_d = c.take(sizeof(double) * npairs);
+    if ((r = ensure_ws(s, c.off)) != SGW_OK) return r;
+    char* w = (char*)s->d_ws;
+    SGW_CUDA(cudaMemcpyAsync(w + o_e, e_ref, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    SGW_CUDA(cudaMemcpyAsync(w + o_o, omega, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    if (delta) SGW_CUDA(cudaMemcpyAsync(w + o_d, delta, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    if ((r = precond_common(s, npairs, (const double2*)in.dev, (const double*)(w + o_e), (const double*)(w + o_o),
+                            delta ? (const double*)(w + o_d) : nullptr, eta, precond, mlp, (double*)out.dev, st)) !=
+        SGW_OK)
+        return r;
+    if ((r = finish_out(out, st, "d copy")) != SGW_OK) return r;
+    SGW_CUDA(cudaStreamSynchronize(st), "precond");
+    return SGW_OK;
+}
+
+sgw_status sgw_training_rows(sgw_system* s, int npairs, const void* rhs, const double* e_ref, const double* omega,
+                             double eta, const double* delta, float* feats, float* targets, void* stream) {
+    g_err.clear();
+    if (!s || !rhs || !e_ref || !omega || !delta || !feats || !targets) return fail(SGW_EINVAL, "NULL argument");
+    if (npairs <= 0) return SGW_OK;
+    if (!is_device_ptr(rhs) || !is_device_ptr(feats) || !is_device_ptr(targets))
+        return fail(SGW_EINVAL, "training rows take device buffers");
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    Carve c;
+    const size_t o_e = c.take(sizeof(double) * npairs), o_o = c.take(sizeof(double) * npairs),
+                 o_d = c.take(sizeof(double) * npairs);
+    sgw_status r;
+    if ((r = ensure_ws(s, c.off)) != SGW_OK) return r;
+    char* w = (char*)s->d_ws;
+    SGW_CUDA(cudaMemcpyAsync(w + o_e, e_ref, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    SGW_CUDA(cudaMemcpyAsync(w + o_o, omega, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    SGW_CUDA(cudaMemcpyAsync(w + o_d, delta, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    TrainRowsArgs a;
+    a.n = npairs;
+    a.rhs = (const double2*)rhs;
+    a.e_ref = (const double*)(w + o_e);
+    a.omega = (const double*)(w + o_o);
+    a.delta = (const double*)(w + o_d);
+    a.eta = eta;
+    a.half_ecut = 0.5 * s->ecut;
+    a.v_mean = s->v_mean;
+    a.feats = feats;
+    a.targets = targets;
+    SGW_CUDA(launch_training_rows(s->plan, a, st), "training rows kernel");
+    SGW_CUDA(cudaStreamSynchronize(st), "training rows");
+    return SGW_OK;
+}
+
+sgw_status sgw_solve_pershift(sgw_system* s, int npairs, const void* rhs, const double* e_ref, const double* omega,
+                              double eta, double tol, int precond, const double* delta, const sgw_mlp* mlp,
+                              const sgw_solve_opts* opts, void* x, sgw_report* report) {
+    g_err.clear();
+    if (!s || !rhs || !e_ref || !omega || !x) return fail(SGW_EINVAL, "NULL argument");
+    if (npairs < 0) return fail(SGW_EINVAL, "negative npairs");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(SGW_EINVAL, "eta must be positive");
+    if (!(tol > 0.0)) return fail(SGW_EINVAL, "tol must be positive");
+    {
+        const sgw_status pr = check_precond(precond, delta, npairs, mlp);
+        if (pr != SGW_OK) return pr;
+    }
+    if (!finite_all(e_ref, npairs) || !finite_all(omega, npairs)) return fail(SGW_EINVAL, "non-finite e_ref or omega");
+    if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+    if (npairs == 0) return SGW_OK;
+    const int ell = opts && opts->ell ? opts->ell : 4;
+    if (ell < 1 || ell > kMaxEll) return fail(SGW_EINVAL, "ell must be 1..4");
+    const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : 40000;
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    const size_t vb = sizeof(double2) * (size_t)s->npw;
+    Staged in, out;
+    sgw_status r;
+    if ((r = stage_in(rhs, vb * npairs, in, st, "rhs")) != SGW_OK) return r;
+    if ((r = stage_out(x, vb * npairs, out, "x")) != SGW_OK) return r;
+    int grid = 0, grid_r = 0;
+    SGW_CUDA(solve_grid(s->plan, 1, npairs, &grid), "solver occupancy");
+    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r), "residual occupancy");
+    grid_r = std::min(grid_r, npairs);
+    Carve c;
+    const size_t o_seed = c.take(vb * (2 * ell + 3) * grid);
+    const size_t o_uw = c.take(vb * grid);
+    const size_t o_pscr = c.take(2 * vb * grid);
+    const size_t o_pre = c.take(sizeof(double) * s->npw * (size_t)npairs);
+    const size_t o_z = c.take(sizeof(double) * npairs);
+    const size_t o_e = c.take(sizeof(double) * npairs);
+    const size_t o_o = c.take(sizeof(double) * npairs);
+    const size_t o_dl = c.take(sizeof(double) * npairs);
+    const size_t o_zero = c.take(sizeof(double));
+    const size_t o_cnt = c.take(sizeof(int));
+    const size_t o_mv = c.take(sizeof(int) * npairs);
+    const size_t o_est = c.take(sizeof(double) * npairs);
+    const size_t o_st = c.take(sizeof(int) * npairs);
+    const size_t o_rscr = c.take(2 * vb * grid_r);
+    const size_t o_rel = c.take(sizeof(double) * npairs);
+    const size_t o_cert = c.take(sizeof(double) * npairs);
+    if ((r = ensure_ws(s, c.off)) != SGW_OK) return r;
+    char* w = (char*)s->d_ws;
+    std::vector<double> zre(npairs);
+    for (int i = 0; i < npairs; ++i) zre[i] = e_ref[i] + omega[i];
+    SGW_CUDA(cudaMemcpyAsync(w + o_z, zre.data(), sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    SGW_CUDA(cudaMemcpyAsync(w + o_e, e_ref, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    SGW_CUDA(cudaMemcpyAsync(w + o_o, omega, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    SGW_CUDA(cudaMemsetAsync(w + o_zero, 0, sizeof(double), st), "memset");
+    if (delta) SGW_CUDA(cudaMemcpyAsync(w + o_dl, delta, sizeof(double) * npairs, cudaMemcpyHostToDevice, st), "copy");
+    int launches = 0;
+    if (precond != SGW_PRECOND_NONE) {
+        if ((r = precond_common(s, npairs, (const double2*)in.dev, (const double*)(w + o_e), (const double*)(w + o_o),
+                                delta ? (const double*)(w + o_dl) : nullptr, eta, precond, mlp, (double*)(w + o_pre),
+                                st)) != SGW_OK)
+            return r;
+        ++launches;
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const bool timed = report && report->kernel_ms;
+    if (timed) {
+        SGW_CUDA(cudaEventCreate(&ev0), "event");
+        SGW_CUDA(cudaEventCreate(&ev1), "event");
+        SGW_CUDA(cudaEventRecord(ev0, st), "event");
+    }
+    SolveArgs A;
+    A.nrhs = npairs;
+    A.nshift = 1;
+    A.ell = ell;
+    A.max_mv = max_mv;
+    A.rhs = (const double2*)in.dev;
+    A.e_ref = (const double*)(w + o_z);
+    A.sig = (const double*)(w + o_zero);
+    A.omega_seed = 0.0;
+    A.eta = eta;
+    A.tol = tol;
+    A.x = (double2*)out.dev;
+    A.uw = (double2*)(w + o_uw);
+    A.seedw = (double2*)(w + o_seed);
+    A.counter = (int*)(w + o_cnt);
+    A.out_mv = (int*)(w + o_mv);
+    A.out_res = (double*)(w + o_est);
+    A.out_status = (int*)(w + o_st);
+    A.pre = precond != SGW_PRECOND_NONE ? (const double*)(w + o_pre) : nullptr;
+    A.pscr = (double2*)(w + o_pscr);
+    SGW_CUDA(launch_solve(s->plan, A, grid, st), "per-shift solver");
+    ++launches;
+    if (timed) SGW_CUDA(cudaEventRecord(ev1, st), "event");
+    SGW_CUDA(launch_residual(s->plan, npairs, 1, nullptr, 0, (const double2*)in.dev, (const double*)(w + o_z),
+                             (const double*)(w + o_zero), eta, (const double2*)out.dev, (double2*)(w + o_rscr),
+                             (double*)(w + o_rel), (double*)(w + o_cert), nullptr, grid_r, st),
+             "residual kernel");
+    ++launches;
+    if ((r = finish_out(out, st, "x copy")) != SGW_OK) return r;
+    std::vector<int> stv(npairs), mvv(npairs);
+    std::vector<double> estv(npairs), relv(npairs), certv(npairs);
+    SGW_CUDA(cudaMemcpyAsync(stv.data(), w + o_st, sizeof(int) * npairs, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(mvv.data(), w + o_mv, sizeof(int) * npairs, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(estv.data(), w + o_est, sizeof(double) * npairs, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(relv.data(), w + o_rel, sizeof(double) * npairs, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(certv.data(), w + o_cert, sizeof(double) * npairs, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaStreamSynchronize(st), "per-shift solve");
+    bool all = true;
+    for (int i = 0; i < npairs; ++i) {
+        if (relv[i] <= tol) stv[i] = SGW_PAIR_CONVERGED;
+        else if (stv[i] == SGW_PAIR_CONVERGED) stv[i] = SGW_PAIR_MAXITER;
+        all = all && stv[i] == SGW_PAIR_CONVERGED;
+    }
+    if (report) {
+        if (report->status) std::memcpy(report->status, stv.data(), sizeof(int) * npairs);
+        if (report->matvecs) std::memcpy(report->matvecs, mvv.data(), sizeof(int) * npairs);
+        if (report->est_res) std::memcpy(report->est_res, estv.data(), sizeof(double) * npairs);
+        if (report->rel_res) std::memcpy(report->rel_res, relv.data(), sizeof(double) * npairs);
+        if (report->cert) std::memcpy(report->cert, certv.data(), sizeof(double) * npairs);
+        if (report->launches) *report->launches = launches;
+        if (timed) {
+            float ms = 0.f;
+            SGW_CUDA(cudaEventElapsedTime(&ms, ev0, ev1), "event");
+            *report->kernel_ms = ms;
+        }
+    }
+    if (timed) {
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+    }
+    if (!all) return fail(SGW_ENOCONV, "some pairs did not reach the tolerance");
     return SGW_OK;
 }
 

@@ -23,6 +23,7 @@
 // U_t = A_0^t u.
 #include <cuda_runtime.h>
 
+#include "mlp.cuh"
 #include "setup.h"
 #include "sgw_internal.cuh"
 
@@ -106,6 +107,33 @@ __device__ __forceinline__ double2 cpowr(double2 a, int e) {
 
 }  // namespace
 
+// out = A D in with A = P_c H P_c - z and D = diag(pre) (right preconditioning of a
+// single-shift system): T1 = D in, T2 = P_c T1, out = P_c H T2 - z T1.  Without `pre` the
+// Krylov vectors already lie in range(P_c) and out = P_c H in - z in.
+static __device__ void apply_op(const Plan& P, unsigned char* smem, const double2* in, double2* out, double2 zs,
+                                const double* pre, double2* t1, double2* t2) {
+    if (!pre) {
+        apply_h_block<ArF64>(P, smem, in, out, zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+        return;
+    }
+    const ApplySmem L = apply_smem_layout(P);
+    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
+    for (int g = tid; g < npw; g += nt) t1[g] = cscal(in[g], pre[g]);
+    __syncthreads();
+    block_dots(P.psi, P.nocc, npw, t1, npw, red, coef);
+    for (int g = tid; g < npw; g += nt) {
+        double2 h = t1[g];
+        for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
+        t2[g] = h;
+    }
+    __syncthreads();
+    apply_h_block<ArF64>(P, smem, t2, out, cz(), APPLY_PROJ_OUT);
+    for (int g = tid; g < npw; g += nt) out[g] = csub(out[g], cmul(zs, t1[g]));
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SeedScalars S;
@@ -145,6 +173,8 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
     }
     double2* RT = W + (size_t)(2 * ell + 2) * npw;
     double2* UW = A.uw + (size_t)blockIdx.x * ns * npw;
+    double2* T1 = A.pscr ? A.pscr + (size_t)blockIdx.x * 2 * npw : nullptr;
+    double2* T2 = T1 ? T1 + npw : nullptr;
     for (int j = tid; j < ns; j += nt) sig[j] = A.sig[j];
 
     for (;;) {
@@ -156,6 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
         const double2* rhs = A.rhs + (size_t)r * npw;
         double2* X = A.x + (size_t)r * ns * npw;
         const double2 zs = make_double2(A.e_ref[r] + A.omega_seed, A.eta);
+        const double* pre = A.pre ? A.pre + (size_t)r * npw : nullptr;   // single-shift systems only
 
         // b = -P_c rhs (Eq. 8 with the sign of the problem statement)
         block_dots(P.psi, P.nocc, npw, rhs, npw, red, coef);
@@ -225,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                         for (int i = 0; i <= j; ++i) U[i][g] = csub(R[i][g], cmul(be, U[i][g]));
                 }
                 __syncthreads();
-                apply_h_block<ArF64>(P, smem, U[j], U[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+                apply_op(P, smem, U[j], U[j + 1], zs, pre, T1, T2);
                 block_dots(RT, 1, 0, U[j + 1], npw, red, s_dot);
                 if (tid == 0) {
                     const double2 gam = s_dot[0];
@@ -276,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                         for (int i = 0; i <= j; ++i) R[i][g] = csub(R[i][g], cmul(al, U[i + 1][g]));
                 }
                 __syncthreads();
-                apply_h_block<ArF64>(P, smem, R[j], R[j + 1], zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+                apply_op(P, smem, R[j], R[j + 1], zs, pre, T1, T2);
                 for (int a = tid; a < S.nact; a += nt) {
                     const int k = act[a];
                     zp[k] = zc[k];
@@ -442,6 +473,9 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
             __syncthreads();
         }
         __syncthreads();
+        if (pre) {   // the iterate solves A D y = b: x = D y
+            for (int g = tid; g < npw; g += nt) X[g] = cscal(X[g], pre[g]);
+        }
         for (int j = tid; j < ns; j += nt) {
             int s = st[j];
             if (s < 0) {
@@ -774,6 +808,103 @@ __global__ void pair_axpy_kernel(int nlist, const int* __restrict__ list, int np
         double2* xp = x + (size_t)list[i] * npw + g;
         *xp = cadd(*xp, d[t]);
     }
+}
+
+// ---------------------------------------------------------- diagonal preconditioners
+//
+// D_G for the per-shift systems (the paper does not say how its systems are
+// preconditioned; these are additions):
+//   plain    M_G = 1 / max(1, T_G / e_prec), e_prec = 1.35 <r|T|r> / <r|r> of the item's
+//            right-hand side r;
+//   Jacobi   J_G = 1 / max(|H_GG - z|, delta), H_GG = T_G + <V_loc> + sum_p D_p |beta_p(G)|^2;
+//   learned  M_G exp(f(phi_G)), phi_G = (T_G / (E_cut/2), omega / 2.205 Ha, e_ref, <V_loc>), f a
+//            4-64-64-1 erf-GELU perceptron evaluated with bf16 weights and FP32 accumulation.
+__device__ __forceinline__ double h_diag(const Plan& P, int g, double v_mean) {
+    double h = P.kin[g] + v_mean;
+    for (int p = 0; p < P.nproj; ++p) h += P.dkb[p] * cabs2(P.beta[(size_t)p * P.npw + g]);
+    return h;
+}
+
+__device__ __forceinline__ double plain_e_prec(const Plan& P, const double2* rv, double2* red, double2* out) {
+    double2 acc[2] = {cz(), cz()};
+    for (int g = threadIdx.x; g < P.npw; g += blockDim.x) {
+        const double m2 = cabs2(rv[g]);
+        acc[0].x += m2 * P.kin[g];
+        acc[1].x += m2;
+    }
+    block_sum<2>(acc, red, out);
+    return out[1].x > 0.0 ? 1.35 * out[0].x / out[1].x : 1.0;
+}
+
+__global__ void __launch_bounds__(kThreads) precond_kernel(Plan P, PrecondArgs a) {
+    __shared__ double2 red[(kMaxThreads / 32) * kRedSlots];
+    __shared__ double2 out[kRedSlots];
+    __shared__ float w[kMlpParams];
+    const int tid = threadIdx.x, nt = blockDim.x, npw = P.npw;
+    if (a.mode == SGW_PRECOND_LEARNED) {
+        for (int i = tid; i < kMlpParams; i += nt) w[i] = __bfloat162float(a.mlp[i]);
+    }
+    for (int it = blockIdx.x; it < a.n; it += gridDim.x) {
+        const double e_prec = plain_e_prec(P, a.rhs + (size_t)it * npw, red, out);
+        const double zr = a.e_ref[it] + a.omega[it];
+        const double delta = a.delta ? a.delta[it] : 0.0;
+        for (int g = tid; g < npw; g += nt) {
+            double m = 1.0 / fmax(1.0, P.kin[g] / e_prec);
+            if (a.mode == SGW_PRECOND_JACOBI) {
+                const double hr = h_diag(P, g, a.v_mean) - zr;
+                m = 1.0 / fmax(sqrt(hr * hr + a.eta * a.eta), delta);
+            } else if (a.mode == SGW_PRECOND_LEARNED) {
+                float x[4] = {(float)(P.kin[g] / a.half_ecut), (float)(a.omega[it] / kOmegaScale), (float)a.e_ref[it],
+                              (float)a.v_mean};
+                m *= exp((double)mlp_eval(w, x));
+            }
+            a.d[(size_t)it * npw + g] = m;
+        }
+        __syncthreads();
+    }
+}
+
+// Training rows of the learned preconditioner: per plane wave of each pair, phi_G and
+// target log(clip(J_G / M_G, e^-3, e^3)) with J the Jacobi diagonal at the pair's best floor
+// delta_i (the floor that solved the pair in the fewest H applications), or 0 where the
+// plain scaling won (delta_i <= 0).
+__global__ void __launch_bounds__(kThreads) training_rows_kernel(Plan P, TrainRowsArgs a) {
+    __shared__ double2 red[(kMaxThreads / 32) * kRedSlots];
+    __shared__ double2 out[kRedSlots];
+    const int tid = threadIdx.x, nt = blockDim.x, npw = P.npw;
+    for (int it = blockIdx.x; it < a.n; it += gridDim.x) {
+        const double e_prec = plain_e_prec(P, a.rhs + (size_t)it * npw, red, out);
+        const double zr = a.e_ref[it] + a.omega[it];
+        const double delta = a.delta[it];
+        for (int g = tid; g < npw; g += nt) {
+            const size_t row = (size_t)it * npw + g;
+            const double m = 1.0 / fmax(1.0, P.kin[g] / e_prec);
+            double t = 0.0;
+            if (delta > 0.0) {
+                const double hr = h_diag(P, g, a.v_mean) - zr;
+                const double j = 1.0 / fmax(sqrt(hr * hr + a.eta * a.eta), delta);
+                t = fmin(fmax(log(j / m), -3.0), 3.0);
+            }
+            a.feats[4 * row + 0] = (float)(P.kin[g] / a.half_ecut);
+            a.feats[4 * row + 1] = (float)(a.omega[it] / kOmegaScale);
+            a.feats[4 * row + 2] = (float)a.e_ref[it];
+            a.feats[4 * row + 3] = (float)a.v_mean;
+            a.targets[row] = (float)t;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_training_rows(const Plan& P, const TrainRowsArgs& a, cudaStream_t st) {
+    if (a.n == 0) return cudaSuccess;
+    training_rows_kernel<<<a.n < 4096 ? a.n : 4096, kThreads, 0, st>>>(P, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_precond(const Plan& P, const PrecondArgs& a, cudaStream_t st) {
+    if (a.n == 0) return cudaSuccess;
+    precond_kernel<<<a.n < 4096 ? a.n : 4096, kThreads, 0, st>>>(P, a);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------ host launchers

@@ -1,6 +1,7 @@
 // Host-side launchers of the set-up kernels (setup.cu) and the hot kernels (kernels.cu).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "sgw_internal.cuh"
@@ -52,7 +53,37 @@ struct SolveArgs {
     int* out_mv;              // [nrhs][nshift]
     double* out_res;          // [nrhs][nshift]
     int* out_status;          // [nrhs][nshift]
+    const double* pre = nullptr;   // [nrhs][npw] right diagonal preconditioner (nshift == 1 only)
+    double2* pscr = nullptr;       // [grid][2][npw] scratch for the preconditioned operator
 };
+
+struct PrecondArgs {
+    int n;                         // items (single-shift systems)
+    int mode;                      // SGW_PRECOND_PLAIN / _JACOBI / _LEARNED
+    const double2* rhs;            // [n][npw]
+    const double* e_ref;           // [n]
+    const double* omega;           // [n]
+    const double* delta;           // [n] Jacobi floors (JACOBI)
+    double eta;
+    double half_ecut;              // E_cut / 2 (Ha)
+    double v_mean;                 // <V_loc> (Ha)
+    const __nv_bfloat16* mlp;      // packed perceptron weights (LEARNED)
+    double* d;                     // [n][npw] out
+};
+cudaError_t launch_precond(const Plan& P, const PrecondArgs& a, cudaStream_t st);
+
+struct TrainRowsArgs {
+    int n;
+    const double2* rhs;            // [n][npw]
+    const double* e_ref;           // [n]
+    const double* omega;           // [n]
+    const double* delta;           // [n] best Jacobi floor of each pair (<= 0: plain was best)
+    double eta, half_ecut, v_mean;
+    float* feats;                  // [n * npw][4]
+    float* targets;                // [n * npw]
+};
+cudaError_t launch_training_rows(const Plan& P, const TrainRowsArgs& a, cudaStream_t st);
+const __nv_bfloat16* mlp_weights(const sgw_mlp* m);
 
 struct LanczosArgs {
     int nrhs, nshift, maxk;

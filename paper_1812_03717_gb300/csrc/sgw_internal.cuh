@@ -327,12 +327,14 @@ __device__ void fft_lines(typename Ar::C* data, int nlines, int lpp, int pstride
 #pragma unroll
                 for (int k = 0; k < 5; ++k)
                     if (k < R) v[k] = data[base + (j + k * nb) * es];
+                if (jm != 0) {   // the first stage (Ns = 1) and every j with j mod Ns = 0 need no twiddle
 #pragma unroll
-                for (int k = 1; k < 5; ++k) {
-                    if (k < R) {
-                        C w = tw[jm * k * stride];
-                        if (SIGN > 0) w = Ar::conj(w);
-                        v[k] = Ar::mul(v[k], w);
+                    for (int k = 1; k < 5; ++k) {
+                        if (k < R) {
+                            C w = tw[jm * k * stride];
+                            if (SIGN > 0) w = Ar::conj(w);
+                            v[k] = Ar::mul(v[k], w);
+                        }
                     }
                 }
                 dft_small<Ar, SIGN>(v, R);

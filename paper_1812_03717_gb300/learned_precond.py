@@ -1,0 +1,161 @@
+"""Training and evaluation driver of the learned diagonal preconditioner.
+
+Training data come from solves the library itself runs: each training pair (a right-hand
+side of a seeded disordered fcc system at one frequency) is solved per shift with the plain
+kinetic scaling and with the Jacobi scaling at several floors; the fastest floor defines the
+per-plane-wave targets (sgw_training_rows).  The perceptron is trained on the GPU with the
+library's forward/backward/Adam kernels (sgw_mlp_train_step).  Evaluation compares
+H-application counts of per-shift solves on held-out systems with the plain and the learned
+preconditioner (the residual decides convergence, so only counts may change).
+
+    python -m paper_1812_03717_gb300.learned_precond --train-seeds 24 --eval-seeds 4 --out weights.npy
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DELTAS = (0.03, 0.1, 0.3, 1.0)     # Jacobi floors (Ha) tried on every training pair
+N_HIDDEN, N_IN = 64, 4
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-uniform hidden layers, zero output layer: the untrained network reproduces the
+    plain scaling exactly.  Packed w1[64][4], b1, w2[64][64], b2, w3[64], b3."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.uniform(-math.sqrt(6 / N_IN), math.sqrt(6 / N_IN), (N_HIDDEN, N_IN))
+    w2 = rng.uniform(-math.sqrt(6 / N_HIDDEN), math.sqrt(6 / N_HIDDEN), (N_HIDDEN, N_HIDDEN))
+    parts = [w1, np.zeros(N_HIDDEN), w2, np.zeros(N_HIDDEN), np.zeros(N_HIDDEN), np.zeros(1)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def _pairs(inst, ik, n_pairs, seed):
+    rng = np.random.default_rng(10_000 + seed)
+    nr = inst.n_occ * inst.n_pert
+    r = rng.integers(0, nr, n_pairs)
+    j = rng.integers(0, len(inst.omega), n_pairs)
+    return r, j
+
+
+def _system(P, inst, ik=0):
+    import torch
+    kp = inst.kpoints[ik]
+    skq = P.System.from_instance(inst, kp.kq_frac)
+    sk = P.System.from_instance(inst, kp.k_frac)
+    skq.set_occupied(kp.psi_kq, kp.eps_kq)
+    rhs = skq.make_rhs(sk, torch.from_numpy(kp.psi_k).cuda(), inst.gp_miller)
+    sk.close()
+    return skq, rhs
+
+
+def training_set(P, seeds, pairs_per_seed=32, tol=1e-8, deltas=DELTAS, make=None):
+    """Rows (feats, targets) on the GPU from per-shift solves on the given seeds."""
+    import torch
+    import instances as I
+    make = make or I.fcc_perturbed
+    feats, targets, stats = [], [], {"pairs": 0, "plain_mv": 0, "best_mv": 0, "wins": [0] * (len(deltas) + 1)}
+    for seed in seeds:
+        inst = make(seed)
+        s, rhs = _system(P, inst)
+        r, j = _pairs(inst, 0, pairs_per_seed, seed)
+        rp = rhs[torch.as_tensor(r, device=rhs.device)].contiguous()
+        e = inst.e_ref(0)[r]
+        om = inst.omega[j]
+        _, rep, _ = s.solve_pershift(rp, e, om, inst.eta, tol=tol, precond="plain")
+        counts = [rep["matvecs"].astype(np.int64)]
+        for dl in deltas:
+            _, rep, _ = s.solve_pershift(rp, e, om, inst.eta, tol=tol, precond="jacobi", delta=dl)
+            mv = rep["matvecs"].astype(np.int64)
+            mv[rep["status"] != 0] = 1 << 30
+            counts.append(mv)
+        counts = np.stack(counts)                     # [1 + n_delta][pairs]
+        best = counts.argmin(axis=0)
+        best_delta = np.where(best == 0, 0.0, np.asarray((0.0,) + tuple(deltas))[best])
+        f, t = s.training_rows(rp, e, om, inst.eta, best_delta)
+        feats.append(f)
+        targets.append(t)
+        stats["pairs"] += len(r)
+        stats["plain_mv"] += int(counts[0].sum())
+        stats["best_mv"] += int(counts.min(axis=0).sum())
+        for b in best:
+            stats["wins"][int(b)] += 1
+        s.close()
+    return torch.cat(feats), torch.cat(targets), stats
+
+
+def train(P, feats, targets, steps=400, lr=3e-3, batch=8192, seed=0, params=None):
+    import torch
+    mlp = P.MLP(init_params(seed) if params is None else params)
+    n = feats.shape[0]
+    g = torch.Generator(device=feats.device)
+    g.manual_seed(seed)
+    losses = []
+    for it in range(steps):
+        idx = torch.randint(0, n, (min(batch, n),), device=feats.device, generator=g)
+        losses.append(mlp.train_step(feats[idx].contiguous(), targets[idx].contiguous(), lr=lr))
+    return mlp, losses
+
+
+def evaluate(P, mlp, seeds, pairs_per_seed=32, tol=1e-10, make=None):
+    """H applications per pair with the plain and the learned preconditioner on held-out seeds."""
+    import torch
+    import instances as I
+    make = make or I.fcc_perturbed
+    out = {"plain": [], "learned": [], "max_rel_res": 0.0, "max_diff": 0.0}
+    for seed in seeds:
+        inst = make(seed)
+        s, rhs = _system(P, inst)
+        r, j = _pairs(inst, 0, pairs_per_seed, seed)
+        rp = rhs[torch.as_tensor(r, device=rhs.device)].contiguous()
+        e = inst.e_ref(0)[r]
+        om = inst.omega[j]
+        x0, rp0, ok0 = s.solve_pershift(rp, e, om, inst.eta, tol=tol, precond="plain")
+        x1, rp1, ok1 = s.solve_pershift(rp, e, om, inst.eta, tol=tol, precond="learned", mlp=mlp)
+        out["plain"] += rp0["matvecs"].tolist()
+        out["learned"] += rp1["matvecs"].tolist()
+        out["max_rel_res"] = max(out["max_rel_res"], float(rp0["rel_res"].max()), float(rp1["rel_res"].max()))
+        d = torch.linalg.norm(x1 - x0, dim=1) / torch.linalg.norm(x0, dim=1)
+        out["max_diff"] = max(out["max_diff"], float(d.max()))
+        s.close()
+    out["plain_mean"] = float(np.mean(out["plain"]))
+    out["learned_mean"] = float(np.mean(out["learned"]))
+    out["gain"] = out["plain_mean"] / out["learned_mean"]
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train-seeds", type=int, default=24)
+    ap.add_argument("--eval-seeds", type=int, default=4)
+    ap.add_argument("--pairs", type=int, default=32)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    import paper_1812_03717_gb300 as P
+    t0 = time.time()
+    feats, targets, stats = training_set(P, range(args.train_seeds), args.pairs)
+    t1 = time.time()
+    mlp, losses = train(P, feats, targets, steps=args.steps, lr=args.lr)
+    t2 = time.time()
+    ev = evaluate(P, mlp, range(1000, 1000 + args.eval_seeds), args.pairs)
+    t3 = time.time()
+    if args.out:
+        np.save(args.out, mlp.params)
+    print(json.dumps({"rows": int(feats.shape[0]), "data": stats, "loss_first": losses[0], "loss_last": losses[-1],
+                      "eval": {k: v for k, v in ev.items() if k not in ("plain", "learned")},
+                      "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}))
+
+
+if __name__ == "__main__":
+    main()

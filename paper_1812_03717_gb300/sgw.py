@@ -25,7 +25,12 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
            "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_residual", "sgw_residual_noalloc",
-           "sgw_destroy_system", "sgw_last_error"]
+           "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
+           "sgw_mlp_forward", "sgw_mlp_grad", "sgw_mlp_train_step", "sgw_mlp_destroy", "sgw_destroy_system",
+           "sgw_last_error"]
+PRECOND_NONE, PRECOND_PLAIN, PRECOND_LEARNED, PRECOND_JACOBI = range(4)
+_PRECOND = {"none": PRECOND_NONE, "plain": PRECOND_PLAIN, "learned": PRECOND_LEARNED, "jacobi": PRECOND_JACOBI}
+MLP_PARAMS = 4545
 
 
 class SgwError(RuntimeError):
@@ -77,11 +82,23 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.POINTER(_Report)]
     lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_residual_noalloc.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
+    lib.sgw_solve_pershift.argtypes = [vp, ip, vp, vp, vp, dp, dp, ip, vp, vp, ctypes.POINTER(_Opts), vp,
+                                       ctypes.POINTER(_Report)]
+    lib.sgw_precond_diag.argtypes = [vp, ip, vp, vp, vp, dp, ip, vp, vp, vp, vp]
+    lib.sgw_training_rows.argtypes = [vp, ip, vp, vp, vp, dp, vp, vp, vp, vp]
+    lib.sgw_mlp_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.sgw_mlp_get_params.argtypes = [vp, vp]
+    lib.sgw_mlp_forward.argtypes = [vp, ip, vp, vp, vp]
+    lib.sgw_mlp_grad.argtypes = [vp, ip, vp, vp, vp, vp, vp, vp]
+    lib.sgw_mlp_train_step.argtypes = [vp, ip, vp, vp, vp, ctypes.c_float, vp, vp]
+    lib.sgw_mlp_destroy.argtypes = [vp]
+    lib.sgw_mlp_destroy.restype = None
     lib.sgw_destroy_system.argtypes = [vp]
     lib.sgw_destroy_system.restype = None
     lib.sgw_last_error.restype = ctypes.c_char_p
-    for name in EXPORTS[:-2]:
-        getattr(lib, name).restype = ctypes.c_int
+    for name in EXPORTS:
+        if name not in ("sgw_destroy_system", "sgw_last_error", "sgw_mlp_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -272,3 +289,104 @@ class System:
         _check(load().sgw_residual_noalloc(self._h, nrhs, rhs.data_ptr(), e_ref.data_ptr(), nw, omega.data_ptr(),
                                            float(eta), dpsi.data_ptr(), rel_res.data_ptr(), cert.data_ptr(),
                                            _stream_of(rhs, stream)))
+
+    def solve_pershift(self, rhs, e_ref, omega, eta, tol=1e-10, precond="plain", delta=None, mlp=None, ell=4,
+                       max_matvec=0, out=None, stream=None):
+        """Independent single-shift solves of pairs (rhs[i], z_i = e_ref[i] + omega[i] + i eta) with a
+        diagonal preconditioner; returns (x [npairs][n_pw], report, converged)."""
+        rhs = _c128(rhs)
+        n = rhs.shape[0]
+        e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        dl = None if delta is None else np.ascontiguousarray(np.broadcast_to(delta, (n,)), dtype=np.float64)
+        if out is None:
+            out = _like(rhs, (n, self.n_pw))
+        rep = {"matvecs": np.zeros(n, dtype=np.int32), "est_res": np.zeros(n), "rel_res": np.zeros(n),
+               "cert": np.zeros(n), "status": np.zeros(n, dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
+               "kernel_ms": np.zeros(1)}
+        opts = _Opts(METHOD_BICGSTAB, PREC_FP64, int(ell), -1, int(max_matvec), -1, 0, _stream_of(rhs, stream))
+        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
+                                                        "kernel_ms")))
+        st = load().sgw_solve_pershift(self._h, n, _ptr(rhs), e_ref.ctypes.data, omega.ctypes.data, float(eta),
+                                       float(tol), _PRECOND[precond], dl.ctypes.data if dl is not None else None,
+                                       mlp._h if mlp is not None else None, ctypes.byref(opts), _ptr(out),
+                                       ctypes.byref(crep))
+        _check(st, allow=(SGW_ENOCONV,))
+        return out, rep, st == SGW_OK
+
+    def precond_diag(self, rhs, e_ref, omega, eta, precond="plain", delta=None, mlp=None):
+        rhs = _c128(rhs)
+        n = rhs.shape[0]
+        d = np.empty((n, self.n_pw))
+        e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        dl = None if delta is None else np.ascontiguousarray(np.broadcast_to(delta, (n,)), dtype=np.float64)
+        _check(load().sgw_precond_diag(self._h, n, _ptr(rhs), e_ref.ctypes.data, omega.ctypes.data, float(eta),
+                                       _PRECOND[precond], dl.ctypes.data if dl is not None else None,
+                                       mlp._h if mlp is not None else None, d.ctypes.data, _stream_of(rhs, None)))
+        return d
+
+    def training_rows(self, rhs, e_ref, omega, eta, delta):
+        """(feats [n*n_pw][4], targets [n*n_pw]) float32 CUDA tensors; rhs a CUDA tensor."""
+        import torch
+        n = rhs.shape[0]
+        rows = n * self.n_pw
+        feats = torch.empty((rows, 4), dtype=torch.float32, device=rhs.device)
+        targets = torch.empty(rows, dtype=torch.float32, device=rhs.device)
+        e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        dl = np.ascontiguousarray(np.broadcast_to(delta, (n,)), dtype=np.float64)
+        _check(load().sgw_training_rows(self._h, n, rhs.data_ptr(), e_ref.ctypes.data, omega.ctypes.data, float(eta),
+                                        dl.ctypes.data, feats.data_ptr(), targets.data_ptr(), _stream_of(rhs, None)))
+        return feats, targets
+
+
+class MLP:
+    """The learned preconditioner's perceptron (sgw_mlp); rows are float32 CUDA tensors."""
+
+    def __init__(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_PARAMS:
+            raise ValueError("expected 4545 parameters")
+        h = ctypes.c_void_p()
+        _check(load().sgw_mlp_create(p.ctypes.data, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sgw_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def params(self):
+        p = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(load().sgw_mlp_get_params(self._h, p.ctypes.data))
+        return p
+
+    def forward(self, feats):
+        import torch
+        out = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
+        _check(load().sgw_mlp_forward(self._h, feats.shape[0], feats.data_ptr(), out.data_ptr(),
+                                      _stream_of(feats, None)))
+        return out
+
+    def grad(self, feats, targets, weight=None):
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _check(load().sgw_mlp_grad(self._h, feats.shape[0], feats.data_ptr(), targets.data_ptr(),
+                                   weight.data_ptr() if weight is not None else None, g.ctypes.data,
+                                   loss.ctypes.data, _stream_of(feats, None)))
+        return float(loss[0]), g
+
+    def train_step(self, feats, targets, weight=None, lr=1e-3):
+        loss = np.zeros(1, dtype=np.float32)
+        _check(load().sgw_mlp_train_step(self._h, feats.shape[0], feats.data_ptr(), targets.data_ptr(),
+                                         weight.data_ptr() if weight is not None else None, float(lr),
+                                         loss.ctypes.data, _stream_of(feats, None)))
+        return float(loss[0])
