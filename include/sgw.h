@@ -140,8 +140,9 @@ typedef struct {
                          true residual are FP64) */
     int ell;          /* BiCGstab(ell) degree 1..4 (0 -> 4); unused by Lanczos */
     int seed_index;   /* BiCGstab seed shift; -1 -> the largest omega; unused by Lanczos */
-    int max_matvec;   /* H applications per right-hand side and per correction solve (0 -> 40000); the
-                         Lanczos basis is also capped by free device memory */
+    int max_matvec;   /* H applications per right-hand side and per correction solve (0 -> 4096 for
+                         Lanczos, whose basis it sizes, 40000 for BiCGstab); the Lanczos basis is also
+                         capped by free device memory */
     int max_refine;   /* rounds of per-shift correction solves (0 -> 3, negative -> none) */
     int threads;      /* CTA size of the Lanczos kernel: 256, 384 or 512 (0 -> 256) */
     void* stream;     /* cudaStream_t, NULL = default stream */

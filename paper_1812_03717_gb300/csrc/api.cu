@@ -93,14 +93,17 @@ bool is_device_ptr(const void* p) {
 
 // A vector argument that may live on the host or the device.  Host data is copied to a
 // temporary device buffer (in) and/or back (out).
+// Staging buffers come from the stream-ordered allocator: no device-wide synchronisation,
+// so solves of several systems on several streams stay concurrent.
 struct Staged {
     void* dev = nullptr;
     const void* host_src = nullptr;
     void* host_dst = nullptr;
     size_t bytes = 0;
     bool owned = false;
+    cudaStream_t st = nullptr;
     ~Staged() {
-        if (owned && dev) cudaFree(dev);
+        if (owned && dev) cudaFreeAsync(dev, st);
     }
 };
 
@@ -111,22 +114,24 @@ sgw_status stage_in(const void* p, size_t bytes, Staged& s, cudaStream_t st, con
         return SGW_OK;
     }
     if (bytes == 0) return SGW_OK;
-    SGW_CUDA(cudaMalloc(&s.dev, bytes), name);
+    SGW_CUDA(cudaMallocAsync(&s.dev, bytes, st), name);
     s.owned = true;
+    s.st = st;
     s.host_src = p;
     SGW_CUDA(cudaMemcpyAsync(s.dev, p, bytes, cudaMemcpyHostToDevice, st), name);
     return SGW_OK;
 }
 
-sgw_status stage_out(void* p, size_t bytes, Staged& s, const char* name) {
+sgw_status stage_out(void* p, size_t bytes, Staged& s, const char* name, cudaStream_t st = nullptr) {
     s.bytes = bytes;
     if (is_device_ptr(p)) {
         s.dev = p;
         return SGW_OK;
     }
     if (bytes == 0) return SGW_OK;
-    SGW_CUDA(cudaMalloc(&s.dev, bytes), name);
+    SGW_CUDA(cudaMallocAsync(&s.dev, bytes, st), name);
     s.owned = true;
+    s.st = st;
     s.host_dst = p;
     return SGW_OK;
 }
@@ -596,7 +601,7 @@ sgw_status sgw_make_rhs(const sgw_system* kq, const sgw_system* k, int n_v, cons
     Staged in, out;
     sgw_status r;
     if ((r = stage_in(psi_k, sizeof(double2) * (size_t)n_v * k->npw, in, st, "psi_k")) != SGW_OK) return r;
-    if ((r = stage_out(rhs, sizeof(double2) * (size_t)n_v * n_pert * kq->npw, out, "rhs")) != SGW_OK) return r;
+    if ((r = stage_out(rhs, sizeof(double2) * (size_t)n_v * n_pert * kq->npw, out, "rhs", st)) != SGW_OK) return r;
     int* d_gp = nullptr;
     SGW_CUDA(cudaMalloc(&d_gp, sizeof(int) * 3 * n_pert), "gp allocation");
     cudaError_t e = cudaMemcpyAsync(d_gp, gp_miller, sizeof(int) * 3 * n_pert, cudaMemcpyHostToDevice, st);
@@ -632,7 +637,7 @@ static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const dou
     Staged in, out;
     sgw_status r;
     if ((r = stage_in(x, vb, in, st, "x")) != SGW_OK) return r;
-    if ((r = stage_out(y, vb, out, "y")) != SGW_OK) return r;
+    if ((r = stage_out(y, vb, out, "y", st)) != SGW_OK) return r;
     int grid = 0;
     SGW_CUDA(resident_grid(apply_kernel_ptr(), apply_smem_bytes(s->plan), &grid), "apply occupancy");
     grid = std::min(grid, nvec);
@@ -700,12 +705,13 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
             if (omega[j] > omega[seed]) seed = j;
     }
     if (seed >= nomega) return fail(SGW_EINVAL, "seed_index out of range");
-    const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : 40000;
+    const bool lanczos = method == SGW_METHOD_LANCZOS;
+    // Lanczos keeps its basis: the default budget of 4096 steps bounds its memory
+    const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : (lanczos ? 4096 : 40000);
     const int max_refine = !opts || opts->max_refine == 0 ? 3 : std::max(0, opts->max_refine);
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     if (nrhs == 0) return SGW_OK;
     SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
-    const bool lanczos = method == SGW_METHOD_LANCZOS;
     const int smem_main = lanczos ? lanczos_smem_bytes(s->plan, nomega) : solve_smem_bytes(s->plan, nomega);
     if (smem_main > max_optin_smem()) return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
@@ -713,7 +719,7 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     Staged in, out;
     sgw_status r;
     if ((r = stage_in(rhs, vb * nrhs, in, st, "rhs")) != SGW_OK) return r;
-    if ((r = stage_out(dpsi, vb * np, out, "dpsi")) != SGW_OK) return r;
+    if ((r = stage_out(dpsi, vb * np, out, "dpsi", st)) != SGW_OK) return r;
     const int chunk = (int)std::min<size_t>(np, 4096);
     int grid = 0, grid1 = 0, grid_r = 0;
     if (lanczos) {
@@ -735,7 +741,7 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     if (lanczos) {
         size_t free_b = 0, total_b = 0;
         SGW_CUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-        const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+        const size_t budget = std::min<size_t>(free_b / 2, (size_t)64 << 30);
         const size_t per_k = std::max<size_t>((size_t)grid * (vb + 16 + 32 * (size_t)nomega),
                                               (size_t)grid1 * (vb + 16 + 32));
         const size_t cap = budget / std::max<size_t>(per_k, 1);
@@ -964,7 +970,7 @@ sgw_status sgw_precond_diag(sgw_system* s, int npairs, const void* rhs, const do
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in, out;
     if ((r = stage_in(rhs, vb * npairs, in, st, "rhs")) != SGW_OK) return r;
-    if ((r = stage_out(d, sizeof(double) * s->npw * (size_t)npairs, out, "d")) != SGW_OK) return r;
+    if ((r = stage_out(d, sizeof(double) * s->npw * (size_t)npairs, out, "d", st)) != SGW_OK) return r;
     Carve c;
     const size_t o_e = c.take(sizeof(double) * npairs), o_o = c.take(sizeof(double) * npairs),
                  o_d = c.take(sizeof(double) * npairs);
@@ -1040,7 +1046,7 @@ sgw_status sgw_solve_pershift(sgw_system* s, int npairs, const void* rhs, const 
     Staged in, out;
     sgw_status r;
     if ((r = stage_in(rhs, vb * npairs, in, st, "rhs")) != SGW_OK) return r;
-    if ((r = stage_out(x, vb * npairs, out, "x")) != SGW_OK) return r;
+    if ((r = stage_out(x, vb * npairs, out, "x", st)) != SGW_OK) return r;
     int grid = 0, grid_r = 0;
     SGW_CUDA(solve_grid(s->plan, 1, npairs, &grid), "solver occupancy");
     SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r), "residual occupancy");

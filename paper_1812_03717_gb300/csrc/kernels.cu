@@ -920,6 +920,17 @@ int bicg_extra(int ns) { return shift_layout(0, ns).end; }
 int lanczos_extra(int ns) { return 3 * align16(ns * 16) + align16(ns * 8) + 2 * align16(ns * 4); }
 }  // namespace
 
+// Raises a kernel's dynamic shared-memory limit to everything the device allows next to its
+// static shared memory.  Always the same value for a kernel, so concurrent solves of systems
+// of different sizes (several host threads) never lower it under one another's launch.
+cudaError_t allow_max_smem(const void* kernel) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin_smem() - (int)fa.sharedSizeBytes);
+}
+
 // The plan with as many xy-planes per pass (4, 2 or 1) as fit next to `extra` bytes of
 // kernel-specific shared memory.
 Plan tuned_plan(const Plan& P, int extra) {
@@ -945,7 +956,7 @@ cudaError_t resident_grid(const void* kernel, int smem, int* grid, int threads) 
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = allow_max_smem(kernel);
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
     if (e != cudaSuccess) return e;
@@ -966,7 +977,7 @@ cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid) {
 cudaError_t launch_solve(const Plan& P0, const SolveArgs& a, int grid, cudaStream_t st) {
     const Plan P = tuned_plan(P0, bicg_extra(a.nshift));
     const int smem = solve_smem_bytes(P0, a.nshift);
-    cudaError_t e = cudaFuncSetAttribute((const void*)ms_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_max_smem((const void*)ms_solve_kernel);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
@@ -979,7 +990,7 @@ cudaError_t launch_apply(const Plan& P0, int nvec, const double2* x, double2* y,
     const Plan P = tuned_plan(P0, 0);
     const int smem = apply_smem_bytes(P0);
     const void* k = precision == SGW_PREC_DF32 ? (const void*)apply_kernel<ArDF> : (const void*)apply_kernel<ArF64>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_max_smem(k);
     if (e != cudaSuccess) return e;
     if (precision == SGW_PREC_DF32)
         apply_kernel<ArDF><<<grid, kThreads, smem, st>>>(P, nvec, x, y, z, project, scratch);
@@ -993,7 +1004,7 @@ cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* lis
                             double* rel, double* cert, double2* store, int grid, cudaStream_t st) {
     const Plan P = tuned_plan(P0, 0);
     const int smem = apply_smem_bytes(P0);
-    cudaError_t e = cudaFuncSetAttribute((const void*)residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_max_smem((const void*)residual_kernel);
     if (e != cudaSuccess) return e;
     residual_kernel<<<grid, kThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
                                                   cert, store);
@@ -1040,7 +1051,7 @@ cudaError_t launch_lanczos(const Plan& P0, const LanczosArgs& a, int grid, int p
     const bool df = precision == SGW_PREC_DF32;
     const int nt = lanczos_threads(threads);
     const void* k = df ? lanczos_ptr<ArDF>(nt) : lanczos_ptr<ArF64>(nt);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_max_smem(k);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
