@@ -54,6 +54,9 @@ struct sgw_system {
     double2* d_beta = nullptr;
     double* d_dkb = nullptr;
     double2* d_psi = nullptr;
+    float2* d_kin_dd = nullptr;  // float-float mirrors of T_G, beta_p(G), psi_v(G)
+    float4* d_beta_dd = nullptr;
+    float4* d_psi_dd = nullptr;
     int* d_lut = nullptr;
     void* d_ws = nullptr;        // solver workspace, grown on demand
     size_t ws_bytes = 0;
@@ -186,6 +189,9 @@ void free_system(sgw_system* s) {
     cudaFree(s->d_beta);
     cudaFree(s->d_dkb);
     cudaFree(s->d_psi);
+    cudaFree(s->d_kin_dd);
+    cudaFree(s->d_beta_dd);
+    cudaFree(s->d_psi_dd);
     cudaFree(s->d_lut);
     cudaFree(s->d_ws);
     delete s;
@@ -368,6 +374,8 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     if (e == cudaSuccess) e = cudaMemcpy(s->d_miller, d_mil, sizeof(int) * 3 * npw, cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_kin, sizeof(double) * npw);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_kin, d_kin, sizeof(double) * npw, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_kin_dd, sizeof(float2) * npw);
+    if (e == cudaSuccess) e = launch_to_dd(s->d_kin, npw, s->d_kin_dd, 0);
     cleanup_tmp();
     if (e != cudaSuccess) {
         free_system(s);
@@ -453,6 +461,10 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
         }
         e = cudaMalloc(&s->d_beta, sizeof(double2) * (size_t)nproj * npw);
         if (e == cudaSuccess) e = launch_beta(ba, nproj, s->d_miller, npw, s->d_beta, 0);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_beta_dd, sizeof(float4) * (size_t)nproj * npw);
+        if (e == cudaSuccess)
+            e = launch_to_dd(reinterpret_cast<const double*>(s->d_beta), 2 * (size_t)nproj * npw,
+                             reinterpret_cast<float2*>(s->d_beta_dd), 0);
         if (e != cudaSuccess) {
             free_system(s);
             return cuda_fail(e, "projector kernel");
@@ -503,12 +515,15 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     P.vloc = s->d_vloc;
     P.vloc_dd = s->d_vloc_dd;
     P.kin = s->d_kin;
+    P.kin_dd = s->d_kin_dd;
     P.twid = s->d_twid;
     P.nproj = nproj;
     P.beta = s->d_beta;
+    P.beta_dd = s->d_beta_dd;
     P.dkb = s->d_dkb;
     P.nocc = 0;
     P.psi = nullptr;
+    P.psi_dd = nullptr;
     P.inv_nbox = 1.0 / (double)nbox;
     if (apply_smem_bytes(P) > max_optin_smem()) {
         char buf[200];
@@ -580,12 +595,28 @@ sgw_status sgw_set_occupied(sgw_system* s, int n_occ, const void* psi_v, const d
             return fail(SGW_EINVAL, buf);
         }
     }
+    float4* d_new_dd = nullptr;
+    if (n_occ > 0) {
+        cudaError_t e = cudaMalloc(&d_new_dd, sizeof(float4) * (size_t)n_occ * s->npw);
+        if (e == cudaSuccess)
+            e = launch_to_dd(reinterpret_cast<const double*>(d_new), 2 * (size_t)n_occ * s->npw,
+                             reinterpret_cast<float2*>(d_new_dd), 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cudaFree(d_new);
+            cudaFree(d_new_dd);
+            return cuda_fail(e, "psi_v float-float copy");
+        }
+    }
     cudaFree(s->d_psi);
+    cudaFree(s->d_psi_dd);
     s->d_psi = d_new;
+    s->d_psi_dd = d_new_dd;
     s->nocc = n_occ;
     s->eps.assign(eps_v, eps_v + n_occ);
     s->plan.nocc = n_occ;
     s->plan.psi = d_new;
+    s->plan.psi_dd = d_new_dd;
     if (apply_smem_bytes(s->plan) > max_optin_smem()) return fail(SGW_EUNSUPPORTED, "too many occupied states");
     return SGW_OK;
 }
@@ -641,7 +672,7 @@ static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const dou
     int grid = 0;
     SGW_CUDA(resident_grid(apply_kernel_ptr(), apply_smem_bytes(s->plan), &grid), "apply occupancy");
     grid = std::min(grid, nvec);
-    const size_t scratch = sizeof(double2) * (size_t)grid * s->npw;
+    const size_t scratch = 3 * sizeof(double2) * (size_t)grid * s->npw;
     const size_t zb = project ? sizeof(double2) * nvec : 0;
     if ((r = ensure_ws(s, scratch + zb + 256)) != SGW_OK) return r;
     double2* d_scr = (double2*)s->d_ws;

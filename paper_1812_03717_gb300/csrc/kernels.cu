@@ -523,12 +523,14 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
     int* kc = reinterpret_cast<int*>(smem + off); off = align16(off + ns * 4);
     int* st = reinterpret_cast<int*>(smem + off);
 
-    double2* V = A.basis + (size_t)blockIdx.x * (maxk + 1) * npw;
+    using C = typename Ar::C;
+    C* V = reinterpret_cast<C*>(A.basis) + (size_t)blockIdx.x * (maxk + 1) * npw;
     double* ab = A.ab + (size_t)blockIdx.x * 2 * (maxk + 1);     // alpha[0..maxk), beta[0..maxk]
     double* al = ab;
     double* be = ab + (maxk + 1);
     double2* Ysc = A.ysc + (size_t)blockIdx.x * 2 * maxk * ns;   // [maxk][ns] y, [maxk][ns] l
     double2* Lsc = Ysc + (size_t)maxk * ns;
+    C* Yc = reinterpret_cast<C*>(Ysc);                          // y in the policy's format (same slots)
 
     for (;;) {
         __syncthreads();
@@ -539,24 +541,26 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
         const double2* rhs = A.rhs + (size_t)r * npw;
         double2* X = A.x + (size_t)r * ns * npw;
 
-        // b = -P_c rhs into V[0], beta_1 = |b|
+        // b = -P_c rhs (FP64), beta_1 = |b|, V[0] = b / beta_1 in the policy's format
         block_dots(P.psi, P.nocc, npw, rhs, npw, red, coef);
         {
             double2 acc[1] = {cz()};
             for (int g = tid; g < npw; g += nt) {
                 double2 h = rhs[g];
                 for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
-                const double2 b = make_double2(-h.x, -h.y);
-                V[g] = b;
-                acc[0].x += cabs2(b);
+                acc[0].x += cabs2(h);
             }
             block_sum<1>(acc, red, s_dot);
         }
         const double b1 = sqrt(s_dot[0].x);
         const bool zero = !(b1 > 0.0), bad = !isfinite(b1);
         {
-            const double inv = (zero || bad) ? 0.0 : 1.0 / b1;
-            for (int g = tid; g < npw; g += nt) V[g] = cscal(V[g], inv);
+            const double inv = (zero || bad) ? 0.0 : -1.0 / b1;
+            for (int g = tid; g < npw; g += nt) {
+                double2 h = rhs[g];
+                for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
+                V[g] = Ar::from_d(cscal(h, inv));
+            }
         }
         for (int j = tid; j < ns; j += nt) {
             zsh[j] = make_double2(A.e_ref[r] + A.omega[j], A.eta);
@@ -573,35 +577,39 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
         __syncthreads();
         int k = 0;
         while (s_nact > 0 && k < maxk) {
-            double2* vk = V + (size_t)k * npw;
-            double2* w = V + (size_t)(k + 1) * npw;
+            C* vk = V + (size_t)k * npw;
+            C* w = V + (size_t)(k + 1) * npw;
             apply_h_block<Ar>(P, smem, vk, w, cz(), APPLY_PROJ_OUT);
             const double bk = be[k];
-            const double2* vkm = k > 0 ? V + (size_t)(k - 1) * npw : nullptr;
+            const C* vkm = k > 0 ? V + (size_t)(k - 1) * npw : nullptr;
             {
-                double2 acc[1] = {cz()};
+                const typename Ar::R bkr = Ar::real(bk);
+                C acc = Ar::zero();
                 for (int g = tid; g < npw; g += nt) {
-                    double2 h = w[g];
-                    if (vkm) h = make_double2(h.x - bk * vkm[g].x, h.y - bk * vkm[g].y);
+                    C h = w[g];
+                    if (vkm) h = Ar::sub(h, Ar::scalr(vkm[g], bkr));
                     w[g] = h;
-                    acc[0] = cadd(acc[0], cmulc(vk[g], h));
+                    acc = Ar::add(acc, Ar::mul(Ar::conj(vk[g]), h));
                 }
-                block_sum<1>(acc, red, s_dot);
+                double2 a2[1] = {Ar::to_d(acc)};
+                block_sum<1>(a2, red, s_dot);
             }
             const double a = s_dot[0].x;
             {
-                double2 acc[1] = {cz()};
+                const typename Ar::R ar = Ar::real(a);
+                C acc = Ar::zero();
                 for (int g = tid; g < npw; g += nt) {
-                    const double2 h = make_double2(w[g].x - a * vk[g].x, w[g].y - a * vk[g].y);
+                    const C h = Ar::sub(w[g], Ar::scalr(vk[g], ar));
                     w[g] = h;
-                    acc[0].x += cabs2(h);
+                    acc = Ar::acc_norm(acc, h);
                 }
-                block_sum<1>(acc, red, s_dot);
+                double2 a2[1] = {Ar::to_d(acc)};
+                block_sum<1>(a2, red, s_dot);
             }
             const double bn = sqrt(s_dot[0].x);
             {
-                const double inv = bn > 0.0 ? 1.0 / bn : 0.0;
-                for (int g = tid; g < npw; g += nt) w[g] = cscal(w[g], inv);
+                const typename Ar::R inv = Ar::real(bn > 0.0 ? 1.0 / bn : 0.0);
+                for (int g = tid; g < npw; g += nt) w[g] = Ar::scalr(w[g], inv);
             }
             if (tid == 0) {
                 al[k] = a;
@@ -673,23 +681,27 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
             for (int i = kj; i < K; ++i) Ysc[(size_t)i * ns + j] = cz();
         }
         __syncthreads();
+        // y in the policy's format (each slot converted in place by the thread of its shift)
+        for (int j = tid; j < ns; j += nt)
+            for (int i = 0; i < K; ++i) Yc[(size_t)i * ns + j] = Ar::from_d(Ysc[(size_t)i * ns + j]);
+        __syncthreads();
         // x_j = V y_j, shifts in tiles of 8
         for (int j0 = 0; j0 < ns; j0 += 8) {
             const int cnt = min(8, ns - j0);
             for (int g = tid; g < npw; g += nt) {
-                double2 acc[8];
+                C acc[8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc[t] = cz();
+                for (int t = 0; t < 8; ++t) acc[t] = Ar::zero();
                 for (int i = 0; i < K; ++i) {
-                    const double2 v = V[(size_t)i * npw + g];
-                    const double2* yr = Ysc + (size_t)i * ns + j0;
+                    const C v = V[(size_t)i * npw + g];
+                    const C* yr = Yc + (size_t)i * ns + j0;
 #pragma unroll
                     for (int t = 0; t < 8; ++t)
-                        if (t < cnt) acc[t] = cfma(yr[t], v, acc[t]);
+                        if (t < cnt) acc[t] = Ar::add(acc[t], Ar::mul(yr[t], v));
                 }
 #pragma unroll
                 for (int t = 0; t < 8; ++t)
-                    if (t < cnt) X[(size_t)(j0 + t) * npw + g] = acc[t];
+                    if (t < cnt) X[(size_t)(j0 + t) * npw + g] = Ar::to_d(acc[t]);
             }
         }
         for (int j = tid; j < ns; j += nt) {
@@ -707,30 +719,33 @@ template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, const double2* __restrict__ x,
                                                             double2* __restrict__ y, const double2* __restrict__ z,
                                                             int project, double2* __restrict__ scratch) {
+    using C = typename Ar::C;
     extern __shared__ __align__(16) unsigned char smem[];
     load_twiddles<Ar>(P, smem);
     const ApplySmem L = apply_smem_layout(P);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
     const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
-    double2* xs = scratch + (size_t)blockIdx.x * npw;
+    double2* xs = scratch + (size_t)blockIdx.x * 3 * npw;     // P_c x (FP64)
+    C* xa = reinterpret_cast<C*>(xs + npw);                    // input in the policy's format
+    C* ya = reinterpret_cast<C*>(xs + 2 * npw);                // output in the policy's format
     for (int v = blockIdx.x; v < nvec; v += gridDim.x) {
         const double2* xv = x + (size_t)v * npw;
         double2* yv = y + (size_t)v * npw;
-        if (!project) {
-            apply_h_block<Ar>(P, smem, xv, yv, cz(), 0);
-            continue;
-        }
-        block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
-        for (int g = tid; g < npw; g += nt) {
-            double2 h = xv[g];
-            for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
-            xs[g] = h;
+        if (project) {
+            block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
+            for (int g = tid; g < npw; g += nt) {
+                double2 h = xv[g];
+                for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
+                xa[g] = Ar::from_d(h);
+            }
+        } else {
+            for (int g = tid; g < npw; g += nt) xa[g] = Ar::from_d(xv[g]);
         }
         __syncthreads();
-        apply_h_block<Ar>(P, smem, xs, yv, cz(), APPLY_PROJ_OUT);
-        const double2 zz = z[v];
-        for (int g = tid; g < npw; g += nt) yv[g] = csub(yv[g], cmul(zz, xv[g]));
+        apply_h_block<Ar>(P, smem, xa, ya, cz(), project ? APPLY_PROJ_OUT : 0);
+        const double2 zz = project ? z[v] : cz();
+        for (int g = tid; g < npw; g += nt) yv[g] = csub(Ar::to_d(ya[g]), cmul(zz, xv[g]));
         __syncthreads();
     }
 }

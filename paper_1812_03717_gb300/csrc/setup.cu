@@ -3,6 +3,8 @@
 // gather and the overlap matrix of the occupied states.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "sgw_internal.cuh"
 #include "setup.h"
 
@@ -177,6 +179,22 @@ cudaError_t launch_rhs(const RhsArgs& a, const int* miller_kq, int npw_kq, const
     if (n_pert == 0 || npw_kq == 0) return cudaSuccess;
     rhs_kernel<<<dim3((npw_kq + 255) / 256, n_pert), 256, 0, st>>>(a, miller_kq, npw_kq, lut_k, psi_k, npw_k, gp,
                                                                     n_v, n_pert, rhs);
+    return cudaGetLastError();
+}
+// Each FP64 value as the float pair (hi, lo) with hi = fl32(x) and lo = fl32(x - hi); a
+// double2 array converts into the (re.hi, re.lo, im.hi, im.lo) layout of the float-float policy.
+__global__ void to_dd_kernel(const double* __restrict__ src, size_t n, float2* __restrict__ dst) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double x = src[i];
+        const float h = __double2float_rn(x);
+        dst[i] = make_float2(h, __double2float_rn(x - (double)h));
+    }
+}
+
+cudaError_t launch_to_dd(const double* src, size_t n, float2* dst, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+    to_dd_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, n, dst);
     return cudaGetLastError();
 }
 cudaError_t launch_gram(const double2* psi, int nocc, int npw, double2* S, cudaStream_t st) {

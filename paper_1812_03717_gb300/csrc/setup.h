@@ -37,6 +37,7 @@ cudaError_t launch_twiddles(const int dims[3], double2* tw, cudaStream_t st);
 cudaError_t launch_rhs(const RhsArgs& a, const int* miller_kq, int npw_kq, const int* lut_k, const double2* psi_k,
                        int npw_k, const int* gp, int n_v, int n_pert, double2* rhs, cudaStream_t st);
 cudaError_t launch_gram(const double2* psi, int nocc, int npw, double2* S, cudaStream_t st);
+cudaError_t launch_to_dd(const double* src, size_t n, float2* dst, cudaStream_t st);
 
 // --- hot path (kernels.cu)
 

@@ -54,6 +54,10 @@ struct Plan {
     int nocc;
     const double2* psi;      // [nocc][npw]
     double inv_nbox;         // 1 / (n1 n2 n3)
+    // float-float mirrors (hi, lo) used by the float-float arithmetic policy
+    const float4* psi_dd;    // [nocc][npw]
+    const float4* beta_dd;   // [nproj][npw]
+    const float2* kin_dd;    // [npw]
 };
 
 // Shared-memory carve-up of an H application (byte offsets from the dynamic base).
@@ -177,6 +181,15 @@ struct ArF64 {
     static __device__ __forceinline__ C zero() { return cz(); }
     // complex times real potential sample
     static __device__ __forceinline__ C mulv(C a, const double* v, const float2*, size_t i) { return cscal(a, v[i]); }
+    // real scalars and reciprocal-space data in this policy's format
+    using R = double;
+    static __device__ __forceinline__ R real(double x) { return x; }
+    static __device__ __forceinline__ C scalr(C a, R s) { return cscal(a, s); }
+    static __device__ __forceinline__ C psi(const Plan& P, size_t i) { return P.psi[i]; }
+    static __device__ __forceinline__ C beta(const Plan& P, size_t i) { return P.beta[i]; }
+    static __device__ __forceinline__ C kinx(const Plan& P, int g, C x) { return cscal(x, P.kin[g]); }
+    // |a|^2 accumulated into the real part of acc
+    static __device__ __forceinline__ C acc_norm(C acc, C a) { return make_double2(acc.x + cabs2(a), acc.y); }
 };
 
 struct dd {
@@ -237,6 +250,19 @@ struct ArDF {
         const dd c{t.x, t.y};
         return mk(dd_mul(re(a), c), dd_mul(im(a), c));
     }
+    using R = dd;
+    static __device__ __forceinline__ R real(double x) { return dd_from(x); }
+    static __device__ __forceinline__ C scalr(C a, R s) { return mk(dd_mul(re(a), s), dd_mul(im(a), s)); }
+    static __device__ __forceinline__ C psi(const Plan& P, size_t i) { return P.psi_dd[i]; }
+    static __device__ __forceinline__ C beta(const Plan& P, size_t i) { return P.beta_dd[i]; }
+    static __device__ __forceinline__ C kinx(const Plan& P, int g, C x) {
+        const float2 t = P.kin_dd[g];
+        return scalr(x, dd{t.x, t.y});
+    }
+    static __device__ __forceinline__ C acc_norm(C acc, C a) {
+        const dd m = dd_add(dd_mul(re(a), re(a)), dd_mul(im(a), im(a)));
+        return mk(dd_add(re(acc), m), im(acc));
+    }
 };
 
 // Real constants of the small DFTs as (double, float hi, float lo).
@@ -251,6 +277,37 @@ SGW_CONST(kS51, 0.95105651629515357212)   // sin(2 pi / 5)
 SGW_CONST(kS52, 0.58778525229247312917)   // sin(4 pi / 5)
 SGW_CONST(kHalf, 0.5)
 #undef SGW_CONST
+
+// out[v] = sum_g conj(src_v[g]) x[g] for v < nv, with src the occupied states (which = 0) or
+// the projectors (which = 1) in the policy's format; per-thread sums in the policy's
+// arithmetic, the block reduction in FP64.  out must hold nv rounded up to 8.
+template <class Ar, int WHICH>
+__device__ __forceinline__ void block_dots_ar(const Plan& P, int nv, const typename Ar::C* x, double2* red,
+                                              double2* out) {
+    using C = typename Ar::C;
+    const int n = P.npw;
+    for (int v0 = 0; v0 < nv; v0 += 8) {
+        C acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = Ar::zero();
+        const int cnt = min(8, nv - v0);
+        for (int g = threadIdx.x; g < n; g += blockDim.x) {
+            const C xv = x[g];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i < cnt) {
+                    const size_t o = (size_t)(v0 + i) * n + g;
+                    const C s = WHICH == 0 ? Ar::psi(P, o) : Ar::beta(P, o);
+                    acc[i] = Ar::add(acc[i], Ar::mul(Ar::conj(s), xv));
+                }
+            }
+        }
+        double2 a2[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a2[i] = Ar::to_d(acc[i]);
+        block_sum<8>(a2, red, out + v0);
+    }
+}
 
 // -------------------------------------------------------------- shared-memory FFT lines
 
@@ -368,18 +425,19 @@ __device__ __forceinline__ void load_twiddles(const Plan& P, unsigned char* smem
     __syncthreads();
 }
 
-// y = H x  (+ options) for one vector, by the whole CTA.  x and y are global and must not
-// alias.  Steps: KB coefficients c_p = D_p <beta_p|x>; scatter x into the sticks; inverse
-// FFT along z on the sticks; per z-plane: scatter the plane, inverse FFT along y (only
-// the x-columns that hold sticks) and x, multiply by V(r), forward FFT along x and y,
-// gather back into the sticks; forward FFT along z; gather the sphere, scale by 1/N^3 and
-// add T_G x_G + sum_p c_p beta_p(G).  The FFT part runs in the arithmetic of Ar; the
-// reciprocal-space parts (kinetic, projectors, P_c) in FP64.
+// y = H x  (+ options) for one vector, by the whole CTA; x and y are vectors of the
+// policy's type (global, must not alias).  Steps: KB coefficients c_p = <beta_p|x>; scatter
+// x into the sticks; inverse FFT along z on the sticks; per group of z-planes: scatter the
+// planes, inverse FFT along y (only the x-columns that hold sticks) and x, multiply by V(r),
+// forward FFT along x and y, gather back into the sticks; forward FFT along z; gather the
+// sphere, scale by 1/N^3 and add T_G x_G + sum_p D_p c_p beta_p(G); optionally project with
+// P_c and subtract z x.  All vector arithmetic in the policy's arithmetic; the block
+// reductions of the projections in FP64.
 // x and y may have been written earlier in the same kernel, so they are read through the
 // coherent path (no __restrict__ / read-only cache).
 template <class Ar>
-__device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, const double2* x, double2* y,
-                                           double2 zsh, int mode) {
+__device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, const typename Ar::C* x,
+                                           typename Ar::C* y, double2 zsh, int mode) {
     using C = typename Ar::C;
     const ApplySmem L = apply_smem_layout(P);
     const C* tw = reinterpret_cast<const C*>(smem + L.tw);
@@ -387,20 +445,25 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
     C* plane = reinterpret_cast<C*>(smem + L.plane);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    C* coefc = reinterpret_cast<C*>(smem + L.coef);   // the same slots, in the policy's format
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3, npw = P.npw, nst = P.nstick;
     const C* tw1 = tw;
     const C* tw2 = tw + n1;
     const C* tw3 = tw + n1 + n2;
 
-    // non-local: c_p = <beta_p|x>
-    if (P.nproj > 0) block_dots(P.beta, P.nproj, npw, x, npw, red, coef);
+    // non-local: D_p <beta_p|x>, kept in the policy's format
+    if (P.nproj > 0) {
+        block_dots_ar<Ar, 1>(P, P.nproj, x, red, coef);
+        if (tid < P.nproj) coefc[tid] = Ar::from_d(cscal(coef[tid], P.dkb[tid]));
+        __syncthreads();
+    }
 
     // sphere -> sticks
     const int n3p = P.n3p;
     for (int i = tid; i < nst * n3p; i += nt) sticks[i] = Ar::zero();
     __syncthreads();
-    for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = Ar::from_d(x[g]);
+    for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = x[g];
     __syncthreads();
     fft_lines<Ar, +1>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
 
@@ -431,25 +494,30 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
     fft_lines<Ar, -1>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
 
     // gather + kinetic + non-local
-    for (int g = tid; g < npw; g += nt) {
-        const double2 xv = x[g];
-        double2 h = cscal(Ar::to_d(sticks[P.g2s[g]]), P.inv_nbox);
-        h = make_double2(fma(P.kin[g], xv.x, h.x), fma(P.kin[g], xv.y, h.y));
-        for (int p = 0; p < P.nproj; ++p) h = cfma(cscal(coef[p], P.dkb[p]), P.beta[(size_t)p * npw + g], h);
-        y[g] = h;
+    {
+        const typename Ar::R invn = Ar::real(P.inv_nbox);
+        for (int g = tid; g < npw; g += nt) {
+            C h = Ar::add(Ar::scalr(sticks[P.g2s[g]], invn), Ar::kinx(P, g, x[g]));
+            for (int p = 0; p < P.nproj; ++p) h = Ar::add(h, Ar::mul(coefc[p], Ar::beta(P, (size_t)p * npw + g)));
+            y[g] = h;
+        }
     }
     __syncthreads();
 
     if (mode & APPLY_PROJ_OUT) {
-        block_dots(P.psi, P.nocc, npw, y, npw, red, coef);
+        block_dots_ar<Ar, 0>(P, P.nocc, y, red, coef);
+        for (int v = tid; v < P.nocc; v += nt) coefc[v] = Ar::from_d(coef[v]);
+        __syncthreads();
+        const C zc = Ar::from_d(zsh);
         for (int g = tid; g < npw; g += nt) {
-            double2 h = y[g];
-            for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
-            if (mode & APPLY_SUB_Z) h = csub(h, cmul(zsh, x[g]));
+            C h = y[g];
+            for (int v = 0; v < P.nocc; ++v) h = Ar::sub(h, Ar::mul(coefc[v], Ar::psi(P, (size_t)v * npw + g)));
+            if (mode & APPLY_SUB_Z) h = Ar::sub(h, Ar::mul(zc, x[g]));
             y[g] = h;
         }
     } else if (mode & APPLY_SUB_Z) {
-        for (int g = tid; g < npw; g += nt) y[g] = csub(y[g], cmul(zsh, x[g]));
+        const C zc = Ar::from_d(zsh);
+        for (int g = tid; g < npw; g += nt) y[g] = Ar::sub(y[g], Ar::mul(zc, x[g]));
     }
     __syncthreads();
 }

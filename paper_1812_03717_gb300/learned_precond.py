@@ -58,12 +58,40 @@ def _system(P, inst, ik=0):
     return skq, rhs
 
 
+def pairs_rows(s, rp, e, om, eta, tol=1e-8, deltas=DELTAS, stats=None):
+    """Training rows of the pairs (rp[i], e[i] + om[i] + i eta) of system s: each pair is
+    solved per shift with the plain scaling and with the Jacobi scaling at every floor; the
+    fastest defines its targets."""
+    _, rep, _ = s.solve_pershift(rp, e, om, eta, tol=tol, precond="plain")
+    counts = [rep["matvecs"].astype(np.int64)]
+    for dl in deltas:
+        _, rep, _ = s.solve_pershift(rp, e, om, eta, tol=tol, precond="jacobi", delta=dl)
+        mv = rep["matvecs"].astype(np.int64)
+        mv[rep["status"] != 0] = 1 << 30
+        counts.append(mv)
+    counts = np.stack(counts)                         # [1 + n_delta][pairs]
+    best = counts.argmin(axis=0)
+    best_delta = np.where(best == 0, 0.0, np.asarray((0.0,) + tuple(deltas))[best])
+    f, t = s.training_rows(rp, e, om, eta, best_delta)
+    if stats is not None:
+        stats["pairs"] += len(e)
+        stats["plain_mv"] += int(counts[0].sum())
+        stats["best_mv"] += int(counts.min(axis=0).sum())
+        for b in best:
+            stats["wins"][int(b)] += 1
+    return f, t
+
+
+def new_stats(deltas=DELTAS):
+    return {"pairs": 0, "plain_mv": 0, "best_mv": 0, "wins": [0] * (len(deltas) + 1)}
+
+
 def training_set(P, seeds, pairs_per_seed=32, tol=1e-8, deltas=DELTAS, make=None):
     """Rows (feats, targets) on the GPU from per-shift solves on the given seeds."""
     import torch
     import instances as I
     make = make or I.fcc_perturbed
-    feats, targets, stats = [], [], {"pairs": 0, "plain_mv": 0, "best_mv": 0, "wins": [0] * (len(deltas) + 1)}
+    feats, targets, stats = [], [], new_stats(deltas)
     for seed in seeds:
         inst = make(seed)
         s, rhs = _system(P, inst)
@@ -71,24 +99,9 @@ def training_set(P, seeds, pairs_per_seed=32, tol=1e-8, deltas=DELTAS, make=None
         rp = rhs[torch.as_tensor(r, device=rhs.device)].contiguous()
         e = inst.e_ref(0)[r]
         om = inst.omega[j]
-        _, rep, _ = s.solve_pershift(rp, e, om, inst.eta, tol=tol, precond="plain")
-        counts = [rep["matvecs"].astype(np.int64)]
-        for dl in deltas:
-            _, rep, _ = s.solve_pershift(rp, e, om, inst.eta, tol=tol, precond="jacobi", delta=dl)
-            mv = rep["matvecs"].astype(np.int64)
-            mv[rep["status"] != 0] = 1 << 30
-            counts.append(mv)
-        counts = np.stack(counts)                     # [1 + n_delta][pairs]
-        best = counts.argmin(axis=0)
-        best_delta = np.where(best == 0, 0.0, np.asarray((0.0,) + tuple(deltas))[best])
-        f, t = s.training_rows(rp, e, om, inst.eta, best_delta)
+        f, t = pairs_rows(s, rp, e, om, inst.eta, tol, deltas, stats)
         feats.append(f)
         targets.append(t)
-        stats["pairs"] += len(r)
-        stats["plain_mv"] += int(counts[0].sum())
-        stats["best_mv"] += int(counts.min(axis=0).sum())
-        for b in best:
-            stats["wins"][int(b)] += 1
         s.close()
     return torch.cat(feats), torch.cat(targets), stats
 
