@@ -22,7 +22,10 @@ What it computes, by plain definition (no blocking, fusion or reordering):
   shift;
 * the sum over all unoccupied eigenstates of the finite basis, which equals that
   solution (used to pin it on tiny bases);
-* the true residual and the a-posteriori error certificate |r| / (eta |dpsi|).
+* the true residual and the a-posteriori error certificate |r| / (eta |dpsi|);
+* columns of the Green's function of Eq. 2-3, G(z) = (z - H)^-1 (no projector), by dense
+  LU per shift and by the spectral sum over all eigenstates, with their residual and
+  certificate |r| / (|Im z| |g|).
 
 Each function cites the passage of the paper it restates.
 """
@@ -235,3 +238,63 @@ def residual(h, psi_v, rhs, e_ref, omega, eta, dpsi):
             rel[r, j] = rn / bn if bn > 0 else 0.0
             cert[r, j] = rn / (eta * xn) if xn > 0 else 0.0
     return rel, cert
+
+
+# ------------------------------------------------------- Eq. 2-3: the Green's function
+
+def unit_columns(n, cols):
+    """e_{G'} for G' = cols, as rows [ncol][n]."""
+    e = np.zeros((len(cols), n), dtype=np.complex128)
+    e[np.arange(len(cols)), np.asarray(cols, dtype=np.int64)] = 1.0
+    return e
+
+
+def green_columns(h, cols, z):
+    """g[c][j] = column cols[c] of G(z_j), i.e. the solution of (H - z_j) g = -delta_{G G'}
+    (Eq. 2 with the operator of Eq. 3: no projector), by one dense LU per shift; z_j is
+    complex with Im z_j != 0 (its sign is the caller's time-ordering choice)."""
+    n = h.shape[0]
+    e = unit_columns(n, cols)
+    out = np.zeros((len(cols), len(z), n), dtype=np.complex128)
+    for j, zj in enumerate(z):
+        lu = scipy.linalg.lu_factor(h - zj * np.eye(n), check_finite=False)
+        out[:, j, :] = scipy.linalg.lu_solve(lu, -e.T, check_finite=False).T
+    return out
+
+
+def green_sum_over_states(h, cols, z):
+    """The spectral representation G(z) = sum_n psi_n psi_n^H / (z - eps_n) over every
+    eigenstate of the finite basis (equal to green_columns by the spectral theorem)."""
+    w, v = np.linalg.eigh(h)
+    cols = np.asarray(cols, dtype=np.int64)
+    out = np.zeros((len(cols), len(z), h.shape[0]), dtype=np.complex128)
+    for j, zj in enumerate(z):
+        out[:, j, :] = ((v / (zj - w)) @ v[cols].conj().T).T
+    return out
+
+
+def green_residual(h, cols, z, g):
+    """rel_res = |-e - (H - z) g| / |e| and the certificate |r| / (|Im z| |g|): H - z is normal
+    with every eigenvalue at distance >= |Im z| from 0, so |g - g*| / |g| <= cert."""
+    n = h.shape[0]
+    e = unit_columns(n, cols)
+    rel = np.zeros((len(cols), len(z)))
+    cert = np.zeros((len(cols), len(z)))
+    for j, zj in enumerate(z):
+        a = h - zj * np.eye(n)
+        for c in range(len(cols)):
+            res = -e[c] - a @ g[c, j]
+            rn = np.linalg.norm(res)
+            xn = np.linalg.norm(g[c, j])
+            rel[c, j] = rn
+            cert[c, j] = rn / (abs(zj.imag) * xn) if xn > 0 else 0.0
+    return rel, cert
+
+
+def time_ordered_shifts(omega, mu, eta):
+    """z_j = omega_j + i eta sgn(omega_j - mu): the retarded side above the chemical potential
+    mu and the advanced side below it (the reading of the time-ordering choice of Eq. 2)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    if np.any(omega == mu):
+        raise ValueError("omega_j = mu has no time-ordering sign")
+    return omega + 1j * eta * np.sign(omega - mu)
