@@ -66,7 +66,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070   # 80.5 TFLOP/s
 # DRAM bytes (read + write) per 512-right-hand-side launch of the multishift kernel, from the
 # ncu captures in profiles/ (16 right-hand sides, scaled by right-hand sides); None once the
 # kernel has changed since the capture.
-TRAFFIC_PER_LAUNCH = {"df32": None, "fp64": 37.0e9}
+TRAFFIC_PER_LAUNCH = {"df32": 40.9e9, "fp64": None}
 
 
 def radix_plan(n):
@@ -347,6 +347,13 @@ def run_ours(args):
     res = {v: timed(v) for v in variants}
     head = res[variants[0]]
 
+    # Green's-function columns (Eq. 2-3) on one k-point's basis: every plane-wave column at 64
+    # time-ordered shifts around the chemical potential, one launch per run
+    green = None
+    if not args.no_green:
+        kg = units_for_step(0, ws, rank, nk)
+        green = measure_green(P, inst, kg, jobs[kg], variants[0], stream)
+
     # per-shift solves of sampled pairs of this workload: plain vs learned diagonal preconditioner
     learned = None
     if not args.no_learned:
@@ -440,12 +447,72 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws} (k-points sharded)", "generate_s": round(t_gen, 1)},
         "quality": head["quality"], "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e,
         "clocks": head["clocks"], "gpu_launches": head["gpu_launches"], "learned_preconditioner": learned,
+        "green_function": green,
         "variants": {v: {k: res[v][k] for k in ("value", "ms_per_step", "kernel_ms_per_launch", "roofline", "quality")}
                      for v in variants},
     }
     if "fp64" in res and variants[0] != "fp64":
         line["speedup_vs_plain_fp64"] = head["value"] / res["fp64"]["value"]
     print(json.dumps(line), flush=True)
+
+
+GREEN_SPAN_EV = 30.0
+HA_EV = 27.211386245988        # eV per Hartree (CODATA 2018)
+
+
+def green_shifts(inst, kp, nz=64, span_ev=GREEN_SPAN_EV):
+    """z_j = omega_j + i eta sgn(omega_j - mu), omega_j = mu + linspace(-span, span, nz) eV, mu in
+    the gap above the occupied states of the basis."""
+    mu = float(kp.eps_kq[-1]) + 0.5 * float(kp.gap_kq)
+    om = mu + np.linspace(-span_ev, span_ev, nz) / HA_EV
+    return om + 1j * inst.eta * np.sign(om - mu), mu
+
+
+def measure_green(P, inst, ik, job, precision, stream, runs=1):
+    """All columns of G(z) for one k-point's basis at 64 time-ordered shifts: one untimed run,
+    then `runs` runs timed with CUDA events; returns a dict for the JSON line."""
+    import torch
+    s = job["sys"]
+    z, mu = green_shifts(inst, inst.kpoints[ik])
+    cols = np.arange(s.n_pw)
+    out = torch.empty((len(cols), len(z), s.n_pw), dtype=torch.complex128, device="cuda")
+    s.solve_green(cols, z, tol=1e-10, precision=precision, out=out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = []
+    for _ in range(runs):
+        _, rep, ok = s.solve_green(cols, z, tol=1e-10, precision=precision, out=out)
+        reps.append(rep)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / runs
+    rep = reps[-1]
+    plan = job["plan"]
+    steps = rep["matvecs"].max(axis=1)
+    if precision == "fp64":
+        work = solver_fp64_flops(plan, rep["matvecs"]) / 1e12
+        roof = {"bound": "alu", "achieved": work / (ms / 1e3), "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "kernel": "lanczos_solve_kernel<ArF64>"}
+    else:
+        work = solver_df32_ops(plan, rep["matvecs"]) / 1e12
+        roof = {"bound": "alu", "achieved": work / (ms / 1e3), "peak": FP32_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "kernel": "lanczos_solve_kernel<ArDF>"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["time"] = "whole call (multishift kernel + FP64 residual check)"
+    roof["traffic"] = None
+    npairs = rep["status"].size
+    del out
+    return {"metric": "Green's-function (column x z) solves/s at 1e-10 residual", "value": npairs / (ms / 1e3),
+            "unit": "solves/s", "ms_per_run": ms, "runs": runs, "precision": precision,
+            "workload": f"all {len(cols)} plane-wave columns G' of G(z) = (z - H)^-1 on the k+q basis of k-point {ik}, "
+                        f"{len(z)} shifts omega = mu + linspace(-{GREEN_SPAN_EV:g}, {GREEN_SPAN_EV:g}) eV, "
+                        f"Im z = eta sgn(omega - mu), eta 0.1 eV",
+            "quality": {"pairs": int(npairs), "converged": int((rep["status"] == 0).sum()),
+                        "max_true_rel_res": float(rep["rel_res"].max()), "max_cert": float(rep["cert"].max()),
+                        "lanczos_steps_median": float(np.median(steps)), "lanczos_steps_max": int(steps.max())},
+            "roofline": roof, "gpu_launches": int(rep["launches"][0])}
 
 
 def run_profile_case(args):
@@ -484,6 +551,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--variants", default="df32,fp64",
                     help="comma list of FFT precisions to time; the first is the headline")
+    ap.add_argument("--no-green", action="store_true", help="skip the Green's-function measurement")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="solve this many right-hand sides of k-point 0 once and exit (for ncu captures)")
     args = ap.parse_args()

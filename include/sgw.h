@@ -184,6 +184,25 @@ sgw_status sgw_solve_shifted(sgw_system* sys, int nrhs, const void* rhs, const d
                              int nomega, const double* omega, double eta, double tol,
                              const sgw_solve_opts* opts, void* dpsi, sgw_report* report);
 
+/* Green's-function columns (Sec. 2.2, Eq. 2 with the operator of Eq. 3).  For every c < ncol
+ * and j < nz solves
+ *   (H - z_j) g[c][j] = -e_{G'},   G' = cols[c],
+ * i.e. g[c][j] is column G' of G(z_j) = (z_j - H)^{-1} in this system's plane-wave basis.
+ * There is no projector: the occupied states set by sgw_set_occupied are not used (and need
+ * not be set).  All shifts of one column share one Krylov space (the Lanczos process on the
+ * Hermitian H, as in sgw_solve_shifted), followed by the FP64 true residual and per-shift
+ * corrections of pairs above tol.
+ *   cols   [ncol] host, plane-wave indices in [0, n_pw) (else SGW_EINVAL).
+ *   z      [nz][2] host, (Re z, Im z) in Ha; Im z != 0 (else SGW_EINVAL) and of either sign
+ *          per shift: the caller chooses it (time ordering: Im z_j = eta sgn(Re z_j - mu)).
+ *   tol    residual target |-e - (H - z) g| <= tol (|e| = 1).
+ *   opts   as sgw_solve_shifted; only SGW_METHOD_LANCZOS (else SGW_EUNSUPPORTED).
+ *   g      complex [ncol][nz][n_pw] (host or device), overwritten.
+ *   report optional per-pair report [ncol][nz]; cert = |r| / (|Im z| |g|).
+ * Returns SGW_ENOCONV if any pair's true residual stays above tol (results still written). */
+sgw_status sgw_solve_green(sgw_system* sys, int ncol, const int* cols, int nz, const double* z, double tol,
+                           const sgw_solve_opts* opts, void* g, sgw_report* report);
+
 /* True FP64 residual of given solutions: for every pair
  *   r = -P_c rhs - (P_c H P_c - z) dpsi,  rel_res = |r| / |P_c rhs|,  cert = |r| / (eta |dpsi|).
  * Since P_c H P_c - z is normal with every eigenvalue at distance >= eta from 0, cert bounds

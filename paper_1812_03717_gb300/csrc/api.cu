@@ -710,23 +710,21 @@ struct Carve {
 
 }  // namespace
 
-sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const double* e_ref, int nomega,
-                             const double* omega, double eta, double tol, const sgw_solve_opts* opts, void* dpsi,
-                             sgw_report* report) {
-    g_err.clear();
-    if (!s || !rhs || !e_ref || !omega || !dpsi) return fail(SGW_EINVAL, "NULL argument");
-    if (nrhs < 0 || nomega < 1) return fail(SGW_EINVAL, "need nrhs >= 0 and nomega >= 1");
-    if (nomega > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nomega above 512");
-    if (!(eta > 0.0) || !std::isfinite(eta))
-        return fail(SGW_EINVAL, "eta must be positive (the shifted systems are singular at eta = 0)");
-    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
-    if (!finite_all(e_ref, nrhs) || !finite_all(omega, nomega)) return fail(SGW_EINVAL, "non-finite e_ref or omega");
-    if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+// The multishift solve of every (rhs, shift) pair with its FP64 true-residual check and
+// per-shift corrections: z_rj = e_ref[r] + omega[j] + i Im z_j, Im z_j = eta_s[j] when
+// eta_s (host) is given, else eta.  rhs_d and X are device buffers; plan fixes the operator
+// (P_c H P_c with the occupied states of the plan; H itself when it has none).  Returns
+// SGW_ENOCONV, with X and the report written, when a pair misses tol.
+static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const double2* rhs_d, const double* e_ref,
+                             int nomega, const double* omega, const double* eta_s, double eta, double tol,
+                             const sgw_solve_opts* opts, double2* X, sgw_report* report, cudaStream_t st) {
     const int method = opts ? opts->method : SGW_METHOD_LANCZOS;
     const int precision = opts ? opts->precision : SGW_PREC_FP64;
     const int threads = opts ? opts->threads : 0;
     if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32) return fail(SGW_EINVAL, "unknown precision");
     if (method != SGW_METHOD_LANCZOS && method != SGW_METHOD_BICGSTAB) return fail(SGW_EINVAL, "unknown method");
+    if (eta_s && method != SGW_METHOD_LANCZOS)
+        return fail(SGW_EUNSUPPORTED, "shifts with different imaginary parts need the Lanczos method");
     const int ell = opts && opts->ell ? opts->ell : 4;
     if (ell < 1 || ell > kMaxEll) return fail(SGW_EINVAL, "ell must be 1, 2, 3 or 4");
     int seed = opts ? opts->seed_index : -1;
@@ -740,27 +738,21 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     // Lanczos keeps its basis: the default budget of 4096 steps bounds its memory
     const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : (lanczos ? 4096 : 40000);
     const int max_refine = !opts || opts->max_refine == 0 ? 3 : std::max(0, opts->max_refine);
-    cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
-    if (nrhs == 0) return SGW_OK;
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
-    const int smem_main = lanczos ? lanczos_smem_bytes(s->plan, nomega) : solve_smem_bytes(s->plan, nomega);
+    const int smem_main = lanczos ? lanczos_smem_bytes(plan, nomega) : solve_smem_bytes(plan, nomega);
     if (smem_main > max_optin_smem()) return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     const size_t np = (size_t)nrhs * nomega;
-    Staged in, out;
     sgw_status r;
-    if ((r = stage_in(rhs, vb * nrhs, in, st, "rhs")) != SGW_OK) return r;
-    if ((r = stage_out(dpsi, vb * np, out, "dpsi", st)) != SGW_OK) return r;
     const int chunk = (int)std::min<size_t>(np, 4096);
     int grid = 0, grid1 = 0, grid_r = 0;
     if (lanczos) {
-        SGW_CUDA(lanczos_grid(s->plan, nomega, nrhs, threads, &grid), "solver occupancy");
-        SGW_CUDA(lanczos_grid(s->plan, 1, chunk, threads, &grid1), "solver occupancy");
+        SGW_CUDA(lanczos_grid(plan, nomega, nrhs, threads, &grid), "solver occupancy");
+        SGW_CUDA(lanczos_grid(plan, 1, chunk, threads, &grid1), "solver occupancy");
     } else {
-        SGW_CUDA(solve_grid(s->plan, nomega, nrhs, &grid), "solver occupancy");
-        SGW_CUDA(solve_grid(s->plan, 1, chunk, &grid1), "solver occupancy");
+        SGW_CUDA(solve_grid(plan, nomega, nrhs, &grid), "solver occupancy");
+        SGW_CUDA(solve_grid(plan, 1, chunk, &grid1), "solver occupancy");
     }
-    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r), "residual occupancy");
+    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(plan), &grid_r), "residual occupancy");
     grid_r = (int)std::min<size_t>(grid_r, np);
     // Krylov workspace of one launch (reused by the correction solves)
     int maxk = max_mv;
@@ -796,6 +788,8 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     const size_t o_rvec = c.take(vb * chunk);
     const size_t o_dbuf = c.take(vb * chunk);
     const size_t o_eref1 = c.take(sizeof(double) * chunk);
+    const size_t o_eta1 = c.take(sizeof(double) * chunk);
+    const size_t o_etas = c.take(sizeof(double) * nomega);
     const size_t o_zero = c.take(sizeof(double));
     const size_t o_mv1 = c.take(sizeof(int) * chunk);
     const size_t o_est1 = c.take(sizeof(double) * chunk);
@@ -808,11 +802,17 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     SGW_CUDA(cudaMemcpyAsync(w + o_om, omega, sizeof(double) * nomega, cudaMemcpyHostToDevice, st), "omega copy");
     SGW_CUDA(cudaMemcpyAsync(w + o_sig, sig.data(), sizeof(double) * nomega, cudaMemcpyHostToDevice, st), "sig copy");
     SGW_CUDA(cudaMemsetAsync(w + o_zero, 0, sizeof(double), st), "memset");
+    const double* d_etas = nullptr;
+    if (eta_s) {
+        SGW_CUDA(cudaMemcpyAsync(w + o_etas, eta_s, sizeof(double) * nomega, cudaMemcpyHostToDevice, st), "eta copy");
+        d_etas = (const double*)(w + o_etas);
+    }
 
-    // One multishift launch of the selected method.  e_ref_d / omega_d give z = e_ref + omega + i eta.
+    // One multishift launch of the selected method: z_rj = e_ref_d[r] + omega_d[j] + i Im z, with
+    // Im z = eta_r_d[r], else eta_s_d[j], else eta.
     auto run = [&](bool corr, int nr, int ns, const double2* rhs_d, const double* e_ref_d, const double* omega_d,
                    double omega_seed, const double* sig_d, double tl, double2* x_d, int* mv_d, double* est_d,
-                   int* st_d, int g) -> cudaError_t {
+                   int* st_d, int g, const double* eta_s_d, const double* eta_r_d) -> cudaError_t {
         if (lanczos) {
             LanczosArgs L;
             L.nrhs = nr;
@@ -832,7 +832,9 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
             L.out_mv = mv_d;
             L.out_res = est_d;
             L.out_status = st_d;
-            return launch_lanczos(s->plan, L, g, corr ? SGW_PREC_FP64 : precision, threads, st);
+            L.eta_s = eta_s_d;
+            L.eta_r = eta_r_d;
+            return launch_lanczos(plan, L, g, corr ? SGW_PREC_FP64 : precision, threads, st);
         }
         SolveArgs A;
         A.nrhs = nr;
@@ -852,11 +854,10 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
         A.out_mv = mv_d;
         A.out_res = est_d;
         A.out_status = st_d;
-        return launch_solve(s->plan, A, g, st);
+        return launch_solve(plan, A, g, st);
     };
 
     // 1. multishift pass
-    double2* X = (double2*)out.dev;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool timed = report && report->kernel_ms;
     if (timed) {
@@ -864,9 +865,9 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
         SGW_CUDA(cudaEventCreate(&ev1), "event");
         SGW_CUDA(cudaEventRecord(ev0, st), "event");
     }
-    SGW_CUDA(run(false, nrhs, nomega, (const double2*)in.dev, (const double*)(w + o_eref), (const double*)(w + o_om),
-                 omega[seed], (const double*)(w + o_sig), tol, X, (int*)(w + o_mv), (double*)(w + o_est),
-                 (int*)(w + o_st), grid),
+    SGW_CUDA(run(false, nrhs, nomega, rhs_d, (const double*)(w + o_eref), (const double*)(w + o_om), omega[seed],
+                 (const double*)(w + o_sig), tol, X, (int*)(w + o_mv), (double*)(w + o_est), (int*)(w + o_st), grid,
+                 d_etas, nullptr),
              "solver kernel");
     int launches = 1;
     if (timed) SGW_CUDA(cudaEventRecord(ev1, st), "event");
@@ -876,8 +877,8 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     double* d_cert = (double*)(w + o_cert);
     const double* d_eref = (const double*)(w + o_eref);
     const double* d_om = (const double*)(w + o_om);
-    SGW_CUDA(launch_residual(s->plan, nrhs, nomega, nullptr, 0, (const double2*)in.dev, d_eref, d_om, eta, X,
-                             (double2*)(w + o_rscr), d_rel, d_cert, nullptr, grid_r, st),
+    SGW_CUDA(launch_residual(plan, nrhs, nomega, nullptr, 0, rhs_d, d_eref, d_om, eta, X,
+                             (double2*)(w + o_rscr), d_rel, d_cert, nullptr, grid_r, st, d_etas),
              "residual kernel");
     ++launches;
     std::vector<int> stv(np), mvv(np);
@@ -897,7 +898,7 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
 
     // 3. per-shift correction solves for pairs above tol: A_j d = r_j, x_j += d
     std::vector<int> list, mv1(chunk);
-    std::vector<double> eref1(chunk);
+    std::vector<double> eref1(chunk), eta1(chunk);
     for (int round = 0; round < max_refine; ++round) {
         list.clear();
         for (size_t q = 0; q < np; ++q)
@@ -909,25 +910,29 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
             for (int i = 0; i < nc; ++i) {
                 const int q = list[c0 + i];
                 eref1[i] = e_ref[q / nomega] + omega[q % nomega];
+                eta1[i] = eta_s ? eta_s[q % nomega] : eta;
                 worst = std::max(worst, relv[q]);
             }
             SGW_CUDA(cudaMemcpyAsync(w + o_list, list.data() + c0, sizeof(int) * nc, cudaMemcpyHostToDevice, st),
                      "list copy");
             SGW_CUDA(cudaMemcpyAsync(w + o_eref1, eref1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st),
                      "list copy");
+            SGW_CUDA(cudaMemcpyAsync(w + o_eta1, eta1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st),
+                     "list copy");
             const int* d_list = (const int*)(w + o_list);
-            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, d_eref, d_om, eta, X,
+            SGW_CUDA(launch_residual(plan, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
                                      (double2*)(w + o_rscr), d_rel, d_cert, (double2*)(w + o_rvec),
-                                     std::min(grid_r, nc), st),
+                                     std::min(grid_r, nc), st, d_etas),
                      "residual kernel");
             const double tl = std::min(0.5, std::max(1e-13, 0.3 * tol / worst));
             SGW_CUDA(run(true, nc, 1, (const double2*)(w + o_rvec), (const double*)(w + o_eref1), (const double*)(w + o_zero),
                          0.0, (const double*)(w + o_zero), tl, (double2*)(w + o_dbuf), (int*)(w + o_mv1),
-                         (double*)(w + o_est1), (int*)(w + o_st1), std::min(grid1, nc)),
+                         (double*)(w + o_est1), (int*)(w + o_st1), std::min(grid1, nc), nullptr,
+                         (const double*)(w + o_eta1)),
                      "correction solve");
             SGW_CUDA(launch_pair_axpy(nc, d_list, s->npw, (const double2*)(w + o_dbuf), X, st), "refinement update");
-            SGW_CUDA(launch_residual(s->plan, nrhs, nomega, d_list, nc, (const double2*)in.dev, d_eref, d_om, eta, X,
-                                     (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(grid_r, nc), st),
+            SGW_CUDA(launch_residual(plan, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
+                                     (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(grid_r, nc), st, d_etas),
                      "residual kernel");
             launches += 4;
             SGW_CUDA(cudaMemcpyAsync(mv1.data(), w + o_mv1, sizeof(int) * nc, cudaMemcpyDeviceToHost, st), "report");
@@ -937,7 +942,6 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
         SGW_CUDA(cudaMemcpyAsync(relv.data(), d_rel, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
         SGW_CUDA(cudaStreamSynchronize(st), "refinement");
     }
-    if ((r = finish_out(out, st, "dpsi copy")) != SGW_OK) return r;
     SGW_CUDA(cudaMemcpyAsync(certv.data(), d_cert, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
     SGW_CUDA(cudaStreamSynchronize(st), "solve");
     bool all = true;
@@ -956,6 +960,79 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     }
     if (!all) return fail(SGW_ENOCONV, "some (rhs, omega) pairs did not reach the tolerance");
     return SGW_OK;
+}
+
+
+sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const double* e_ref, int nomega,
+                             const double* omega, double eta, double tol, const sgw_solve_opts* opts, void* dpsi,
+                             sgw_report* report) {
+    g_err.clear();
+    if (!s || !rhs || !e_ref || !omega || !dpsi) return fail(SGW_EINVAL, "NULL argument");
+    if (nrhs < 0 || nomega < 1) return fail(SGW_EINVAL, "need nrhs >= 0 and nomega >= 1");
+    if (nomega > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nomega above 512");
+    if (!(eta > 0.0) || !std::isfinite(eta))
+        return fail(SGW_EINVAL, "eta must be positive (the shifted systems are singular at eta = 0)");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
+    if (!finite_all(e_ref, nrhs) || !finite_all(omega, nomega)) return fail(SGW_EINVAL, "non-finite e_ref or omega");
+    if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+    if (nrhs == 0) return SGW_OK;
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    const size_t vb = sizeof(double2) * (size_t)s->npw;
+    Staged in, out;
+    sgw_status r;
+    if ((r = stage_in(rhs, vb * nrhs, in, st, "rhs")) != SGW_OK) return r;
+    if ((r = stage_out(dpsi, vb * (size_t)nrhs * nomega, out, "dpsi", st)) != SGW_OK) return r;
+    const sgw_status rs = multishift(s, s->plan, nrhs, (const double2*)in.dev, e_ref, nomega, omega, nullptr, eta, tol,
+                                     opts, (double2*)out.dev, report, st);
+    if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
+    if ((r = finish_out(out, st, "dpsi copy")) != SGW_OK) return r;
+    SGW_CUDA(cudaStreamSynchronize(st), "solve");
+    return rs;
+}
+
+sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, const double* z, double tol,
+                           const sgw_solve_opts* opts, void* g, sgw_report* report) {
+    g_err.clear();
+    if (!s || !z || !g || (ncol > 0 && !cols)) return fail(SGW_EINVAL, "NULL argument");
+    if (ncol < 0 || nz < 1) return fail(SGW_EINVAL, "need ncol >= 0 and nz >= 1");
+    if (nz > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nz above 512");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
+    std::vector<double> zre(nz), zim(nz);
+    for (int j = 0; j < nz; ++j) {
+        zre[j] = z[2 * j];
+        zim[j] = z[2 * j + 1];
+        if (!std::isfinite(zre[j]) || !std::isfinite(zim[j])) return fail(SGW_EINVAL, "non-finite z");
+        if (zim[j] == 0.0) return fail(SGW_EINVAL, "Im z must be nonzero (z - H is singular on the real axis)");
+    }
+    if (ncol > 0 && is_device_ptr(cols)) return fail(SGW_EINVAL, "cols must be a host array");
+    for (int c = 0; c < ncol; ++c)
+        if (cols[c] < 0 || cols[c] >= s->npw) return fail(SGW_EINVAL, "column index outside [0, n_pw)");
+    if (ncol == 0) return SGW_OK;
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    // the operator is H itself: the plan without occupied states
+    Plan plan = s->plan;
+    plan.nocc = 0;
+    plan.psi = nullptr;
+    plan.psi_dd = nullptr;
+    const size_t vb = sizeof(double2) * (size_t)s->npw;
+    Staged in_cols, rb, out;
+    sgw_status r;
+    if ((r = stage_in(cols, sizeof(int) * ncol, in_cols, st, "cols")) != SGW_OK) return r;
+    SGW_CUDA(cudaMallocAsync(&rb.dev, vb * ncol, st), "rhs allocation");
+    rb.owned = true;
+    rb.st = st;
+    SGW_CUDA(launch_unit_rhs((const int*)in_cols.dev, ncol, s->npw, (double2*)rb.dev, st), "unit rhs kernel");
+    if ((r = stage_out(g, vb * (size_t)ncol * nz, out, "g", st)) != SGW_OK) return r;
+    std::vector<double> e0(ncol, 0.0);
+    const sgw_status rs = multishift(s, plan, ncol, (const double2*)rb.dev, e0.data(), nz, zre.data(), zim.data(), 0.0,
+                                     tol, opts, (double2*)out.dev, report, st);
+    if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
+    if (report && report->launches) *report->launches += 1;
+    if ((r = finish_out(out, st, "g copy")) != SGW_OK) return r;
+    SGW_CUDA(cudaStreamSynchronize(st), "solve");
+    return rs;
 }
 
 static sgw_status precond_common(sgw_system* s, int npairs, const double2* rhs_d, const double* eref_d,

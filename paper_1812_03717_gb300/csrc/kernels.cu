@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
             }
         }
         for (int j = tid; j < ns; j += nt) {
-            zsh[j] = make_double2(A.e_ref[r] + A.omega[j], A.eta);
+            zsh[j] = make_double2(A.e_ref[r] + A.omega[j], A.eta_r ? A.eta_r[r] : (A.eta_s ? A.eta_s[j] : A.eta));
             est[j] = 1.0;
             kc[j] = 0;
             st[j] = bad ? SGW_PAIR_NONFINITE : (zero ? SGW_PAIR_CONVERGED : -1);
@@ -761,7 +761,8 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs,
                                                                const double* __restrict__ omega, double eta,
                                                                const double2* __restrict__ x,
                                                                double2* __restrict__ scratch, double* __restrict__ rel,
-                                                               double* __restrict__ cert, double2* __restrict__ store) {
+                                                               double* __restrict__ cert, double2* __restrict__ store,
+                                                               const double* __restrict__ eta_s) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double2 s_dot[kRedSlots];
     load_twiddles<ArF64>(P, smem);
@@ -777,7 +778,7 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs,
         const int r = q / ns, j = q % ns;
         const double2* xv = x + (size_t)q * npw;
         const double2* rv = rhs + (size_t)r * npw;
-        const double2 z = make_double2(e_ref[r] + omega[j], eta);
+        const double2 z = make_double2(e_ref[r] + omega[j], eta_s ? eta_s[j] : eta);
         block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
         for (int g = tid; g < npw; g += nt) {
             double2 h = xv[g];
@@ -807,10 +808,19 @@ __global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs,
                 cert[q] = NAN;
             } else {
                 rel[q] = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
-                cert[q] = xn > 0.0 ? rn / (eta * xn) : (rn > 0.0 ? INFINITY : 0.0);
+                cert[q] = xn > 0.0 ? rn / (fabs(z.y) * xn) : (rn > 0.0 ? INFINITY : 0.0);
             }
         }
         __syncthreads();
+    }
+}
+
+// rhs[c] = e_{cols[c]}: the unit right-hand sides of the Green's-function equation (Eq. 2).
+__global__ void unit_rhs_kernel(const int* __restrict__ cols, int ncol, int npw, double2* __restrict__ rhs) {
+    const size_t n = (size_t)ncol * npw;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / npw), g = (int)(t % npw);
+        rhs[t] = make_double2(g == cols[c] ? 1.0 : 0.0, 0.0);
     }
 }
 
@@ -1016,16 +1026,23 @@ cudaError_t launch_apply(const Plan& P0, int nvec, const double2* x, double2* y,
 
 cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
-                            double* rel, double* cert, double2* store, int grid, cudaStream_t st) {
+                            double* rel, double* cert, double2* store, int grid, cudaStream_t st,
+                            const double* eta_s) {
     const Plan P = tuned_plan(P0, 0);
     const int smem = apply_smem_bytes(P0);
     cudaError_t e = allow_max_smem((const void*)residual_kernel);
     if (e != cudaSuccess) return e;
     residual_kernel<<<grid, kThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
-                                                  cert, store);
+                                                  cert, store, eta_s);
     return cudaGetLastError();
 }
 
+cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st) {
+    const size_t n = (size_t)ncol * npw;
+    if (n == 0) return cudaSuccess;
+    unit_rhs_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, st>>>(cols, ncol, npw, rhs);
+    return cudaGetLastError();
+}
 cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st) {
     if (nlist == 0) return cudaSuccess;
     pair_axpy_kernel<<<1024, 256, 0, st>>>(nlist, list, npw, d, x);

@@ -100,6 +100,9 @@ struct LanczosArgs {
     int* out_mv;              // [nrhs][nshift]  Lanczos steps when the pair converged
     double* out_res;          // [nrhs][nshift]
     int* out_status;          // [nrhs][nshift]
+    // Im z_rj: eta_r[r] when given, else eta_s[j] when given, else eta (any sign but 0)
+    const double* eta_s = nullptr;   // [nshift]
+    const double* eta_r = nullptr;   // [nrhs]
 };
 
 int lanczos_smem_bytes(const Plan& P, int nshift);
@@ -112,9 +115,13 @@ cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid);
 cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
                          double2* scratch, int grid, int precision, cudaStream_t st);
+// Im z_rj = eta_s[j] when eta_s is given, else eta; the certificate divides by |Im z|.
 cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
-                            double* rel, double* cert, double2* store, int grid, cudaStream_t st);
+                            double* rel, double* cert, double2* store, int grid, cudaStream_t st,
+                            const double* eta_s = nullptr);
+// rhs[c][g] = 1 if g == cols[c] else 0 ([ncol][npw]); the right-hand sides of Eq. 2.
+cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st);
 cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st);
 cudaError_t resident_grid(const void* kernel, int smem, int* grid, int threads = kThreads);
 

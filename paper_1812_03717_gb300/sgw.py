@@ -24,7 +24,7 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
                 "SGW_EUNSUPPORTED"]
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
-           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_residual", "sgw_residual_noalloc",
+           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_residual", "sgw_residual_noalloc",
            "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
            "sgw_mlp_forward", "sgw_mlp_grad", "sgw_mlp_train_step", "sgw_mlp_destroy", "sgw_destroy_system",
            "sgw_last_error"]
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_apply_shifted.argtypes = [vp, ip, vp, vp, vp, ip, vp]
     lib.sgw_solve_shifted.argtypes = [vp, ip, vp, vp, ip, vp, dp, dp, ctypes.POINTER(_Opts), vp,
                                       ctypes.POINTER(_Report)]
+    lib.sgw_solve_green.argtypes = [vp, ip, vp, ip, vp, dp, ctypes.POINTER(_Opts), vp, ctypes.POINTER(_Report)]
     lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_residual_noalloc.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_solve_pershift.argtypes = [vp, ip, vp, vp, vp, dp, dp, ip, vp, vp, ctypes.POINTER(_Opts), vp,
@@ -264,6 +265,34 @@ class System:
                                                         "kernel_ms")))
         s = load().sgw_solve_shifted(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data,
                                      float(eta), float(tol), ctypes.byref(opts), _ptr(out), ctypes.byref(crep))
+        _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
+        return out, rep, s == SGW_OK
+
+    def solve_green(self, cols, z, tol=1e-10, precision="fp64", max_matvec=0, max_refine=0, threads=0, out=None,
+                    device=None, stream=None, raise_on_noconv=False):
+        """Columns cols of G(z_j) = (z_j - H)^-1 (sgw_solve_green): returns (g [ncol][nz][n_pw], report
+        dict, converged flag).  z: complex shifts with Im z != 0.  The result is a CUDA tensor when
+        out is one or device is "cuda", else a numpy array."""
+        cols = np.ascontiguousarray(cols, dtype=np.int32)
+        zc = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).ravel())
+        zz = np.ascontiguousarray(np.column_stack([zc.real, zc.imag]))
+        nc, nz = len(cols), len(zc)
+        if out is None:
+            if device is not None and str(device).startswith("cuda"):
+                import torch
+                out = torch.empty((nc, nz, self.n_pw), dtype=torch.complex128, device=device)
+            else:
+                out = np.empty((nc, nz, self.n_pw), dtype=np.complex128)
+        rep = {"matvecs": np.zeros((nc, nz), dtype=np.int32), "est_res": np.zeros((nc, nz)),
+               "rel_res": np.zeros((nc, nz)), "cert": np.zeros((nc, nz)),
+               "status": np.zeros((nc, nz), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
+               "kernel_ms": np.zeros(1)}
+        opts = _Opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(out, stream))
+        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
+                                                        "kernel_ms")))
+        s = load().sgw_solve_green(self._h, nc, cols.ctypes.data, nz, zz.ctypes.data, float(tol), ctypes.byref(opts),
+                                   _ptr(out), ctypes.byref(crep))
         _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
         return out, rep, s == SGW_OK
 
