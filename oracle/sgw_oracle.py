@@ -25,7 +25,10 @@ What it computes, by plain definition (no blocking, fusion or reordering):
 * the true residual and the a-posteriori error certificate |r| / (eta |dpsi|);
 * columns of the Green's function of Eq. 2-3, G(z) = (z - H)^-1 (no projector), by dense
   LU per shift and by the spectral sum over all eigenstates, with their residual and
-  certificate |r| / (|Im z| |g|).
+  certificate |r| / (|Im z| |g|);
+* one k-point's contribution to the density response of Eq. 5 by the paper's route
+  (Sternheimer solutions at +-(omega + i eta), real-space product with the unperturbed
+  periodic part, Fourier transform back) and by the sum over the eigenstates of H_{k+q}.
 
 Each function cites the passage of the paper it restates.
 """
@@ -298,3 +301,85 @@ def time_ordered_shifts(omega, mu, eta):
     if np.any(omega == mu):
         raise ValueError("omega_j = mu has no time-ordering sign")
     return omega + 1j * eta * np.sign(omega - mu)
+
+
+# -------------------------------------------------------------- Eq. 5: density response
+
+def solve_shifted_z(h, psi_v, rhs, z):
+    """x[r][j] solving (P_c H P_c - z[r][j]) x = -P_c rhs_r for arbitrary complex z[r][j]
+    (one dense LU per distinct shift)."""
+    rhs = np.atleast_2d(np.asarray(rhs, np.complex128))
+    z = np.asarray(z, np.complex128)
+    b = -project_c(psi_v, rhs)
+    n = h.shape[0]
+    pc = np.eye(n, dtype=np.complex128) - np.asarray(psi_v).T @ np.asarray(psi_v).conj()
+    pcp = pc @ h @ pc
+    out = np.zeros((len(rhs), z.shape[1], n), dtype=np.complex128)
+    for zz in np.unique(z):
+        rows, cols = np.nonzero(z == zz)
+        lu = scipy.linalg.lu_factor(pcp - zz * np.eye(n), check_finite=False)
+        out[rows, cols, :] = scipy.linalg.lu_solve(lu, b[rows].T, check_finite=False).T
+    return out
+
+
+def periodic_on_box(coef, miller, dims):
+    """u(r_j) = sum_G c_G exp(i G.r_j) on the box (the convention of the FFT apply)."""
+    box = np.zeros(tuple(dims), dtype=np.complex128)
+    m = np.asarray(miller, dtype=np.int64) % np.asarray(dims)
+    box[m[:, 0], m[:, 1], m[:, 2]] = coef
+    return np.fft.ifftn(box) * float(np.prod(dims))
+
+
+def box_coefficient(f, g_miller, dims):
+    """c_G = N^-3 sum_j f(r_j) exp(-i G.r_j) for the listed G."""
+    c = np.fft.fftn(f) / float(np.prod(dims))
+    m = np.asarray(g_miller, dtype=np.int64) % np.asarray(dims)
+    return c[m[:, 0], m[:, 1], m[:, 2]]
+
+
+def density_response(h_kq, psi_v_kq, psi_k, miller_k, miller_kq, eps_k, gp_miller, omega, eta, dims, weight):
+    """One k-point's contribution to Eq. 5, by the paper's route:
+        dn[G][G'][j] = weight * sum_v sum_{+-} FT_G[ conj(u_{v,k}(r)) du_{v,k+q,G'}(r; +-omega_j) ]
+    where du(+-omega) solves the Sternheimer equation (P_c H P_c - z) du = -P_c dV_G' psi_v with
+    the complex frequency omega_j + i eta taken with both signs, z = eps_v +- (omega_j + i eta);
+    u and du are the periodic parts on the box (coefficients of Eq. 1 summed with exp(iG.r)),
+    the product is formed in real space and Fourier transformed back (box DFT, N^-3); G and
+    G' both run over the perturbation list gp_miller (weight = 2 / N_k for spin and the
+    k-point average)."""
+    psi_k = np.atleast_2d(np.asarray(psi_k, np.complex128))
+    n_v, n_p, n_w = len(psi_k), len(gp_miller), len(omega)
+    rhs = make_rhs(miller_kq, miller_k, psi_k, gp_miller)          # row v * n_p + p
+    omega = np.asarray(omega, np.float64)
+    out = np.zeros((n_p, n_p, n_w), dtype=np.complex128)
+    for v in range(n_v):
+        u = periodic_on_box(psi_k[v], miller_k, dims)
+        zc = omega + 1j * eta
+        z = np.concatenate([eps_k[v] + zc, eps_k[v] - zc])[None, :].repeat(n_p, axis=0)
+        x = solve_shifted_z(h_kq, psi_v_kq, rhs[v * n_p:(v + 1) * n_p], z)   # [n_p][2 n_w][npw]
+        for p_in in range(n_p):
+            for j in range(n_w):
+                for s in (j, n_w + j):
+                    du = periodic_on_box(x[p_in, s], miller_kq, dims)
+                    out[:, p_in, j] += weight * box_coefficient(np.conj(u) * du, gp_miller, dims)
+    return out
+
+
+def density_response_sos(h_kq, n_occ_kq, psi_k, miller_k, miller_kq, eps_k, gp_miller, omega, eta, weight):
+    """The same contribution from the eigenstates of H_{k+q} (an Adler-Wiser-type sum over the
+    unoccupied states c, the n_occ_kq lowest being occupied):
+        dn[G][G'][j] = weight sum_v sum_c conj(M_vc(G)) M_vc(G') [1/(eps_v + w_j - e_c)
+                                                                 + 1/(eps_v - w_j - e_c)],
+    w_j = omega_j + i eta, M_vc(G') = <psi_c | exp(i(q+G').r) psi_{v,k}>."""
+    w, vec = np.linalg.eigh(h_kq)
+    vc, ec = vec[:, n_occ_kq:], w[n_occ_kq:]
+    psi_k = np.atleast_2d(np.asarray(psi_k, np.complex128))
+    n_v, n_p = len(psi_k), len(gp_miller)
+    rhs = make_rhs(miller_kq, miller_k, psi_k, gp_miller)
+    out = np.zeros((n_p, n_p, len(omega)), dtype=np.complex128)
+    for v in range(n_v):
+        m = rhs[v * n_p:(v + 1) * n_p] @ vc.conj()          # [p][c] = <psi_c|rhs_vp>
+        for j, om in enumerate(omega):
+            wc = om + 1j * eta
+            f = 1.0 / (eps_k[v] + wc - ec) + 1.0 / (eps_k[v] - wc - ec)
+            out[:, :, j] += weight * (m.conj() * f) @ m.T
+    return out
