@@ -354,6 +354,13 @@ def run_ours(args):
         kg = units_for_step(0, ws, rank, nk)
         green = measure_green(P, inst, kg, jobs[kg], variants[0], stream)
 
+    # density response of Eq. 5 for one k-point: its 512 right-hand sides at +-omega (128
+    # shifts per Krylov space) and the reduction to dn[G][G'][omega]
+    density = None
+    if not args.no_density:
+        kd = units_for_step(0, ws, rank, nk)
+        density = measure_density(P, inst, kd, jobs[kd], variants[0], stream, nk)
+
     # per-shift solves of sampled pairs of this workload: plain vs learned diagonal preconditioner
     learned = None
     if not args.no_learned:
@@ -447,7 +454,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws} (k-points sharded)", "generate_s": round(t_gen, 1)},
         "quality": head["quality"], "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e,
         "clocks": head["clocks"], "gpu_launches": head["gpu_launches"], "learned_preconditioner": learned,
-        "green_function": green,
+        "green_function": green, "density_response": density,
         "variants": {v: {k: res[v][k] for k in ("value", "ms_per_step", "kernel_ms_per_launch", "roofline", "quality")}
                      for v in variants},
     }
@@ -515,6 +522,46 @@ def measure_green(P, inst, ik, job, precision, stream, runs=1):
             "roofline": roof, "gpu_launches": int(rep["launches"][0])}
 
 
+def measure_density(P, inst, ik, job, precision, stream, nk, runs=1):
+    """One k-point's contribution to Eq. 5 (all bands x all G' x 64 omega, both signs): one
+    untimed call, then `runs` calls timed with CUDA events; returns a dict for the JSON line."""
+    import torch
+    s = job["sys"]
+    kp = inst.kpoints[ik]
+    n_p = len(inst.gp_miller)
+    out = torch.zeros((n_p, n_p, len(inst.omega)), dtype=torch.complex128, device="cuda")
+    s.density_response(job["rhs"], kp.eps_k, inst.omega, inst.eta, weight=2.0 / nk, tol=1e-10,
+                       precision=precision, out=out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(runs):
+        _, rep, ok = s.density_response(job["rhs"], kp.eps_k, inst.omega, inst.eta, weight=2.0 / nk, tol=1e-10,
+                                        precision=precision, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / runs
+    npairs = rep["status"].size
+    steps = rep["matvecs"].max(axis=1)
+    plan = job["plan"]
+    work = (solver_fp64_flops(plan, rep["matvecs"]) if precision == "fp64" else solver_df32_ops(plan, rep["matvecs"]))
+    peak = (FP64_PEAK_GFLOPS if precision == "fp64" else FP32_PEAK_GFLOPS) / 1e3
+    roof = {"bound": "alu", "achieved": work / 1e12 / (ms / 1e3), "peak": peak, "unit": "TFLOP/s",
+            "kernel": "lanczos_solve_kernel<%s>" % ("ArF64" if precision == "fp64" else "ArDF"),
+            "time": "whole call (multishift kernel, FP64 residual check, density reduction)", "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    return {"metric": "density-response Sternheimer solves/s (rhs x +-omega) incl. the Eq. 5 reduction",
+            "value": npairs / (ms / 1e3), "unit": "solves/s", "ms_per_run": ms, "runs": runs,
+            "dn_columns_per_s": n_p * len(inst.omega) / (ms / 1e3), "precision": precision,
+            "workload": f"k-point {ik}: {kp.psi_k.shape[0]} bands x {n_p} G' right-hand sides, {len(inst.omega)} "
+                        f"omega in [0, 60] eV at + and - (omega + i eta), dn[G][G'][omega] for the {n_p} G",
+            "quality": {"pairs": int(npairs), "converged": int((rep["status"] == 0).sum()),
+                        "max_true_rel_res": float(rep["rel_res"].max()),
+                        "lanczos_steps_median": float(np.median(steps)), "lanczos_steps_max": int(steps.max())},
+            "roofline": roof, "gpu_launches": int(rep["launches"][0])}
+
+
 def run_profile_case(args):
     """One solve of the first --profile-case right-hand sides of k-point 0 (no timing contract):
     the small case that ncu captures of the multishift kernel run."""
@@ -552,6 +599,7 @@ def main():
     ap.add_argument("--variants", default="df32,fp64",
                     help="comma list of FFT precisions to time; the first is the headline")
     ap.add_argument("--no-green", action="store_true", help="skip the Green's-function measurement")
+    ap.add_argument("--no-density", action="store_true", help="skip the density-response measurement")
     ap.add_argument("--profile-case", type=int, default=0,
                     help="solve this many right-hand sides of k-point 0 once and exit (for ncu captures)")
     args = ap.parse_args()

@@ -203,6 +203,29 @@ sgw_status sgw_solve_shifted(sgw_system* sys, int nrhs, const void* rhs, const d
 sgw_status sgw_solve_green(sgw_system* sys, int ncol, const int* cols, int nz, const double* z, double tol,
                            const sgw_solve_opts* opts, void* g, sgw_report* report);
 
+/* One k-point's contribution to the density response of Eq. 5 (Sec. 2.3):
+ *   dn[G][G'][j] += weight * sum_v sum_{+-} FT_G[ conj(u_{v,k}(r)) du_{v,k+q,G'}(r; +-w_j) ],
+ * w_j = omega[j] + i eta, with du(+-w) the Sternheimer solutions
+ *   (P_c H P_c - z) du = -P_c rhs[v n_pert + p],   z = eps_v[v] +- w_j,
+ * both signs sharing one Krylov space per right-hand side (2 nomega shifts, the -w branch
+ * with Im z = -eta), followed by the FP64 true residual and corrections as in
+ * sgw_solve_shifted.  u_{v,k}(r) = sum_G psi_{v,k}(G) e^{iG.r} and du likewise (periodic parts);
+ * FT_G is the box coefficient N^-3 sum_r f(r) e^{-iG.r}.  The library evaluates it in
+ * reciprocal space as <dV_G psi_v | du> (equal by the convolution theorem; dV_G psi_v is the
+ * Eq. 8 right-hand side for G).  G and G' both run over the n_pert perturbations of rhs.
+ *   rhs     complex [n_v * n_pert][n_pw] (host or device): sgw_make_rhs output, row v n_pert + p.
+ *   eps_v   [n_v] host, Ha (the unperturbed energies eps_{v,k}).   omega [nomega] host, Ha;
+ *           2 nomega <= 512 (else SGW_EUNSUPPORTED).   eta > 0 (else SGW_EINVAL).
+ *   weight  e.g. 2 / N_k (spin, k-point average); dn is ACCUMULATED: call once per k-point.
+ *   dn      complex [n_pert (G)][n_pert (G')][nomega] (host or device), read and updated.
+ *   report  optional per-pair report [n_v * n_pert][2 nomega] (shift j < nomega at +w_j,
+ *           nomega + j at -w_j); launches counts the density kernel too.
+ * Returns SGW_ESTATE without occupied states, SGW_ENOCONV (dn still updated) if a pair's
+ * true residual stays above tol. */
+sgw_status sgw_density_response(sgw_system* sys, int n_v, int n_pert, const void* rhs, const double* eps_v,
+                                int nomega, const double* omega, double eta, double weight, double tol,
+                                const sgw_solve_opts* opts, void* dn, sgw_report* report);
+
 /* True FP64 residual of given solutions: for every pair
  *   r = -P_c rhs - (P_c H P_c - z) dpsi,  rel_res = |r| / |P_c rhs|,  cert = |r| / (eta |dpsi|).
  * Since P_c H P_c - z is normal with every eigenvalue at distance >= eta from 0, cert bounds

@@ -1035,6 +1035,52 @@ sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, con
     return rs;
 }
 
+sgw_status sgw_density_response(sgw_system* s, int n_v, int n_pert, const void* rhs, const double* eps_v, int nomega,
+                                const double* omega, double eta, double weight, double tol,
+                                const sgw_solve_opts* opts, void* dn, sgw_report* report) {
+    g_err.clear();
+    if (!s || !eps_v || !omega || !dn || (n_v > 0 && n_pert > 0 && !rhs)) return fail(SGW_EINVAL, "NULL argument");
+    if (n_v < 0 || n_pert < 0 || nomega < 1) return fail(SGW_EINVAL, "need n_v, n_pert >= 0 and nomega >= 1");
+    if (2 * nomega > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nomega above 256 (2 nomega shifts per right-hand side)");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(SGW_EINVAL, "eta must be positive");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
+    if (!std::isfinite(weight)) return fail(SGW_EINVAL, "non-finite weight");
+    if (!finite_all(eps_v, n_v) || !finite_all(omega, nomega)) return fail(SGW_EINVAL, "non-finite eps_v or omega");
+    if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+    const int nrhs = n_v * n_pert;
+    if (nrhs == 0) return SGW_OK;
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    const size_t vb = sizeof(double2) * (size_t)s->npw;
+    const size_t dn_bytes = sizeof(double2) * (size_t)n_pert * n_pert * nomega;
+    Staged in, xb, dnb;
+    sgw_status r;
+    if ((r = stage_in(rhs, vb * nrhs, in, st, "rhs")) != SGW_OK) return r;
+    if ((r = stage_in(dn, dn_bytes, dnb, st, "dn")) != SGW_OK) return r;
+    SGW_CUDA(cudaMallocAsync(&xb.dev, vb * (size_t)nrhs * 2 * nomega, st), "solution allocation");
+    xb.owned = true;
+    xb.st = st;
+    // shifts z = eps_v + omega_j + i eta (j < nomega) and eps_v - omega_j - i eta (the -omega branch)
+    std::vector<double> e_rows(nrhs), om2(2 * nomega), eta2(2 * nomega);
+    for (int i = 0; i < nrhs; ++i) e_rows[i] = eps_v[i / n_pert];
+    for (int j = 0; j < nomega; ++j) {
+        om2[j] = omega[j];
+        eta2[j] = eta;
+        om2[nomega + j] = -omega[j];
+        eta2[nomega + j] = -eta;
+    }
+    const sgw_status rs = multishift(s, s->plan, nrhs, (const double2*)in.dev, e_rows.data(), 2 * nomega, om2.data(),
+                                     eta2.data(), eta, tol, opts, (double2*)xb.dev, report, st);
+    if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
+    SGW_CUDA(launch_density(n_v, n_pert, nomega, s->npw, (const double2*)in.dev, (const double2*)xb.dev, weight,
+                            (double2*)dnb.dev, st),
+             "density kernel");
+    if (report && report->launches) *report->launches += 1;
+    if (dnb.owned) SGW_CUDA(cudaMemcpyAsync(dn, dnb.dev, dn_bytes, cudaMemcpyDeviceToHost, st), "dn copy");
+    SGW_CUDA(cudaStreamSynchronize(st), "density response");
+    return rs;
+}
+
 static sgw_status precond_common(sgw_system* s, int npairs, const double2* rhs_d, const double* eref_d,
                                  const double* om_d, const double* delta_d, double eta, int precond,
                                  const sgw_mlp* mlp, double* d_d, cudaStream_t st) {

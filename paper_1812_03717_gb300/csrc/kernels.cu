@@ -824,6 +824,60 @@ __global__ void unit_rhs_kernel(const int* __restrict__ cols, int ncol, int npw,
     }
 }
 
+// ------------------------------------------------------------- density response (Eq. 5)
+//
+// One k-point's contribution to the density response,
+//   dn[G][G'][j] += weight * sum_v sum_{+-} FT_G[ conj(u_v(r)) du_{v,G'}(r; +-w_j) ],
+// computed coefficient by coefficient in reciprocal space: the box Fourier coefficient of
+// the product at G is sum_{G1} conj(psi_v(G1)) du(G1 + G) = <dV_G psi_v | du> (the
+// convolution theorem; the box holds the product without aliasing), and dV_G psi_v in the
+// k+q basis is exactly the Eq. 8 right-hand side R[v][G].  So, with X the Sternheimer
+// solutions [v * np + p][2 nw][npw] (shift j at +w_j, nw + j at -w_j),
+//   dn[po][pi][j] += weight * sum_v sum_g conj(R[v np + po][g]) (X[v np + pi][j][g] + X[..][nw + j][g]).
+// A CTA owns a tile of kDnP output G's x kDnJ frequencies for one G'; it walks v and the
+// plane waves in chunks staged in shared memory (rows padded by one element so the 16-byte
+// reads of one quarter-warp fall in distinct banks); each thread accumulates one output in
+// FP64.  X is read once from HBM, R (a few MB) from L2.
+constexpr int kDnP = 32, kDnJ = 8, kDnCh = 64;
+
+__global__ void __launch_bounds__(kDnP * kDnJ) density_kernel(int n_v, int n_p, int nw, int npw,
+                                                              const double2* __restrict__ R,
+                                                              const double2* __restrict__ X, double weight,
+                                                              double2* __restrict__ dn) {
+    __shared__ double2 rs[kDnP][kDnCh + 1];
+    __shared__ double2 ys[kDnJ][kDnCh + 1];
+    const int tid = threadIdx.x;
+    const int jl = tid % kDnJ, pl = tid / kDnJ;
+    const int po0 = blockIdx.x * kDnP, pi = blockIdx.y, j0 = blockIdx.z * kDnJ;
+    double2 acc = cz();
+    for (int v = 0; v < n_v; ++v) {
+        const double2* rv = R + (size_t)v * n_p * npw;
+        const double2* xv = X + ((size_t)v * n_p + pi) * 2 * nw * npw;
+        for (int g0 = 0; g0 < npw; g0 += kDnCh) {
+            for (int i = tid; i < kDnP * kDnCh; i += blockDim.x) {
+                const int p = i / kDnCh, g = i % kDnCh;
+                rs[p][g] = (po0 + p < n_p && g0 + g < npw) ? rv[(size_t)(po0 + p) * npw + g0 + g] : cz();
+            }
+            for (int i = tid; i < kDnJ * kDnCh; i += blockDim.x) {
+                const int j = i / kDnCh, g = i % kDnCh;
+                double2 y = cz();
+                if (j0 + j < nw && g0 + g < npw)
+                    y = cadd(xv[(size_t)(j0 + j) * npw + g0 + g], xv[(size_t)(nw + j0 + j) * npw + g0 + g]);
+                ys[j][g] = y;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int g = 0; g < kDnCh; ++g) acc = cadd(acc, cmulc(rs[pl][g], ys[jl][g]));
+            __syncthreads();
+        }
+    }
+    const int po = po0 + pl, j = j0 + jl;
+    if (po < n_p && j < nw) {
+        double2* o = dn + ((size_t)po * n_p + pi) * nw + j;
+        *o = make_double2(o->x + weight * acc.x, o->y + weight * acc.y);
+    }
+}
+
 // x[list[i]] += d[i] for the listed pairs (refinement update).
 __global__ void pair_axpy_kernel(int nlist, const int* __restrict__ list, int npw, const double2* __restrict__ d,
                                  double2* __restrict__ x) {
@@ -1037,6 +1091,13 @@ cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* lis
     return cudaGetLastError();
 }
 
+cudaError_t launch_density(int n_v, int n_p, int nw, int npw, const double2* R, const double2* X, double weight,
+                           double2* dn, cudaStream_t st) {
+    if (n_v == 0 || n_p == 0 || nw == 0) return cudaSuccess;
+    const dim3 grid((n_p + kDnP - 1) / kDnP, n_p, (nw + kDnJ - 1) / kDnJ);
+    density_kernel<<<grid, kDnP * kDnJ, 0, st>>>(n_v, n_p, nw, npw, R, X, weight, dn);
+    return cudaGetLastError();
+}
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st) {
     const size_t n = (size_t)ncol * npw;
     if (n == 0) return cudaSuccess;

@@ -120,6 +120,10 @@ cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int grid, cudaStream_t st,
                             const double* eta_s = nullptr);
+// dn[po][pi][j] += weight sum_v sum_g conj(R[v n_p + po][g]) (X[v n_p + pi][j][g] + X[v n_p + pi][nw + j][g])
+// (Eq. 5 in reciprocal space); R [n_v n_p][npw], X [n_v n_p][2 nw][npw], dn [n_p][n_p][nw].
+cudaError_t launch_density(int n_v, int n_p, int nw, int npw, const double2* R, const double2* X, double weight,
+                           double2* dn, cudaStream_t st);
 // rhs[c][g] = 1 if g == cols[c] else 0 ([ncol][npw]); the right-hand sides of Eq. 2.
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st);
 cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st);

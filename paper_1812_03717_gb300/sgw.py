@@ -24,7 +24,7 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
                 "SGW_EUNSUPPORTED"]
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
-           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_residual", "sgw_residual_noalloc",
+           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_residual", "sgw_residual_noalloc",
            "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
            "sgw_mlp_forward", "sgw_mlp_grad", "sgw_mlp_train_step", "sgw_mlp_destroy", "sgw_destroy_system",
            "sgw_last_error"]
@@ -81,6 +81,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_solve_shifted.argtypes = [vp, ip, vp, vp, ip, vp, dp, dp, ctypes.POINTER(_Opts), vp,
                                       ctypes.POINTER(_Report)]
     lib.sgw_solve_green.argtypes = [vp, ip, vp, ip, vp, dp, ctypes.POINTER(_Opts), vp, ctypes.POINTER(_Report)]
+    lib.sgw_density_response.argtypes = [vp, ip, ip, vp, vp, ip, vp, dp, dp, dp, ctypes.POINTER(_Opts), vp,
+                                         ctypes.POINTER(_Report)]
     lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_residual_noalloc.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_solve_pershift.argtypes = [vp, ip, vp, vp, vp, dp, dp, ip, vp, vp, ctypes.POINTER(_Opts), vp,
@@ -293,6 +295,39 @@ class System:
                                                         "kernel_ms")))
         s = load().sgw_solve_green(self._h, nc, cols.ctypes.data, nz, zz.ctypes.data, float(tol), ctypes.byref(opts),
                                    _ptr(out), ctypes.byref(crep))
+        _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
+        return out, rep, s == SGW_OK
+
+    def density_response(self, rhs, eps_v, omega, eta, weight=1.0, tol=1e-10, precision="fp64", max_matvec=0,
+                         max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False):
+        """One k-point's contribution to Eq. 5 (sgw_density_response): rhs [n_v * n_pert][n_pw] from
+        make_rhs, eps_v [n_v].  Accumulates into out [n_pert][n_pert][nomega] (zeros when None; a
+        CUDA tensor stays on the device) and returns (out, report [n_v * n_pert][2 nomega], converged)."""
+        rhs = _c128(rhs)
+        eps_v = np.ascontiguousarray(eps_v, dtype=np.float64)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        n_v = len(eps_v)
+        if n_v == 0 or rhs.shape[0] % n_v:
+            raise ValueError("rhs rows must be n_v * n_pert")
+        n_p, nw = rhs.shape[0] // n_v, len(omega)
+        if out is None:
+            if _is_torch(rhs):
+                import torch
+                out = torch.zeros((n_p, n_p, nw), dtype=torch.complex128, device=rhs.device)
+            else:
+                out = np.zeros((n_p, n_p, nw), dtype=np.complex128)
+        nr = rhs.shape[0]
+        rep = {"matvecs": np.zeros((nr, 2 * nw), dtype=np.int32), "est_res": np.zeros((nr, 2 * nw)),
+               "rel_res": np.zeros((nr, 2 * nw)), "cert": np.zeros((nr, 2 * nw)),
+               "status": np.zeros((nr, 2 * nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
+               "kernel_ms": np.zeros(1)}
+        opts = _Opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(rhs, stream))
+        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
+                                                        "kernel_ms")))
+        s = load().sgw_density_response(self._h, n_v, n_p, _ptr(rhs), eps_v.ctypes.data, nw, omega.ctypes.data,
+                                        float(eta), float(weight), float(tol), ctypes.byref(opts), _ptr(out),
+                                        ctypes.byref(crep))
         _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
         return out, rep, s == SGW_OK
 
