@@ -163,11 +163,27 @@ bool factor_235(int n, AxisPlan& ax) {
     for (int r : rads) {
         while (m % r == 0) {
             if (ax.nst >= kMaxStages) return false;
-            ax.rad[ax.nst++] = r;
             m /= r;
+            ax.span[ax.nst] = m;
+            ax.rad[ax.nst++] = r;
         }
     }
     return m == 1;
+}
+
+// Real-space index held at each position after the in-place decimation-in-frequency FFT of
+// the axis: frequency k = r_0 + R_0 (r_1 + R_1 (...)) lands at sum_s r_s m_s.
+std::vector<int> dif_order(const AxisPlan& ax) {
+    std::vector<int> k_at(ax.n);
+    for (int k = 0; k < ax.n; ++k) {
+        int rest = k, pos = 0;
+        for (int s = 0; s < ax.nst; ++s) {
+            pos += (rest % ax.rad[s]) * ax.span[s];
+            rest /= ax.rad[s];
+        }
+        k_at[pos] = k;
+    }
+    return k_at;
 }
 
 bool finite_all(const double* p, size_t n) {
@@ -417,12 +433,15 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
         if (xs_used[x]) xbase.push_back(x * n2p);
     s->nstick = (int)stick_xy.size();
     s->nxcol = (int)xbase.size();
-    // potential, one contiguous (padded) plane per z: [z][x][y < n2p]
+    // potential, one contiguous (padded) plane per z: [z][x][y < n2p], every axis in the
+    // digit-reversed order in which the inverse FFTs leave real space
     const size_t nboxp = (size_t)n1 * n2p * n3;
     std::vector<double> vz(nboxp, 0.0);
-    for (int x = 0; x < n1; ++x)
-        for (int y = 0; y < n2; ++y)
-            for (int z = 0; z < n3; ++z) vz[((size_t)z * n1 + x) * n2p + y] = vloc_r[((size_t)x * n2 + y) * n3 + z];
+    const std::vector<int> ox = dif_order(s->plan.ax[0]), oy = dif_order(s->plan.ax[1]), oz = dif_order(s->plan.ax[2]);
+    for (int px = 0; px < n1; ++px)
+        for (int py = 0; py < n2; ++py)
+            for (int pz = 0; pz < n3; ++pz)
+                vz[((size_t)pz * n1 + px) * n2p + py] = vloc_r[((size_t)ox[px] * n2 + oy[py]) * n3 + oz[pz]];
     std::vector<float2> vzdd(nboxp);
     for (size_t i = 0; i < nboxp; ++i) {
         const float h = (float)vz[i];
@@ -752,7 +771,7 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
         SGW_CUDA(solve_grid(plan, nomega, nrhs, &grid), "solver occupancy");
         SGW_CUDA(solve_grid(plan, 1, chunk, &grid1), "solver occupancy");
     }
-    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(plan), &grid_r), "residual occupancy");
+    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(plan), &grid_r, kResThreads), "residual occupancy");
     grid_r = (int)std::min<size_t>(grid_r, np);
     // Krylov workspace of one launch (reused by the correction solves)
     int maxk = max_mv;
@@ -1203,7 +1222,7 @@ sgw_status sgw_solve_pershift(sgw_system* s, int npairs, const void* rhs, const 
     if ((r = stage_out(x, vb * npairs, out, "x", st)) != SGW_OK) return r;
     int grid = 0, grid_r = 0;
     SGW_CUDA(solve_grid(s->plan, 1, npairs, &grid), "solver occupancy");
-    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r), "residual occupancy");
+    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r, kResThreads), "residual occupancy");
     grid_r = std::min(grid_r, npairs);
     Carve c;
     const size_t o_seed = c.take(vb * (2 * ell + 3) * grid);
@@ -1327,7 +1346,7 @@ sgw_status sgw_residual(sgw_system* s, int nrhs, const void* rhs, const double* 
     if ((r = stage_in(rhs, vb * nrhs, in_r, st, "rhs")) != SGW_OK) return r;
     if ((r = stage_in(dpsi, vb * np, in_x, st, "dpsi")) != SGW_OK) return r;
     int grid = 0;
-    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid), "residual occupancy");
+    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid, kResThreads), "residual occupancy");
     grid = (int)std::min<size_t>(grid, np);
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t off_er = al(2 * vb * grid);

@@ -591,8 +591,8 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
                     w[g] = h;
                     acc = Ar::add(acc, Ar::mul(Ar::conj(vk[g]), h));
                 }
-                double2 a2[1] = {Ar::to_d(acc)};
-                block_sum<1>(a2, red, s_dot);
+                C a2[1] = {acc};
+                block_sum_c<1>(a2, red, s_dot);
             }
             const double a = s_dot[0].x;
             {
@@ -603,8 +603,8 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
                     w[g] = h;
                     acc = Ar::acc_norm(acc, h);
                 }
-                double2 a2[1] = {Ar::to_d(acc)};
-                block_sum<1>(a2, red, s_dot);
+                C a2[1] = {acc};
+                block_sum_c<1>(a2, red, s_dot);
             }
             const double bn = sqrt(s_dot[0].x);
             {
@@ -685,23 +685,49 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
         for (int j = tid; j < ns; j += nt)
             for (int i = 0; i < K; ++i) Yc[(size_t)i * ns + j] = Ar::from_d(Ysc[(size_t)i * ns + j]);
         __syncthreads();
-        // x_j = V y_j, shifts in tiles of 8
-        for (int j0 = 0; j0 < ns; j0 += 8) {
-            const int cnt = min(8, ns - j0);
-            for (int g = tid; g < npw; g += nt) {
-                C acc[8];
+        // x_j = V y_j, shifts in tiles of TJ (fewer live accumulators for the larger CTAs).  The
+        // tile's y coefficients are staged in the (now idle) FFT buffers of shared memory, KC
+        // Lanczos steps at a time; every thread reads them as broadcasts.
+        constexpr int TJ = NT >= 384 ? 4 : 8;
+        {
+            C* ys = reinterpret_cast<C*>(smem + L.sticks);
+            const int KC = (L.red - L.sticks) / (TJ * (int)sizeof(C));
+            for (int j0 = 0; j0 < ns; j0 += TJ) {
+                const int cnt = min(TJ, ns - j0);
+                int Kt = 0;   // the tile's longest Lanczos run (y is zero beyond each shift's own)
+                for (int t = 0; t < cnt; ++t) Kt = max(Kt, kc[j0 + t]);
+                if (Kt == 0)
+                    for (size_t i = tid; i < (size_t)cnt * npw; i += nt) X[(size_t)j0 * npw + i] = cz();
+                for (int k0 = 0; k0 < Kt; k0 += KC) {
+                    const int kn = min(KC, Kt - k0);
+                    __syncthreads();
+                    for (int i = tid; i < kn * TJ; i += nt) {
+                        const int ii = i / TJ, t = i - ii * TJ;
+                        ys[i] = t < cnt ? Yc[(size_t)(k0 + ii) * ns + j0 + t] : Ar::zero();
+                    }
+                    __syncthreads();
+                    for (int g = tid; g < npw; g += nt) {
+                        C acc[TJ];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) acc[t] = Ar::zero();
-                for (int i = 0; i < K; ++i) {
-                    const C v = V[(size_t)i * npw + g];
-                    const C* yr = Yc + (size_t)i * ns + j0;
+                        for (int t = 0; t < TJ; ++t) acc[t] = Ar::zero();
+                        const C* vg = V + (size_t)k0 * npw + g;
+#pragma unroll 2
+                        for (int i = 0; i < kn; ++i) {
+                            const C v = vg[(size_t)i * npw];
+                            const C* yr = ys + i * TJ;
 #pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        if (t < cnt) acc[t] = Ar::add(acc[t], Ar::mul(yr[t], v));
+                            for (int t = 0; t < TJ; ++t) acc[t] = Ar::add(acc[t], Ar::mul(yr[t], v));
+                        }
+#pragma unroll
+                        for (int t = 0; t < TJ; ++t) {
+                            if (t < cnt) {
+                                double2* xo = X + (size_t)(j0 + t) * npw + g;
+                                const double2 d = Ar::to_d(acc[t]);
+                                *xo = k0 == 0 ? d : cadd(*xo, d);
+                            }
+                        }
+                    }
                 }
-#pragma unroll
-                for (int t = 0; t < 8; ++t)
-                    if (t < cnt) X[(size_t)(j0 + t) * npw + g] = Ar::to_d(acc[t]);
             }
         }
         for (int j = tid; j < ns; j += nt) {
@@ -755,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, co
 //   rel[q] = |res| / |P_c rhs_r|,  cert[q] = |res| / (eta |x_rj|),
 // and, when store is given, store[i] = -res (the right-hand side of the correction
 // equation in the solver's convention b = -P_c rhs).
-__global__ void __launch_bounds__(kThreads, 1) residual_kernel(Plan P, int nrhs, int ns, const int* __restrict__ list,
+__global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nrhs, int ns, const int* __restrict__ list,
                                                                int nlist, const double2* __restrict__ rhs,
                                                                const double* __restrict__ e_ref,
                                                                const double* __restrict__ omega, double eta,
@@ -1086,7 +1112,7 @@ cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* lis
     const int smem = apply_smem_bytes(P0);
     cudaError_t e = allow_max_smem((const void*)residual_kernel);
     if (e != cudaSuccess) return e;
-    residual_kernel<<<grid, kThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
+    residual_kernel<<<grid, kResThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
                                                   cert, store, eta_s);
     return cudaGetLastError();
 }
@@ -1121,7 +1147,7 @@ const void* lanczos_ptr(int nt) {
     if (nt == 384) return (const void*)lanczos_solve_kernel<Ar, 384>;
     return (const void*)lanczos_solve_kernel<Ar, 256>;
 }
-int lanczos_threads(int requested) { return requested == 384 || requested == 512 ? requested : 256; }
+int lanczos_threads(int requested) { return requested == 256 || requested == 512 ? requested : 384; }
 }  // namespace
 
 cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int threads, int* grid) {

@@ -88,7 +88,7 @@ extern "C" sgw_status sgw_residual_noalloc(sgw_system* sys, int nrhs, const void
         scratch = g_scratch_ptr[dev];
     }
     int grid = 0;
-    e = resident_grid(residual_kernel_ptr(), apply_smem_bytes(*P), &grid);
+    e = resident_grid(residual_kernel_ptr(), apply_smem_bytes(*P), &grid, kResThreads);
     if (e != cudaSuccess) return noalloc_fail(SGW_ECUDA, cudaGetErrorString(e));
     grid = (int)std::min<size_t>({(size_t)grid, kScratchElems / per_cta, np});
     // The kernel writes every scratch element it reads before reading it: nothing to clear.

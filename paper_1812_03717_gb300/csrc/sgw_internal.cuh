@@ -2,7 +2,9 @@
 //
 // Data layout in device memory (all complex values are FP64 pairs, double2):
 //   plane-wave vectors      [nvec][npw]              canonical G order (Miller lexicographic)
-//   local potential         [N3][N1][N2p]            one contiguous (padded) xy-plane per z
+//   local potential         [N3][N1][N2p]            one contiguous (padded) xy-plane per z, each
+//                                                    axis in the digit-reversed order that the
+//                                                    in-place FFT leaves real space in
 //   stick buffer (on chip)  [nstick][N3p]            z-columns of the box that hold a G (N3p odd)
 //   plane buffer (on chip)  [nplanes][N1][N2p]       a few xy-planes of the box, rows padded to odd N2p
 //   KB projectors           [nproj][npw]             <k+G|beta_p>
@@ -22,6 +24,7 @@
 namespace sgw {
 
 constexpr int kThreads = 256;          // threads per CTA of the library kernels
+constexpr int kResThreads = 384;       // threads per CTA of the FP64 true-residual kernel
 constexpr int kMaxThreads = 512;       // largest CTA any kernel launches (sizes the reduction scratch)
 constexpr int kMaxStages = 12;         // radix stages per axis (N <= 5^12)
 constexpr int kMaxShifts = 512;        // frequencies per solve
@@ -31,7 +34,8 @@ constexpr int kRedSlots = 16;          // complex values reduced per block reduc
 struct AxisPlan {
     int n;
     int nst;
-    int rad[kMaxStages];
+    int rad[kMaxStages];    // radices R_0, R_1, ... (R_0 acts on the full length)
+    int span[kMaxStages];   // m_s = n / (R_0 ... R_s)
 };
 
 // Everything an H application needs; passed by value to kernels.
@@ -179,8 +183,10 @@ struct ArF64 {
     static __device__ __forceinline__ C from_d(double2 a) { return a; }
     static __device__ __forceinline__ double2 to_d(C a) { return a; }
     static __device__ __forceinline__ C zero() { return cz(); }
-    // complex times real potential sample
-    static __device__ __forceinline__ C mulv(C a, const double* v, const float2*, size_t i) { return cscal(a, v[i]); }
+    // the potential sample in this policy's format, and the product with it
+    using VT = double;
+    static __device__ __forceinline__ VT vload(const Plan& P, size_t i) { return P.vloc[i]; }
+    static __device__ __forceinline__ C vmul(C a, VT v) { return cscal(a, v); }
     // real scalars and reciprocal-space data in this policy's format
     using R = double;
     static __device__ __forceinline__ R real(double x) { return x; }
@@ -245,9 +251,10 @@ struct ArDF {
     static __device__ __forceinline__ C from_d(double2 a) { return mk(dd_from(a.x), dd_from(a.y)); }
     static __device__ __forceinline__ double2 to_d(C a) { return make_double2(dd_to(re(a)), dd_to(im(a))); }
     static __device__ __forceinline__ C zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-    static __device__ __forceinline__ C mulv(C a, const double*, const float2* v, size_t i) {
-        const float2 t = v[i];
-        const dd c{t.x, t.y};
+    using VT = float2;
+    static __device__ __forceinline__ VT vload(const Plan& P, size_t i) { return P.vloc_dd[i]; }
+    static __device__ __forceinline__ C vmul(C a, VT v) {
+        const dd c{v.x, v.y};
         return mk(dd_mul(re(a), c), dd_mul(im(a), c));
     }
     using R = dd;
@@ -278,9 +285,46 @@ SGW_CONST(kS52, 0.58778525229247312917)   // sin(4 pi / 5)
 SGW_CONST(kHalf, 0.5)
 #undef SGW_CONST
 
+// Block sums of NV complex values per thread in the policy's format: the FP64 pair goes
+// through block_sum; float-float values are reduced within each warp in float-float on the
+// FP32 pipes (shuffles of the four floats), and only the per-warp partials are converted
+// and summed in FP64 by NV threads (GB300's FP64 pipe is ~1/64 of its FP32 rate, so a
+// shuffle tree of FP64 additions costs more than the dot products it finishes).
+template <int NV>
+__device__ __forceinline__ void block_sum_c(double2 (&v)[NV], double2* red, double2* out) {
+    block_sum<NV>(v, red, out);
+}
+template <int NV>
+__device__ __forceinline__ void block_sum_c(float4 (&v)[NV], double2* red, double2* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float4 t;
+            t.x = __shfl_down_sync(0xffffffffu, v[i].x, o);
+            t.y = __shfl_down_sync(0xffffffffu, v[i].y, o);
+            t.z = __shfl_down_sync(0xffffffffu, v[i].z, o);
+            t.w = __shfl_down_sync(0xffffffffu, v[i].w, o);
+            v[i] = ArDF::add(v[i], t);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[warp * kRedSlots + i] = ArDF::to_d(v[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double2 s = cz();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[w * kRedSlots + threadIdx.x]);
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
 // out[v] = sum_g conj(src_v[g]) x[g] for v < nv, with src the occupied states (which = 0) or
 // the projectors (which = 1) in the policy's format; per-thread sums in the policy's
-// arithmetic, the block reduction in FP64.  out must hold nv rounded up to 8.
+// arithmetic, the block reduction by block_sum_c.  out must hold nv rounded up to 8.
 template <class Ar, int WHICH>
 __device__ __forceinline__ void block_dots_ar(const Plan& P, int nv, const typename Ar::C* x, double2* red,
                                               double2* out) {
@@ -302,10 +346,7 @@ __device__ __forceinline__ void block_dots_ar(const Plan& P, int nv, const typen
                 }
             }
         }
-        double2 a2[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) a2[i] = Ar::to_d(acc[i]);
-        block_sum<8>(a2, red, out + v0);
+        block_sum_c<8>(acc, red, out + v0);
     }
 }
 
@@ -351,61 +392,91 @@ __device__ __forceinline__ void dft_small(typename Ar::C (&v)[5], int R) {
     }
 }
 
-// In-place batched FFT of `nlines` lines of length ax.n held in shared memory, `lpp` lines
-// per plane, planes `pstride` elements apart.  Line l = p * lpp + q starts at
-// base(l) = p * pstride + (line_base ? line_base[q] : q * ls), element i at base + i * es.
-// Stockham autosort, decimation in time: stage with radix R and span Ns reads
-// x[j + k N/R], twiddles by w^(k (j mod Ns) N/(Ns R)), and writes the R outputs to
-// (j / Ns) Ns R + (j mod Ns) + k Ns.  Each stage reads all of a group of lines into
-// registers before any thread writes, so no second buffer is needed.
-// tw[m] = exp(-2 pi i m / n).  All threads of the CTA must call.
-template <class Ar, int SIGN>
-__device__ void fft_lines(typename Ar::C* data, int nlines, int lpp, int pstride, const int* __restrict__ line_base,
-                          int ls, int es, const AxisPlan& ax, const typename Ar::C* tw) {
+// Butterfly `b` of a stage of fft_inplace: its first element's index in `data`.
+__device__ __forceinline__ int fft_bfly_base(int b, int nb, int m, int L, int lpp, int pstride,
+                                             const int* __restrict__ line_base, int ls, int es, int& j) {
+    const int l = b / nb, rem = b - l * nb;
+    const int blk = rem / m;
+    j = rem - blk * m;
+    const int pl = l / lpp, q = l - pl * lpp;
+    return pl * pstride + (line_base ? line_base[q] : q * ls) + (blk * L + j) * es;
+}
+
+// One stage of fft_inplace with a compile-time radix R: every butterfly reads its R
+// elements m * es apart, twiddles (before the DFT for DIT, after it for DIF), applies the
+// R-point DFT and writes back to the same places.  Butterflies b and b + nt run together.
+template <class Ar, int SIGN, bool DIF, int R>
+__device__ __forceinline__ void fft_stage(typename Ar::C* data, int total, int nb, int m, int lpp, int pstride,
+                                          const int* __restrict__ line_base, int ls, int es,
+                                          const typename Ar::C* tw, int twstep) {
     using C = typename Ar::C;
-    const int N = ax.n;
-    int Ns = 1;
-    for (int st = 0; st < ax.nst; ++st) {
-        const int R = ax.rad[st];
-        const int nb = N / R;
-        const int lpg = max(1, (int)blockDim.x / nb);
-        const int stride = N / (Ns * R);
-        for (int l0 = 0; l0 < nlines; l0 += lpg) {
-            const int t = threadIdx.x;
-            const int l = l0 + t / nb;
-            const int j = t % nb;
-            const bool act = (t < lpg * nb) && (l < nlines);
-            C v[5];
-            int base = 0;
-            const int jm = j % Ns;
-            if (act) {
-                const int pl = l / lpp, q = l - pl * lpp;
-                base = pl * pstride + (line_base ? line_base[q] : q * ls);
+    const int L = m * R, mes = m * es, nt = blockDim.x;
+    for (int b0 = threadIdx.x; b0 < total; b0 += 2 * nt) {
+        const bool two = b0 + nt < total;
+        int j[2], base[2];
+        C v[2][5];
+        base[0] = fft_bfly_base(b0, nb, m, L, lpp, pstride, line_base, ls, es, j[0]);
+        base[1] = two ? fft_bfly_base(b0 + nt, nb, m, L, lpp, pstride, line_base, ls, es, j[1]) : base[0];
+        if (!two) j[1] = j[0];
 #pragma unroll
-                for (int k = 0; k < 5; ++k)
-                    if (k < R) v[k] = data[base + (j + k * nb) * es];
-                if (jm != 0) {   // the first stage (Ns = 1) and every j with j mod Ns = 0 need no twiddle
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
-                    for (int k = 1; k < 5; ++k) {
-                        if (k < R) {
-                            C w = tw[jm * k * stride];
-                            if (SIGN > 0) w = Ar::conj(w);
-                            v[k] = Ar::mul(v[k], w);
-                        }
-                    }
+            for (int k = 0; k < R; ++k) v[u][k] = data[base[u] + k * mes];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!DIF && j[u] != 0) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) {
+                    C w = tw[j[u] * k * twstep];
+                    if (SIGN > 0) w = Ar::conj(w);
+                    v[u][k] = Ar::mul(v[u][k], w);
                 }
-                dft_small<Ar, SIGN>(v, R);
             }
-            __syncthreads();
-            if (act) {
-                const int d0 = (j / Ns) * Ns * R + jm;
+            dft_small<Ar, SIGN>(v[u], R);
+            if (DIF && j[u] != 0) {
 #pragma unroll
-                for (int k = 0; k < 5; ++k)
-                    if (k < R) data[base + (d0 + k * Ns) * es] = v[k];
+                for (int k = 1; k < R; ++k) {
+                    C w = tw[j[u] * k * twstep];
+                    if (SIGN > 0) w = Ar::conj(w);
+                    v[u][k] = Ar::mul(v[u][k], w);
+                }
             }
-            __syncthreads();
         }
-        Ns *= R;
+#pragma unroll
+        for (int k = 0; k < R; ++k) data[base[0] + k * mes] = v[0][k];
+        if (two) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) data[base[1] + k * mes] = v[1][k];
+        }
+    }
+}
+
+// In-place batched mixed-radix FFT (sign SIGN: exp(SIGN 2 pi i n k / N), unnormalised) of
+// `nlines` lines of length N = ax.n in shared memory, `lpp` lines per plane, planes
+// `pstride` elements apart; line l = p * lpp + q starts at
+// p * pstride + (line_base ? line_base[q] : q * ls), element i at base + i * es.
+// Decimation in frequency (DIF) takes natural order to digit-reversed order: with
+// k = r_0 + R_0 (r_1 + R_1 (r_2 + ...)), X_k lands at position sum_s r_s m_s.  Decimation in
+// time (DIT, the stages in reverse) takes that order back to natural order.  A stage with
+// radix R on blocks of L = m R elements reads x[blk L + j + k m] (k < R), applies the
+// R-point DFT and the twiddles w_L^(j k), and writes back to the same places, so the
+// butterflies of a stage are disjoint and need no barrier between them: one barrier per
+// stage.  tw[i] = exp(-2 pi i i / N).  All threads of the CTA must call.
+template <class Ar, int SIGN, bool DIF>
+__device__ void fft_inplace(typename Ar::C* data, int nlines, int lpp, int pstride, const int* __restrict__ line_base,
+                            int ls, int es, const AxisPlan& ax, const typename Ar::C* tw) {
+    const int N = ax.n;
+    for (int si = 0; si < ax.nst; ++si) {
+        const int s = DIF ? si : ax.nst - 1 - si;
+        const int R = ax.rad[s], m = ax.span[s];
+        const int nb = N / R, twstep = N / (m * R), total = nlines * nb;
+        switch (R) {
+            case 4: fft_stage<Ar, SIGN, DIF, 4>(data, total, nb, m, lpp, pstride, line_base, ls, es, tw, twstep); break;
+            case 3: fft_stage<Ar, SIGN, DIF, 3>(data, total, nb, m, lpp, pstride, line_base, ls, es, tw, twstep); break;
+            case 5: fft_stage<Ar, SIGN, DIF, 5>(data, total, nb, m, lpp, pstride, line_base, ls, es, tw, twstep); break;
+            default: fft_stage<Ar, SIGN, DIF, 2>(data, total, nb, m, lpp, pstride, line_base, ls, es, tw, twstep); break;
+        }
+        __syncthreads();
     }
 }
 
@@ -430,6 +501,9 @@ __device__ __forceinline__ void load_twiddles(const Plan& P, unsigned char* smem
 // x into the sticks; inverse FFT along z on the sticks; per group of z-planes: scatter the
 // planes, inverse FFT along y (only the x-columns that hold sticks) and x, multiply by V(r),
 // forward FFT along x and y, gather back into the sticks; forward FFT along z; gather the
+// (the inverse FFTs are decimation in frequency, leaving real space digit-reversed along
+// each axis, where V is stored in the same order; the forward FFTs are decimation in time
+// and return to natural order, so the permutation costs nothing);
 // sphere, scale by 1/N^3 and add T_G x_G + sum_p D_p c_p beta_p(G); optionally project with
 // P_c and subtract z x.  All vector arithmetic in the policy's arithmetic; the block
 // reductions of the projections in FP64.
@@ -465,7 +539,7 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
     __syncthreads();
     for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = x[g];
     __syncthreads();
-    fft_lines<Ar, +1>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
+    fft_inplace<Ar, +1, true>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
 
     // nplanes xy-planes per pass: one set of barriers serves all of them
     const int n2p = P.n2p, psz = n1 * n2p;
@@ -478,20 +552,31 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
             plane[pl * psz + P.stick_xy[s]] = sticks[s * n3p + iz0 + pl];
         }
         __syncthreads();
-        fft_lines<Ar, +1>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);  // y, occupied x only
-        fft_lines<Ar, +1>(plane, npl * n2, n2, psz, nullptr, 1, n2p, P.ax[0], tw1);          // x, every y
+        fft_inplace<Ar, +1, true>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);  // y, occupied x
+        fft_inplace<Ar, +1, true>(plane, npl * n2, n2, psz, nullptr, 1, n2p, P.ax[0], tw1);          // x, every y
         const size_t zo = (size_t)iz0 * psz;
-        for (int i = tid; i < npl * psz; i += nt) plane[i] = Ar::mulv(plane[i], P.vloc, P.vloc_dd, zo + i);
+        {   // four potential loads in flight per thread
+            const int cnt = npl * psz;
+            for (int i0 = tid; i0 < cnt; i0 += 4 * nt) {
+                typename Ar::VT vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * nt < cnt) vv[u] = Ar::vload(P, zo + i0 + u * nt);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u * nt < cnt) plane[i0 + u * nt] = Ar::vmul(plane[i0 + u * nt], vv[u]);
+            }
+        }
         __syncthreads();
-        fft_lines<Ar, -1>(plane, npl * n2, n2, psz, nullptr, 1, n2p, P.ax[0], tw1);
-        fft_lines<Ar, -1>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);
+        fft_inplace<Ar, -1, false>(plane, npl * n2, n2, psz, nullptr, 1, n2p, P.ax[0], tw1);
+        fft_inplace<Ar, -1, false>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);
         for (int i = tid; i < npl * nst; i += nt) {
             const int pl = i / nst, s = i - pl * nst;
             sticks[s * n3p + iz0 + pl] = plane[pl * psz + P.stick_xy[s]];
         }
         __syncthreads();
     }
-    fft_lines<Ar, -1>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
+    fft_inplace<Ar, -1, false>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
 
     // gather + kinetic + non-local
     {
