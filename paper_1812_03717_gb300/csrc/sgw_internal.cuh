@@ -418,12 +418,33 @@ __device__ __forceinline__ void dft_small(typename Ar::C (&v)[5], int R) {
 // index varies fastest with b, so the eight threads of a quarter-warp read the same offset
 // of eight neighbouring lines: line starts N3p or N2p (odd) elements apart, or adjacent
 // rows, which fall in distinct shared-memory banks for 16-byte elements.
-__device__ __forceinline__ int fft_bfly_base(int b, int nlines, int m, int L, int lpp, int pstride,
+// q = a / n, r = a - q n for 0 <= a < 2^22 and n >= 1, given inv = 1.0f / n: the float
+// quotient is within one of the true one and is corrected exactly (an integer division by a
+// run-time divisor costs several times more instructions than this).
+__device__ __forceinline__ int divmod_f(int a, int n, float inv, int& r) {
+    int q = __float2int_rz(__int2float_rn(a) * inv);
+    r = a - q * n;
+    if (r < 0) {
+        --q;
+        r += n;
+    } else if (r >= n) {
+        ++q;
+        r -= n;
+    }
+    return q;
+}
+
+struct FftIdx {   // per-stage divisors of fft_bfly_base and their reciprocals
+    int nlines, m, lpp;
+    float inv_nlines, inv_m, inv_lpp;
+};
+
+__device__ __forceinline__ int fft_bfly_base(int b, const FftIdx& d, int L, int pstride,
                                              const int* __restrict__ line_base, int ls, int es, int& j) {
-    const int rem = b / nlines, l = b - rem * nlines;
-    const int blk = rem / m;
-    j = rem - blk * m;
-    const int pl = l / lpp, q = l - pl * lpp;
+    int l, q;
+    const int rem = divmod_f(b, d.nlines, d.inv_nlines, l);
+    const int blk = divmod_f(rem, d.m, d.inv_m, j);
+    const int pl = divmod_f(l, d.lpp, d.inv_lpp, q);
     return pl * pstride + (line_base ? line_base[q] : q * ls) + (blk * L + j) * es;
 }
 
@@ -436,12 +457,13 @@ __device__ __forceinline__ void fft_stage(typename Ar::C* data, int total, int n
                                           const typename Ar::C* tw, int twstep) {
     using C = typename Ar::C;
     const int L = m * R, mes = m * es, nt = blockDim.x;
+    const FftIdx d{nlines, m, lpp, 1.0f / (float)nlines, 1.0f / (float)m, 1.0f / (float)lpp};
     for (int b0 = threadIdx.x; b0 < total; b0 += 2 * nt) {
         const bool two = b0 + nt < total;
         int j[2], base[2];
         C v[2][5];
-        base[0] = fft_bfly_base(b0, nlines, m, L, lpp, pstride, line_base, ls, es, j[0]);
-        base[1] = two ? fft_bfly_base(b0 + nt, nlines, m, L, lpp, pstride, line_base, ls, es, j[1]) : base[0];
+        base[0] = fft_bfly_base(b0, d, L, pstride, line_base, ls, es, j[0]);
+        base[1] = two ? fft_bfly_base(b0 + nt, d, L, pstride, line_base, ls, es, j[1]) : base[0];
         if (!two) j[1] = j[0];
 #pragma unroll
         for (int u = 0; u < 2; ++u)
