@@ -28,7 +28,9 @@ What it computes, by plain definition (no blocking, fusion or reordering):
   certificate |r| / (|Im z| |g|);
 * one k-point's contribution to the density response of Eq. 5 by the paper's route
   (Sternheimer solutions at +-(omega + i eta), real-space product with the unperturbed
-  periodic part, Fourier transform back) and by the sum over the eigenstates of H_{k+q}.
+  periodic part, Fourier transform back) and by the sum over the eigenstates of H_{k+q};
+* the spherically truncated Coulomb potential of Sec. 2.6, the dielectric matrix of Eq. 4
+  and its inverse, and the correlation part W-bar of the screened interaction (Eq. 9).
 
 Each function cites the passage of the paper it restates.
 """
@@ -383,3 +385,51 @@ def density_response_sos(h_kq, n_occ_kq, psi_k, miller_k, miller_kq, eps_k, gp_m
             f = 1.0 / (eps_k[v] + wc - ec) + 1.0 / (eps_k[v] - wc - ec)
             out[:, :, j] += weight * (m.conj() * f) @ m.T
     return out
+
+
+# --------------------------------------------- Eq. 4, 9 and Sec. 2.6: epsilon^-1 and W-bar
+
+def coulomb_spherical(qg, r_cut):
+    """v(q) = 4 pi / q^2 [1 - cos(q R_cut)] (Hartree units, e^2 / (4 pi eps0) = 1), the
+    Coulomb potential cut off at distance R_cut (Sec. 2.6); its q -> 0 limit is 2 pi R_cut^2.
+    r_cut <= 0 gives the bare 4 pi / q^2 (q = 0 is then an error)."""
+    q = np.linalg.norm(np.atleast_2d(np.asarray(qg, np.float64)), axis=1)
+    if r_cut <= 0:
+        if np.any(q == 0):
+            raise ValueError("q + G = 0 needs a truncated Coulomb potential")
+        return 4.0 * math.pi / q ** 2
+    out = np.empty_like(q)
+    small = q * r_cut < 1e-4
+    qs = q[~small]
+    out[~small] = 4.0 * math.pi / qs ** 2 * (1.0 - np.cos(qs * r_cut))
+    x = q[small] * r_cut                     # series of 4 pi R^2 (1 - cos x) / x^2
+    out[small] = 4.0 * math.pi * r_cut ** 2 * (0.5 - x ** 2 / 24.0 + x ** 4 / 720.0)
+    return out
+
+
+def screened_coulomb(dn, qg, volume, r_cut):
+    """From the accumulated density response dn[G][G'][w] (Eq. 5, weights included):
+        eps[G][G'] = delta - dn[G][G'] v(q + G') / Omega        (Eq. 4, the response to the
+                                                                  Coulomb potential of a unit
+                                                                  plane-wave charge at q + G')
+        W-bar[G][G'] = v(q + G) (eps^-1[G][G'] - delta)          (Eq. 9)
+    per frequency by a dense inverse; rows and columns with q + G = 0 keep only their diagonal
+    in eps^-1 (Sec. 2.4).  Returns (eps^-1, W-bar), each [G][G'][w]."""
+    dn = np.asarray(dn, np.complex128)
+    n, _, nw = dn.shape
+    v = coulomb_spherical(qg, r_cut)
+    zero = np.linalg.norm(np.atleast_2d(qg), axis=1) == 0
+    einv = np.zeros_like(dn)
+    wbar = np.zeros_like(dn)
+    eye = np.eye(n)
+    for j in range(nw):
+        eps = eye - dn[:, :, j] * v[None, :] / volume
+        inv = np.linalg.inv(eps)
+        for g in np.nonzero(zero)[0]:
+            d = inv[g, g]
+            inv[g, :] = 0.0
+            inv[:, g] = 0.0
+            inv[g, g] = d
+        einv[:, :, j] = inv
+        wbar[:, :, j] = v[:, None] * (inv - eye)
+    return einv, wbar
