@@ -226,6 +226,25 @@ sgw_status sgw_density_response(sgw_system* sys, int n_v, int n_pert, const void
                                 int nomega, const double* omega, double eta, double weight, double tol,
                                 const sgw_solve_opts* opts, void* dn, sgw_report* report);
 
+/* Screening from an accumulated density response (Sec. 2.4, Eq. 4 and 9, with the Coulomb
+ * potential of Sec. 2.6).  Per frequency j:
+ *   v(q)          = 4 pi / |q|^2 [1 - cos(|q| r_cut)]   (spherical truncation; its limit
+ *                   2 pi r_cut^2 at q = 0; the bare 4 pi / |q|^2 when r_cut <= 0; Hartree units)
+ *   eps[G][G']    = delta - dn[G][G'][j] v(q + G') / volume   (the response to the Coulomb
+ *                   potential of a unit plane-wave charge at q + G')
+ *   eps_inv       = eps^-1 by Gauss-Jordan elimination with partial pivoting in FP64; rows and
+ *                   columns with q + G = 0 keep only their diagonal
+ *   wbar[G][G'][j] = v(q + G) (eps_inv[G][G'] - delta)
+ *   dn       complex [n_g][n_g][nomega] (host or device): sgw_density_response's output summed
+ *            over k-points (weights included).
+ *   qg       [n_g][3] host: the Cartesian vectors q + G (bohr^-1) of the perturbations, in the
+ *            order of dn's rows.   volume: cell volume (bohr^3) > 0.
+ *   eps_inv  complex [n_g][n_g][nomega] (host or device) or NULL; wbar likewise, required.
+ * n_g <= 64 (else SGW_EUNSUPPORTED).  q + G = 0 with r_cut <= 0 is SGW_EINVAL.  A singular
+ * eps at some frequency gives NaN outputs for it and SGW_ENOCONV. */
+sgw_status sgw_screened_coulomb(int n_g, int nomega, const void* dn, const double* qg, double volume, double r_cut,
+                                void* eps_inv, void* wbar, void* stream);
+
 /* True FP64 residual of given solutions: for every pair
  *   r = -P_c rhs - (P_c H P_c - z) dpsi,  rel_res = |r| / |P_c rhs|,  cert = |r| / (eta |dpsi|).
  * Since P_c H P_c - z is normal with every eigenvalue at distance >= eta from 0, cert bounds

@@ -1100,6 +1100,45 @@ sgw_status sgw_density_response(sgw_system* s, int n_v, int n_pert, const void* 
     return rs;
 }
 
+sgw_status sgw_screened_coulomb(int n_g, int nomega, const void* dn, const double* qg, double volume, double r_cut,
+                                void* eps_inv, void* wbar, void* stream) {
+    g_err.clear();
+    if (n_g < 0 || nomega < 0) return fail(SGW_EINVAL, "negative size");
+    if (n_g == 0 || nomega == 0) return SGW_OK;
+    if (!dn || !qg || !wbar) return fail(SGW_EINVAL, "NULL argument");
+    if (n_g > 64) return fail(SGW_EUNSUPPORTED, "n_g above 64 (the matrix is inverted in shared memory)");
+    if (!(volume > 0.0) || !std::isfinite(volume)) return fail(SGW_EINVAL, "volume must be positive");
+    if (!std::isfinite(r_cut)) return fail(SGW_EINVAL, "non-finite r_cut");
+    if (is_device_ptr(qg)) return fail(SGW_EINVAL, "qg must be a host array");
+    if (!finite_all(qg, 3 * (size_t)n_g)) return fail(SGW_EINVAL, "non-finite q + G");
+    if (r_cut <= 0.0)
+        for (int g = 0; g < n_g; ++g)
+            if (qg[3 * g] == 0.0 && qg[3 * g + 1] == 0.0 && qg[3 * g + 2] == 0.0)
+                return fail(SGW_EINVAL, "q + G = 0 needs a truncated Coulomb potential (r_cut > 0)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t mb = sizeof(double2) * (size_t)n_g * n_g * nomega;
+    Staged in, q, oe, ow, flag;
+    sgw_status r;
+    if ((r = stage_in(dn, mb, in, st, "dn")) != SGW_OK) return r;
+    if ((r = stage_in(qg, sizeof(double) * 3 * (size_t)n_g, q, st, "q + G")) != SGW_OK) return r;
+    if (eps_inv && (r = stage_out(eps_inv, mb, oe, "eps_inv", st)) != SGW_OK) return r;
+    if ((r = stage_out(wbar, mb, ow, "wbar", st)) != SGW_OK) return r;
+    SGW_CUDA(cudaMallocAsync(&flag.dev, sizeof(int), st), "flag allocation");
+    flag.owned = true;
+    flag.st = st;
+    SGW_CUDA(cudaMemsetAsync(flag.dev, 0, sizeof(int), st), "memset");
+    SGW_CUDA(launch_screening(n_g, nomega, (const double2*)in.dev, (const double*)q.dev, 1.0 / volume, r_cut,
+                              eps_inv ? (double2*)oe.dev : nullptr, (double2*)ow.dev, (int*)flag.dev, st),
+             "screening kernel");
+    int bad = 0;
+    SGW_CUDA(cudaMemcpyAsync(&bad, flag.dev, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+    if (eps_inv && (r = finish_out(oe, st, "eps_inv copy")) != SGW_OK) return r;
+    if ((r = finish_out(ow, st, "wbar copy")) != SGW_OK) return r;
+    SGW_CUDA(cudaStreamSynchronize(st), "screening");
+    if (bad) return fail(SGW_ENOCONV, "epsilon is singular at some frequency (its outputs are NaN)");
+    return SGW_OK;
+}
+
 static sgw_status precond_common(sgw_system* s, int npairs, const double2* rhs_d, const double* eref_d,
                                  const double* om_d, const double* delta_d, double eta, int precond,
                                  const sgw_mlp* mlp, double* d_d, cudaStream_t st) {

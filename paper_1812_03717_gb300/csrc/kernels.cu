@@ -506,7 +506,6 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
 template <class Ar, int NT>
 __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_ab[2];          // alpha_k, beta_{k+1}
     __shared__ double2 s_dot[kRedSlots];
     __shared__ int s_r, s_nact, s_kmax, s_fail;
     load_twiddles<Ar>(P, smem);
@@ -904,6 +903,106 @@ __global__ void __launch_bounds__(kDnP * kDnJ) density_kernel(int n_v, int n_p, 
     }
 }
 
+// ----------------------------------------------- screening: epsilon^-1 and W-bar (Eq. 4, 9)
+//
+// One CTA per frequency j.  v(q + G) is the Coulomb potential cut off at R_cut (Sec. 2.6:
+// 4 pi / q^2 [1 - cos(q R_cut)], its series 4 pi R^2 (1/2 - x^2/24 + x^4/720), x = q R, for
+// x < 1e-4; the bare 4 pi / q^2 when R_cut <= 0).  The dielectric matrix
+//   eps[G][G'] = delta - dn[G][G'][j] v(q + G') / Omega
+// (the response to the Coulomb potential of a unit plane-wave charge at q + G') is inverted
+// in shared memory by Gauss-Jordan elimination with partial pivoting on [eps | 1] in FP64;
+// rows and columns with q + G = 0 keep only their diagonal (Sec. 2.4), and
+//   W-bar[G][G'] = v(q + G) (eps^-1[G][G'] - delta).
+// A zero or non-finite pivot marks the frequency singular: its outputs are NaN and *bad is set.
+__device__ __forceinline__ double coulomb_cut(double q, double r_cut) {
+    if (r_cut <= 0.0) return 4.0 * M_PI / (q * q);
+    const double x = q * r_cut;
+    if (x < 1e-4) return 4.0 * M_PI * r_cut * r_cut * (0.5 - x * x / 24.0 + x * x * x * x / 720.0);
+    return 4.0 * M_PI / (q * q) * (1.0 - cos(x));
+}
+
+__global__ void __launch_bounds__(kThreads) screening_kernel(int n, int nw, const double2* __restrict__ dn,
+                                                             const double* __restrict__ qg, double inv_vol,
+                                                             double r_cut, double2* __restrict__ einv,
+                                                             double2* __restrict__ wbar, int* __restrict__ bad) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w2 = 2 * n + 1;                       // row stride of [eps | 1] (odd: bank spread)
+    double2* a = reinterpret_cast<double2*>(smem);  // [n][w2]
+    double* v = reinterpret_cast<double*>(a + (size_t)n * w2);
+    double2* f = reinterpret_cast<double2*>(v + n + (n & 1));   // column factors
+    __shared__ int s_piv, s_bad;
+    const int j = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    for (int g = tid; g < n; g += nt) {
+        const double q = sqrt(qg[3 * g] * qg[3 * g] + qg[3 * g + 1] * qg[3 * g + 1] + qg[3 * g + 2] * qg[3 * g + 2]);
+        v[g] = coulomb_cut(q, r_cut);
+    }
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int i = tid; i < n * 2 * n; i += nt) {
+        const int r = i / (2 * n), c = i - r * 2 * n;
+        double2 e;
+        if (c < n) {
+            const double2 d = dn[((size_t)r * n + c) * nw + j];
+            const double s = v[c] * inv_vol;
+            e = make_double2((r == c ? 1.0 : 0.0) - d.x * s, -d.y * s);
+        } else {
+            e = make_double2(c - n == r ? 1.0 : 0.0, 0.0);
+        }
+        a[(size_t)r * w2 + c] = e;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (tid == 0) {
+            int p = k;
+            double best = -1.0;
+            for (int i = k; i < n; ++i) {
+                const double m = cabs2(a[(size_t)i * w2 + k]);
+                if (m > best) {
+                    best = m;
+                    p = i;
+                }
+            }
+            if (!(best > 0.0) || !isfinite(best)) s_bad = 1;
+            s_piv = p;
+        }
+        __syncthreads();
+        if (s_bad) break;
+        const int p = s_piv;
+        if (p != k)
+            for (int c = tid; c < 2 * n; c += nt) {
+                const double2 t = a[(size_t)k * w2 + c];
+                a[(size_t)k * w2 + c] = a[(size_t)p * w2 + c];
+                a[(size_t)p * w2 + c] = t;
+            }
+        __syncthreads();
+        const double2 inv = cdiv(make_double2(1.0, 0.0), a[(size_t)k * w2 + k]);
+        __syncthreads();
+        for (int c = tid; c < 2 * n; c += nt) a[(size_t)k * w2 + c] = cmul(a[(size_t)k * w2 + c], inv);
+        for (int i = tid; i < n; i += nt) f[i] = a[(size_t)i * w2 + k];
+        __syncthreads();
+        for (int i = tid; i < n * 2 * n; i += nt) {
+            const int r = i / (2 * n), c = i - r * 2 * n;
+            if (r != k) a[(size_t)r * w2 + c] = csub(a[(size_t)r * w2 + c], cmul(f[r], a[(size_t)k * w2 + c]));
+        }
+        __syncthreads();
+    }
+    const bool sing = s_bad != 0;
+    if (sing && tid == 0) atomicExch(bad, 1);
+    for (int i = tid; i < n * n; i += nt) {
+        const int r = i / n, c = i - r * n;
+        double2 e = a[(size_t)r * w2 + n + c];
+        const bool zr = qg[3 * r] == 0.0 && qg[3 * r + 1] == 0.0 && qg[3 * r + 2] == 0.0;
+        const bool zc = qg[3 * c] == 0.0 && qg[3 * c + 1] == 0.0 && qg[3 * c + 2] == 0.0;
+        if (r != c && (zr || zc)) e = cz();
+        if (sing) e = make_double2(NAN, NAN);
+        const size_t o = ((size_t)r * n + c) * nw + j;
+        if (einv) einv[o] = e;
+        wbar[o] = cscal(make_double2(e.x - (r == c ? 1.0 : 0.0), e.y), v[r]);
+    }
+}
+
+int screening_smem_bytes(int n) { return (int)(sizeof(double2) * ((size_t)n * (2 * n + 1) + n + 1) + 8 * (n + 1)); }
+
 // x[list[i]] += d[i] for the listed pairs (refinement update).
 __global__ void pair_axpy_kernel(int nlist, const int* __restrict__ list, int npw, const double2* __restrict__ d,
                                  double2* __restrict__ x) {
@@ -1122,6 +1221,15 @@ cudaError_t launch_density(int n_v, int n_p, int nw, int npw, const double2* R, 
     if (n_v == 0 || n_p == 0 || nw == 0) return cudaSuccess;
     const dim3 grid((n_p + kDnP - 1) / kDnP, n_p, (nw + kDnJ - 1) / kDnJ);
     density_kernel<<<grid, kDnP * kDnJ, 0, st>>>(n_v, n_p, nw, npw, R, X, weight, dn);
+    return cudaGetLastError();
+}
+cudaError_t launch_screening(int n, int nw, const double2* dn, const double* qg, double inv_vol, double r_cut,
+                             double2* einv, double2* wbar, int* bad, cudaStream_t st) {
+    if (n == 0 || nw == 0) return cudaSuccess;
+    const int smem = screening_smem_bytes(n);
+    cudaError_t e = allow_max_smem((const void*)screening_kernel);
+    if (e != cudaSuccess) return e;
+    screening_kernel<<<nw, kThreads, smem, st>>>(n, nw, dn, qg, inv_vol, r_cut, einv, wbar, bad);
     return cudaGetLastError();
 }
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st) {

@@ -124,6 +124,11 @@ cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list
 // (Eq. 5 in reciprocal space); R [n_v n_p][npw], X [n_v n_p][2 nw][npw], dn [n_p][n_p][nw].
 cudaError_t launch_density(int n_v, int n_p, int nw, int npw, const double2* R, const double2* X, double weight,
                            double2* dn, cudaStream_t st);
+// epsilon^-1 and W-bar per frequency (Eq. 4, 9) from dn [n][n][nw] and q + G [n][3] (device);
+// einv may be null; *bad (device int) is set when a frequency's epsilon is singular.
+int screening_smem_bytes(int n);
+cudaError_t launch_screening(int n, int nw, const double2* dn, const double* qg, double inv_vol, double r_cut,
+                             double2* einv, double2* wbar, int* bad, cudaStream_t st);
 // rhs[c][g] = 1 if g == cols[c] else 0 ([ncol][npw]); the right-hand sides of Eq. 2.
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st);
 cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st);

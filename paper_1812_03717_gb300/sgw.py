@@ -24,7 +24,7 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
                 "SGW_EUNSUPPORTED"]
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
-           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_residual", "sgw_residual_noalloc",
+           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_screened_coulomb", "sgw_residual", "sgw_residual_noalloc",
            "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
            "sgw_mlp_forward", "sgw_mlp_grad", "sgw_mlp_train_step", "sgw_mlp_destroy", "sgw_destroy_system",
            "sgw_last_error"]
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_solve_green.argtypes = [vp, ip, vp, ip, vp, dp, ctypes.POINTER(_Opts), vp, ctypes.POINTER(_Report)]
     lib.sgw_density_response.argtypes = [vp, ip, ip, vp, vp, ip, vp, dp, dp, dp, ctypes.POINTER(_Opts), vp,
                                          ctypes.POINTER(_Report)]
+    lib.sgw_screened_coulomb.argtypes = [ip, ip, vp, vp, dp, dp, vp, vp, vp]
     lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_residual_noalloc.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_solve_pershift.argtypes = [vp, ip, vp, vp, vp, dp, dp, ip, vp, vp, ctypes.POINTER(_Opts), vp,
@@ -151,6 +152,22 @@ def _stream_of(x, stream):
         import torch
         return torch.cuda.current_stream(x.device).cuda_stream
     return None
+
+
+def screened_coulomb(dn, qg, volume, r_cut, want_eps_inv=True, stream=None):
+    """sgw_screened_coulomb: (eps_inv or None, wbar), each [n_g][n_g][nomega] like dn (a CUDA
+    tensor stays on the device).  qg: [n_g][3] Cartesian q + G (bohr^-1)."""
+    dn = _c128(dn)
+    qg = np.ascontiguousarray(qg, dtype=np.float64).reshape(-1, 3)
+    n, nw = qg.shape[0], (dn.shape[2] if dn.ndim == 3 else 0)
+    if tuple(dn.shape[:2]) != (n, n):
+        raise ValueError("dn must be [n_g][n_g][nomega] with n_g = len(qg)")
+    wbar = _like(dn, tuple(dn.shape))
+    einv = _like(dn, tuple(dn.shape)) if want_eps_inv else None
+    _check(load().sgw_screened_coulomb(n, nw, _ptr(dn), qg.ctypes.data, float(volume), float(r_cut),
+                                       _ptr(einv) if einv is not None else None, _ptr(wbar),
+                                       _stream_of(dn, stream)))
+    return einv, wbar
 
 
 class System:
