@@ -168,13 +168,51 @@ bool factor_235(int n, AxisPlan& ax) {
             ax.rad[ax.nst++] = r;
         }
     }
-    return m == 1;
+    if (m != 1) return false;
+    // prime-factor parts 2^a, 3^b, 5^c when every one has a register DFT (2, 3, 4, 5, 8, 9)
+    ax.npart = 0;
+    int rest = n;
+    bool ok = true;
+    for (int p : {2, 3, 5}) {
+        int q = 1;
+        while (rest % p == 0) {
+            rest /= p;
+            q *= p;
+        }
+        if (q > 1) {
+            ok = ok && (q == 2 || q == 3 || q == 4 || q == 5 || q == 8 || q == 9);
+            if (ax.npart < 3) ax.part[ax.npart] = q;
+            ++ax.npart;
+        }
+    }
+    if (!ok || ax.npart > 3) ax.npart = 0;
+    return true;
 }
 
-// Real-space index held at each position after the in-place decimation-in-frequency FFT of
-// the axis: frequency k = r_0 + R_0 (r_1 + R_1 (...)) lands at sum_s r_s m_s.
-std::vector<int> dif_order(const AxisPlan& ax) {
+int mod_inverse(int a, int m) {
+    for (int x = 1; x < m; ++x)
+        if ((long long)a * x % m == 1) return x;
+    return m == 1 ? 0 : -1;
+}
+
+// Real-space index held at each position after the inverse in-place FFT of the axis.
+// Radix stages (decimation in frequency): frequency k = r_0 + R_0 (r_1 + R_1 (...)) lands
+// at sum_s r_s m_s.  Prime-factor parts P_t: position p holds i_t = (p mod P_t) u_t mod P_t
+// per part, u_t = (N / P_t)^-1 mod P_t, i.e. frequency sum_t (N / P_t) u_t i_t mod N.
+std::vector<int> real_order(const AxisPlan& ax) {
     std::vector<int> k_at(ax.n);
+    if (ax.npart > 0) {
+        for (int p = 0; p < ax.n; ++p) {
+            long long f = 0;
+            for (int t = 0; t < ax.npart; ++t) {
+                const int P = ax.part[t], c = ax.n / P, u = mod_inverse(c % P, P);
+                const int i = (p % P) * u % P;
+                f += (long long)c * u * i;
+            }
+            k_at[p] = (int)(f % ax.n);
+        }
+        return k_at;
+    }
     for (int k = 0; k < ax.n; ++k) {
         int rest = k, pos = 0;
         for (int s = 0; s < ax.nst; ++s) {
@@ -434,10 +472,10 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     s->nstick = (int)stick_xy.size();
     s->nxcol = (int)xbase.size();
     // potential, one contiguous (padded) plane per z: [z][x][y < n2p], every axis in the
-    // digit-reversed order in which the inverse FFTs leave real space
+    // order in which the inverse FFTs leave real space
     const size_t nboxp = (size_t)n1 * n2p * n3;
     std::vector<double> vz(nboxp, 0.0);
-    const std::vector<int> ox = dif_order(s->plan.ax[0]), oy = dif_order(s->plan.ax[1]), oz = dif_order(s->plan.ax[2]);
+    const std::vector<int> ox = real_order(s->plan.ax[0]), oy = real_order(s->plan.ax[1]), oz = real_order(s->plan.ax[2]);
     for (int px = 0; px < n1; ++px)
         for (int py = 0; py < n2; ++py)
             for (int pz = 0; pz < n3; ++pz)

@@ -3,8 +3,8 @@
 // Data layout in device memory (all complex values are FP64 pairs, double2):
 //   plane-wave vectors      [nvec][npw]              canonical G order (Miller lexicographic)
 //   local potential         [N3][N1][N2p]            one contiguous (padded) xy-plane per z, each
-//                                                    axis in the digit-reversed order that the
-//                                                    in-place FFT leaves real space in
+//                                                    axis in the order that the in-place FFT
+//                                                    leaves real space in
 //   stick buffer (on chip)  [nstick][N3p]            z-columns of the box that hold a G (N3p odd)
 //   plane buffer (on chip)  [nplanes][N1][N2p]       a few xy-planes of the box, rows padded to odd N2p
 //   KB projectors           [nproj][npw]             <k+G|beta_p>
@@ -36,6 +36,8 @@ struct AxisPlan {
     int nst;
     int rad[kMaxStages];    // radices R_0, R_1, ... (R_0 acts on the full length)
     int span[kMaxStages];   // m_s = n / (R_0 ... R_s)
+    int npart;              // > 0: prime-factor algorithm over these coprime parts (2^a, 3^b, 5^c
+    int part[3];            //      in {2, 3, 4, 5, 8, 9}); 0: the radix stages above
 };
 
 // Everything an H application needs; passed by value to kernels.
@@ -498,6 +500,86 @@ __device__ __forceinline__ void fft_stage(typename Ar::C* data, int total, int n
     }
 }
 
+// P-point DFT of v[0..P) in registers, sign SIGN, for P in {2, 3, 4, 5, 8, 9}.  A composite
+// P = Q R is split as X[k1 + Q k2] = sum_n2 w_R^(n2 k2) w_P^(n2 k1) sum_n1 v[R n1 + n2] w_Q^(n1 k1)
+// (Cooley-Tukey inside the thread); w_P^m = tw[tstep m] with tw[i] = exp(-2 pi i i / N),
+// tstep = N / P (conjugated for SIGN > 0).
+template <class Ar, int SIGN, int P>
+__device__ __forceinline__ void dft_reg(typename Ar::C* v, const typename Ar::C* tw, int tstep) {
+    using C = typename Ar::C;
+    if constexpr (P <= 5) {
+        C t[5];
+#pragma unroll
+        for (int k = 0; k < P; ++k) t[k] = v[k];
+        dft_small<Ar, SIGN>(t, P);
+#pragma unroll
+        for (int k = 0; k < P; ++k) v[k] = t[k];
+    } else {
+        constexpr int Q = P == 8 ? 4 : 3;
+        constexpr int R = P / Q;
+        C y[P];
+#pragma unroll
+        for (int n2 = 0; n2 < R; ++n2) {
+            C t[Q];
+#pragma unroll
+            for (int n1 = 0; n1 < Q; ++n1) t[n1] = v[R * n1 + n2];
+            dft_reg<Ar, SIGN, Q>(t, tw, tstep);
+#pragma unroll
+            for (int k1 = 0; k1 < Q; ++k1) {
+                if (n2 != 0 && k1 != 0) {
+                    C w = tw[tstep * n2 * k1];
+                    if (SIGN > 0) w = Ar::conj(w);
+                    t[k1] = Ar::mul(t[k1], w);
+                }
+                y[n2 * Q + k1] = t[k1];
+            }
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < Q; ++k1) {
+            C t[R];
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) t[n2] = y[n2 * Q + k1];
+            dft_reg<Ar, SIGN, R>(t, tw, tstep);
+#pragma unroll
+            for (int k2 = 0; k2 < R; ++k2) v[k1 + Q * k2] = t[k2];
+        }
+    }
+}
+
+// One stage of the prime-factor algorithm (Good-Thomas) for the coprime part P of N: for
+// m < N / P, the P elements at (P m + (N / P) k) mod N, k < P, are replaced by their P-point
+// DFT.  The stages of all parts commute and need no twiddles between them; starting from
+// natural order they leave X_f at the position p with p mod P_t = (N / P_t) k_t mod P_t, f the
+// CRT combination of the k_t (and take that order back to natural order with the opposite
+// sign).  Line l = p * lpp + q as in fft_inplace; consecutive threads take neighbouring lines.
+template <class Ar, int SIGN, int P>
+__device__ __forceinline__ void fft_pfa_stage(typename Ar::C* data, int nlines, int lpp, int pstride,
+                                              const int* __restrict__ line_base, int ls, int es, int N,
+                                              const typename Ar::C* tw) {
+    using C = typename Ar::C;
+    const int st = N / P, total = nlines * st, nt = blockDim.x;
+    const float inv_nlines = 1.0f / (float)nlines, inv_lpp = 1.0f / (float)lpp;
+    for (int b = threadIdx.x; b < total; b += nt) {
+        int l, q;
+        const int m = divmod_f(b, nlines, inv_nlines, l);
+        const int pl = divmod_f(l, lpp, inv_lpp, q);
+        const int base = pl * pstride + (line_base ? line_base[q] : q * ls);
+        int pos[P];
+        C v[P];
+        int p0 = P * m;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            pos[k] = base + p0 * es;
+            v[k] = data[pos[k]];
+            p0 += st;
+            if (p0 >= N) p0 -= N;
+        }
+        dft_reg<Ar, SIGN, P>(v, tw, st);
+#pragma unroll
+        for (int k = 0; k < P; ++k) data[pos[k]] = v[k];
+    }
+}
+
 // In-place batched mixed-radix FFT (sign SIGN: exp(SIGN 2 pi i n k / N), unnormalised) of
 // `nlines` lines of length N = ax.n in shared memory, `lpp` lines per plane, planes
 // `pstride` elements apart; line l = p * lpp + q starts at
@@ -508,11 +590,29 @@ __device__ __forceinline__ void fft_stage(typename Ar::C* data, int total, int n
 // radix R on blocks of L = m R elements reads x[blk L + j + k m] (k < R), applies the
 // R-point DFT and the twiddles w_L^(j k), and writes back to the same places, so the
 // butterflies of a stage are disjoint and need no barrier between them: one barrier per
-// stage.  tw[i] = exp(-2 pi i i / N).  All threads of the CTA must call.
+// stage.  When the axis has prime-factor parts (ax.npart > 0) the stages are those of the
+// prime-factor algorithm instead (fft_pfa_stage: no twiddles between stages, another
+// permutation of real space; DIF = true runs the parts in order, DIT in reverse).
+// tw[i] = exp(-2 pi i i / N).  All threads of the CTA must call.
 template <class Ar, int SIGN, bool DIF>
 __device__ void fft_inplace(typename Ar::C* data, int nlines, int lpp, int pstride, const int* __restrict__ line_base,
                             int ls, int es, const AxisPlan& ax, const typename Ar::C* tw) {
     const int N = ax.n;
+    if (ax.npart > 0) {   // prime-factor algorithm: parts in order for DIF, reversed for DIT
+        for (int ti = 0; ti < ax.npart; ++ti) {
+            const int P = ax.part[DIF ? ti : ax.npart - 1 - ti];
+            switch (P) {
+                case 2: fft_pfa_stage<Ar, SIGN, 2>(data, nlines, lpp, pstride, line_base, ls, es, N, tw); break;
+                case 3: fft_pfa_stage<Ar, SIGN, 3>(data, nlines, lpp, pstride, line_base, ls, es, N, tw); break;
+                case 4: fft_pfa_stage<Ar, SIGN, 4>(data, nlines, lpp, pstride, line_base, ls, es, N, tw); break;
+                case 5: fft_pfa_stage<Ar, SIGN, 5>(data, nlines, lpp, pstride, line_base, ls, es, N, tw); break;
+                case 8: fft_pfa_stage<Ar, SIGN, 8>(data, nlines, lpp, pstride, line_base, ls, es, N, tw); break;
+                default: fft_pfa_stage<Ar, SIGN, 9>(data, nlines, lpp, pstride, line_base, ls, es, N, tw); break;
+            }
+            __syncthreads();
+        }
+        return;
+    }
     for (int si = 0; si < ax.nst; ++si) {
         const int s = DIF ? si : ax.nst - 1 - si;
         const int R = ax.rad[s], m = ax.span[s];
@@ -548,9 +648,9 @@ __device__ __forceinline__ void load_twiddles(const Plan& P, unsigned char* smem
 // x into the sticks; inverse FFT along z on the sticks; per group of z-planes: scatter the
 // planes, inverse FFT along y (only the x-columns that hold sticks) and x, multiply by V(r),
 // forward FFT along x and y, gather back into the sticks; forward FFT along z; gather the
-// (the inverse FFTs are decimation in frequency, leaving real space digit-reversed along
-// each axis, where V is stored in the same order; the forward FFTs are decimation in time
-// and return to natural order, so the permutation costs nothing);
+// (the inverse FFTs leave real space permuted along each axis -- digit-reversed or in the
+// prime-factor order -- where V is stored in the same order; the forward FFTs return to
+// natural order, so the permutation costs nothing);
 // sphere, scale by 1/N^3 and add T_G x_G + sum_p D_p c_p beta_p(G); optionally project with
 // P_c and subtract z x.  All vector arithmetic in the policy's arithmetic; the block
 // reductions of the projections in FP64.
