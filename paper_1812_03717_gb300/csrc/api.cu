@@ -891,7 +891,9 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
             L.out_status = st_d;
             L.eta_s = eta_s_d;
             L.eta_r = eta_r_d;
-            return launch_lanczos(plan, L, g, corr ? SGW_PREC_FP64 : precision, threads, st);
+            // correction solves only need a fraction of a digit (their target is about
+            // 0.3 tol / |r|); they run in the pass's precision and the FP64 check re-judges
+            return launch_lanczos(plan, L, g, precision, threads, st);
         }
         SolveArgs A;
         A.nrhs = nr;
