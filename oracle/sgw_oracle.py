@@ -30,7 +30,9 @@ What it computes, by plain definition (no blocking, fusion or reordering):
   (Sternheimer solutions at +-(omega + i eta), real-space product with the unperturbed
   periodic part, Fourier transform back) and by the sum over the eigenstates of H_{k+q};
 * the spherically truncated Coulomb potential of Sec. 2.6, the dielectric matrix of Eq. 4
-  and its inverse, and the correlation part W-bar of the screened interaction (Eq. 9).
+  and its inverse, and the correlation part W-bar of the screened interaction (Eq. 9);
+* the density response at imaginary frequencies and the AAA rational approximation used to
+  continue such data to the real axis (Sec. 2.7).
 
 Each function cites the passage of the paper it restates.
 """
@@ -348,15 +350,21 @@ def density_response(h_kq, psi_v_kq, psi_k, miller_k, miller_kq, eps_k, gp_mille
     the product is formed in real space and Fourier transformed back (box DFT, N^-3); G and
     G' both run over the perturbation list gp_miller (weight = 2 / N_k for spin and the
     k-point average)."""
+    w = np.asarray(omega, np.float64) + 1j * eta
+    return density_response_w(h_kq, psi_v_kq, psi_k, miller_k, miller_kq, eps_k, gp_miller, w, dims, weight)
+
+
+def density_response_w(h_kq, psi_v_kq, psi_k, miller_k, miller_kq, eps_k, gp_miller, w, dims, weight):
+    """density_response at arbitrary complex frequencies w_j (z = eps_v +- w_j); w_j = i omega_j
+    gives the response on the imaginary axis (Sec. 2.7)."""
     psi_k = np.atleast_2d(np.asarray(psi_k, np.complex128))
-    n_v, n_p, n_w = len(psi_k), len(gp_miller), len(omega)
+    w = np.asarray(w, np.complex128)
+    n_v, n_p, n_w = len(psi_k), len(gp_miller), len(w)
     rhs = make_rhs(miller_kq, miller_k, psi_k, gp_miller)          # row v * n_p + p
-    omega = np.asarray(omega, np.float64)
     out = np.zeros((n_p, n_p, n_w), dtype=np.complex128)
     for v in range(n_v):
         u = periodic_on_box(psi_k[v], miller_k, dims)
-        zc = omega + 1j * eta
-        z = np.concatenate([eps_k[v] + zc, eps_k[v] - zc])[None, :].repeat(n_p, axis=0)
+        z = np.concatenate([eps_k[v] + w, eps_k[v] - w])[None, :].repeat(n_p, axis=0)
         x = solve_shifted_z(h_kq, psi_v_kq, rhs[v * n_p:(v + 1) * n_p], z)   # [n_p][2 n_w][npw]
         for p_in in range(n_p):
             for j in range(n_w):
@@ -366,22 +374,23 @@ def density_response(h_kq, psi_v_kq, psi_k, miller_k, miller_kq, eps_k, gp_mille
     return out
 
 
-def density_response_sos(h_kq, n_occ_kq, psi_k, miller_k, miller_kq, eps_k, gp_miller, omega, eta, weight):
+def density_response_sos(h_kq, n_occ_kq, psi_k, miller_k, miller_kq, eps_k, gp_miller, omega, eta, weight, w=None):
     """The same contribution from the eigenstates of H_{k+q} (an Adler-Wiser-type sum over the
     unoccupied states c, the n_occ_kq lowest being occupied):
         dn[G][G'][j] = weight sum_v sum_c conj(M_vc(G)) M_vc(G') [1/(eps_v + w_j - e_c)
                                                                  + 1/(eps_v - w_j - e_c)],
-    w_j = omega_j + i eta, M_vc(G') = <psi_c | exp(i(q+G').r) psi_{v,k}>."""
-    w, vec = np.linalg.eigh(h_kq)
-    vc, ec = vec[:, n_occ_kq:], w[n_occ_kq:]
+    w_j = omega_j + i eta (or the complex frequencies w when given),
+    M_vc(G') = <psi_c | exp(i(q+G').r) psi_{v,k}>."""
+    wv, vec = np.linalg.eigh(h_kq)
+    vc, ec = vec[:, n_occ_kq:], wv[n_occ_kq:]
     psi_k = np.atleast_2d(np.asarray(psi_k, np.complex128))
     n_v, n_p = len(psi_k), len(gp_miller)
+    freqs = (np.asarray(omega, np.float64) + 1j * eta) if w is None else np.asarray(w, np.complex128)
     rhs = make_rhs(miller_kq, miller_k, psi_k, gp_miller)
-    out = np.zeros((n_p, n_p, len(omega)), dtype=np.complex128)
+    out = np.zeros((n_p, n_p, len(freqs)), dtype=np.complex128)
     for v in range(n_v):
         m = rhs[v * n_p:(v + 1) * n_p] @ vc.conj()          # [p][c] = <psi_c|rhs_vp>
-        for j, om in enumerate(omega):
-            wc = om + 1j * eta
+        for j, wc in enumerate(freqs):
             f = 1.0 / (eps_k[v] + wc - ec) + 1.0 / (eps_k[v] - wc - ec)
             out[:, :, j] += weight * (m.conj() * f) @ m.T
     return out
@@ -433,3 +442,58 @@ def screened_coulomb(dn, qg, volume, r_cut):
         einv[:, :, j] = inv
         wbar[:, :, j] = v[:, None] * (inv - eye)
     return einv, wbar
+
+
+
+# ------------------------------------------ Sec. 2.7: analytic continuation by AAA
+
+def aaa(z, f, tol=1e-13, mmax=32):
+    """The adaptive Antoulas-Anderson rational approximation (Nakatsukasa, Sete and Trefethen,
+    SIAM J. Sci. Comput. 40, A1494, 2018) of samples f at points z, as Sec. 2.7 uses it: greedy
+    choice of support points (the sample where the current approximant errs most, the first
+    on ties; the first approximant is the mean of f), barycentric weights from the right
+    singular vector of the Loewner matrix for its smallest singular value, stop when the
+    largest deviation on the remaining samples is <= tol * max|f| or at mmax support points.
+    Returns (support points, support values, weights)."""
+    z = np.asarray(z, np.complex128)
+    f = np.asarray(f, np.complex128)
+    m = len(z)
+    fmax = np.abs(f).max()
+    rest = np.ones(m, bool)
+    sup = []
+    r = np.full(m, f.mean())
+    w = np.zeros(0, np.complex128)
+    for _ in range(min(mmax, m)):
+        err = np.where(rest, np.abs(f - r), -1.0)
+        j = int(np.argmax(err))
+        sup.append(j)
+        rest[j] = False
+        zs, fs = z[sup], f[sup]
+        idx = np.nonzero(rest)[0]
+        cauchy = 1.0 / (z[idx][:, None] - zs[None, :])
+        loewner = (f[idx][:, None] - fs[None, :]) * cauchy
+        if len(idx) == 0:
+            w = np.ones(len(sup), np.complex128) / math.sqrt(len(sup))
+            break
+        _, _, vh = np.linalg.svd(loewner, full_matrices=True)
+        w = vh[-1].conj()
+        r = f.copy()
+        r[idx] = (cauchy @ (w * fs)) / (cauchy @ w)
+        if np.abs(f[idx] - r[idx]).max() <= tol * fmax:
+            break
+    return z[sup], f[sup], w
+
+
+def aaa_eval(zs, fs, w, x):
+    """r(x) = sum_j w_j f_j / (x - z_j) / sum_j w_j / (x - z_j), and f_j at x = z_j."""
+    x = np.asarray(x, np.complex128)
+    out = np.empty(x.shape, np.complex128)
+    for i, xi in enumerate(x.ravel()):
+        d = xi - zs
+        hit = np.nonzero(d == 0)[0]
+        if len(hit):
+            out.ravel()[i] = fs[hit[0]]
+        else:
+            c = w / d
+            out.ravel()[i] = np.sum(c * fs) / np.sum(c)
+    return out
