@@ -226,6 +226,31 @@ sgw_status sgw_density_response(sgw_system* sys, int n_v, int n_pert, const void
                                 int nomega, const double* omega, double eta, double weight, double tol,
                                 const sgw_solve_opts* opts, void* dn, sgw_report* report);
 
+/* sgw_density_response at arbitrary complex frequencies w_j (Sec. 2.7: the imaginary-axis
+ * variant takes w_j = i omega_j): shifts z = eps_v + w_j and eps_v - w_j, everything else as
+ * sgw_density_response.  w: [nw][2] host, (Re w, Im w) in Ha with Im w != 0 (else
+ * SGW_EINVAL); 2 nw <= 512.  dn: [n_pert][n_pert][nw], accumulated. */
+sgw_status sgw_density_response_w(sgw_system* sys, int n_v, int n_pert, const void* rhs, const double* eps_v,
+                                  int nw, const double* w, double weight, double tol, const sgw_solve_opts* opts,
+                                  void* dn, sgw_report* report);
+
+/* AAA rational approximation (Sec. 2.7; Nakatsukasa, Sete and Trefethen 2018), batched over
+ * nfun functions that share the m sample points, and its evaluation: the analytic
+ * continuation of data on the imaginary axis to other complex frequencies.  Per function:
+ * the first approximant is the mean of the samples; each step adds the sample with the
+ * largest deviation (the first on ties) to the support set and takes the barycentric weights
+ * from the right singular vector of the Loewner matrix for its smallest singular value
+ * (one-sided Jacobi SVD in FP64); it stops when the largest deviation on the other samples
+ * is <= tol max|f|, at mmax support points, or when no sample is left.
+ *   z       complex [m] host, distinct finite sample points; m <= 128.
+ *   f       complex [nfun][m] (host or device) samples.   mmax <= 32.
+ *   z_eval  complex [n_eval] host; r_eval complex [nfun][n_eval] (host or device), the
+ *           approximant there (the sample value where a point is a support point).
+ *   degree  [nfun] (host or device) or NULL: support points used.
+ * A function with a non-finite sample gets NaN outputs and the call returns SGW_EINVAL. */
+sgw_status sgw_aaa(int nfun, int m, const void* z, const void* f, double tol, int mmax, int n_eval,
+                   const void* z_eval, void* r_eval, int* degree, void* stream);
+
 /* Screening from an accumulated density response (Sec. 2.4, Eq. 4 and 9, with the Coulomb
  * potential of Sec. 2.6).  Per frequency j:
  *   v(q)          = 4 pi / |q|^2 [1 - cos(|q| r_cut)]   (spherical truncation; its limit

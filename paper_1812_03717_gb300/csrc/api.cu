@@ -1094,17 +1094,14 @@ sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, con
     return rs;
 }
 
-sgw_status sgw_density_response(sgw_system* s, int n_v, int n_pert, const void* rhs, const double* eps_v, int nomega,
-                                const double* omega, double eta, double weight, double tol,
-                                const sgw_solve_opts* opts, void* dn, sgw_report* report) {
-    g_err.clear();
-    if (!s || !eps_v || !omega || !dn || (n_v > 0 && n_pert > 0 && !rhs)) return fail(SGW_EINVAL, "NULL argument");
-    if (n_v < 0 || n_pert < 0 || nomega < 1) return fail(SGW_EINVAL, "need n_v, n_pert >= 0 and nomega >= 1");
-    if (2 * nomega > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nomega above 256 (2 nomega shifts per right-hand side)");
-    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(SGW_EINVAL, "eta must be positive");
+// One k-point's contribution to Eq. 5 at complex frequencies w_j = wre[j] + i wim[j]
+// (Im w_j != 0): shifts z = eps_v + w_j and eps_v - w_j in one Krylov space per right-hand side.
+static sgw_status density_common(sgw_system* s, int n_v, int n_pert, const void* rhs, const double* eps_v,
+                                 int nomega, const double* wre, const double* wim, double weight, double tol,
+                                 const sgw_solve_opts* opts, void* dn, sgw_report* report) {
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
     if (!std::isfinite(weight)) return fail(SGW_EINVAL, "non-finite weight");
-    if (!finite_all(eps_v, n_v) || !finite_all(omega, nomega)) return fail(SGW_EINVAL, "non-finite eps_v or omega");
+    if (!finite_all(eps_v, n_v)) return fail(SGW_EINVAL, "non-finite eps_v");
     if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
     const int nrhs = n_v * n_pert;
     if (nrhs == 0) return SGW_OK;
@@ -1119,17 +1116,17 @@ sgw_status sgw_density_response(sgw_system* s, int n_v, int n_pert, const void* 
     SGW_CUDA(cudaMallocAsync(&xb.dev, vb * (size_t)nrhs * 2 * nomega, st), "solution allocation");
     xb.owned = true;
     xb.st = st;
-    // shifts z = eps_v + omega_j + i eta (j < nomega) and eps_v - omega_j - i eta (the -omega branch)
+    // shifts z = eps_v + w_j (j < nomega) and eps_v - w_j (the -w branch)
     std::vector<double> e_rows(nrhs), om2(2 * nomega), eta2(2 * nomega);
     for (int i = 0; i < nrhs; ++i) e_rows[i] = eps_v[i / n_pert];
     for (int j = 0; j < nomega; ++j) {
-        om2[j] = omega[j];
-        eta2[j] = eta;
-        om2[nomega + j] = -omega[j];
-        eta2[nomega + j] = -eta;
+        om2[j] = wre[j];
+        eta2[j] = wim[j];
+        om2[nomega + j] = -wre[j];
+        eta2[nomega + j] = -wim[j];
     }
     const sgw_status rs = multishift(s, s->plan, nrhs, (const double2*)in.dev, e_rows.data(), 2 * nomega, om2.data(),
-                                     eta2.data(), eta, tol, opts, (double2*)xb.dev, report, st);
+                                     eta2.data(), 1.0, tol, opts, (double2*)xb.dev, report, st);
     if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
     SGW_CUDA(launch_density(n_v, n_pert, nomega, s->npw, (const double2*)in.dev, (const double2*)xb.dev, weight,
                             (double2*)dnb.dev, st),
@@ -1138,6 +1135,79 @@ sgw_status sgw_density_response(sgw_system* s, int n_v, int n_pert, const void* 
     if (dnb.owned) SGW_CUDA(cudaMemcpyAsync(dn, dnb.dev, dn_bytes, cudaMemcpyDeviceToHost, st), "dn copy");
     SGW_CUDA(cudaStreamSynchronize(st), "density response");
     return rs;
+}
+
+sgw_status sgw_density_response(sgw_system* s, int n_v, int n_pert, const void* rhs, const double* eps_v, int nomega,
+                                const double* omega, double eta, double weight, double tol,
+                                const sgw_solve_opts* opts, void* dn, sgw_report* report) {
+    g_err.clear();
+    if (!s || !eps_v || !omega || !dn || (n_v > 0 && n_pert > 0 && !rhs)) return fail(SGW_EINVAL, "NULL argument");
+    if (n_v < 0 || n_pert < 0 || nomega < 1) return fail(SGW_EINVAL, "need n_v, n_pert >= 0 and nomega >= 1");
+    if (2 * nomega > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nomega above 256 (2 nomega shifts per right-hand side)");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(SGW_EINVAL, "eta must be positive");
+    if (!finite_all(omega, nomega)) return fail(SGW_EINVAL, "non-finite omega");
+    std::vector<double> wim(nomega, eta);
+    return density_common(s, n_v, n_pert, rhs, eps_v, nomega, omega, wim.data(), weight, tol, opts, dn, report);
+}
+
+sgw_status sgw_density_response_w(sgw_system* s, int n_v, int n_pert, const void* rhs, const double* eps_v, int nw,
+                                  const double* w, double weight, double tol, const sgw_solve_opts* opts, void* dn,
+                                  sgw_report* report) {
+    g_err.clear();
+    if (!s || !eps_v || !w || !dn || (n_v > 0 && n_pert > 0 && !rhs)) return fail(SGW_EINVAL, "NULL argument");
+    if (n_v < 0 || n_pert < 0 || nw < 1) return fail(SGW_EINVAL, "need n_v, n_pert >= 0 and nw >= 1");
+    if (2 * nw > kMaxShifts) return fail(SGW_EUNSUPPORTED, "nw above 256 (2 nw shifts per right-hand side)");
+    std::vector<double> wre(nw), wim(nw);
+    for (int j = 0; j < nw; ++j) {
+        wre[j] = w[2 * j];
+        wim[j] = w[2 * j + 1];
+        if (!std::isfinite(wre[j]) || !std::isfinite(wim[j])) return fail(SGW_EINVAL, "non-finite w");
+        if (wim[j] == 0.0) return fail(SGW_EINVAL, "Im w must be nonzero (the shifted systems are singular on the real axis)");
+    }
+    return density_common(s, n_v, n_pert, rhs, eps_v, nw, wre.data(), wim.data(), weight, tol, opts, dn, report);
+}
+
+sgw_status sgw_aaa(int nfun, int m, const void* z, const void* f, double tol, int mmax, int n_eval, const void* z_eval,
+                   void* r_eval, int* degree, void* stream) {
+    g_err.clear();
+    if (nfun < 0 || m < 0 || n_eval < 0 || mmax < 1) return fail(SGW_EINVAL, "negative size or mmax < 1");
+    if (nfun == 0) return SGW_OK;
+    if (m < 1) return fail(SGW_EINVAL, "need at least one sample");
+    if (!z || !f || (n_eval > 0 && (!z_eval || !r_eval))) return fail(SGW_EINVAL, "NULL argument");
+    if (m > 128 || mmax > 32) return fail(SGW_EUNSUPPORTED, "m above 128 or mmax above 32");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be >= 0");
+    if (is_device_ptr(z) || (n_eval > 0 && is_device_ptr(z_eval)))
+        return fail(SGW_EINVAL, "z and z_eval must be host arrays");
+    const double* zd = (const double*)z;
+    if (!finite_all(zd, 2 * (size_t)m) || (n_eval > 0 && !finite_all((const double*)z_eval, 2 * (size_t)n_eval)))
+        return fail(SGW_EINVAL, "non-finite sample or evaluation point");
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < i; ++j)
+            if (zd[2 * i] == zd[2 * j] && zd[2 * i + 1] == zd[2 * j + 1]) return fail(SGW_EINVAL, "repeated sample point");
+    cudaStream_t st = (cudaStream_t)stream;
+    Staged zb, fb, eb, rb, db, flag;
+    sgw_status r;
+    if ((r = stage_in(z, sizeof(double2) * m, zb, st, "z")) != SGW_OK) return r;
+    if ((r = stage_in(f, sizeof(double2) * (size_t)nfun * m, fb, st, "f")) != SGW_OK) return r;
+    if (n_eval > 0) {
+        if ((r = stage_in(z_eval, sizeof(double2) * n_eval, eb, st, "z_eval")) != SGW_OK) return r;
+        if ((r = stage_out(r_eval, sizeof(double2) * (size_t)nfun * n_eval, rb, "r_eval", st)) != SGW_OK) return r;
+    }
+    if (degree && (r = stage_out(degree, sizeof(int) * nfun, db, "degree", st)) != SGW_OK) return r;
+    SGW_CUDA(cudaMallocAsync(&flag.dev, sizeof(int), st), "flag allocation");
+    flag.owned = true;
+    flag.st = st;
+    SGW_CUDA(cudaMemsetAsync(flag.dev, 0, sizeof(int), st), "memset");
+    SGW_CUDA(launch_aaa(nfun, m, (const double2*)zb.dev, (const double2*)fb.dev, tol, mmax, n_eval,
+                        (const double2*)eb.dev, (double2*)rb.dev, degree ? (int*)db.dev : nullptr, (int*)flag.dev, st),
+             "AAA kernel");
+    int bad = 0;
+    SGW_CUDA(cudaMemcpyAsync(&bad, flag.dev, sizeof(int), cudaMemcpyDeviceToHost, st), "flag copy");
+    if (n_eval > 0 && (r = finish_out(rb, st, "r_eval copy")) != SGW_OK) return r;
+    if (degree && (r = finish_out(db, st, "degree copy")) != SGW_OK) return r;
+    SGW_CUDA(cudaStreamSynchronize(st), "AAA");
+    if (bad) return fail(SGW_EINVAL, "non-finite samples (their functions' outputs are NaN)");
+    return SGW_OK;
 }
 
 sgw_status sgw_screened_coulomb(int n_g, int nomega, const void* dn, const double* qg, double volume, double r_cut,

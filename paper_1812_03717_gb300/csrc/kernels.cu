@@ -1003,6 +1003,246 @@ __global__ void __launch_bounds__(kThreads) screening_kernel(int n, int nw, cons
 
 int screening_smem_bytes(int n) { return (int)(sizeof(double2) * ((size_t)n * (2 * n + 1) + n + 1) + 8 * (n + 1)); }
 
+// ------------------------------------------------ AAA rational approximation (Sec. 2.7)
+//
+// One CTA per function (FP64 throughout).  Greedy AAA (Nakatsukasa, Sete, Trefethen 2018):
+// the first approximant is the mean of the samples; each step moves the sample where the
+// approximant errs most (the first on ties) into the support set, builds the Loewner matrix
+// A[i][j] = (F_i - f_j) / (Z_i - z_j) over the other samples (support rows left at zero,
+// which changes no right singular vector), and takes the barycentric weights from the right
+// singular vector of its smallest singular value.  The SVD is one-sided Jacobi (Hestenes):
+// column pairs in a round-robin order, one warp per pair, complex rotations that make each
+// pair orthogonal, accumulated in V, until a sweep rotates nothing (at most kAaaSweeps).
+// The loop ends when the largest deviation on the remaining samples is <= tol max|F|, at
+// mmax support points, or when no sample is left; the approximant is then evaluated at the
+// targets (the support value where a target coincides with a support point).
+constexpr int kAaaMaxM = 128, kAaaMaxK = 32, kAaaSweeps = 40, kAaaThreads = 256;
+
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+__global__ void __launch_bounds__(kAaaThreads) aaa_kernel(int m, const double2* __restrict__ z, const double2* __restrict__ f,
+                                                          double tol, int mmax, int ne,
+                                                          const double2* __restrict__ ze, double2* __restrict__ re,
+                                                          int* __restrict__ degree, int* __restrict__ bad) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double2 (*A)[kAaaMaxM] = reinterpret_cast<double2 (*)[kAaaMaxM]>(smem);   // A[col][row], Loewner matrix
+    double2 (*V)[kAaaMaxK] = reinterpret_cast<double2 (*)[kAaaMaxK]>(smem + sizeof(double2) * kAaaMaxK * kAaaMaxM);
+    __shared__ double2 Z[kAaaMaxM], F[kAaaMaxM], R[kAaaMaxM];
+    __shared__ double2 W[kAaaMaxK];
+    __shared__ int sup[kAaaMaxK], rest[kAaaMaxM];
+    __shared__ double s_red[kAaaThreads / 32];
+    __shared__ int s_idx[kAaaThreads / 32];
+    __shared__ int s_k, s_done, s_rot, s_bad;
+    __shared__ double2 s_mean;
+    __shared__ double s_fmax;
+    const int fn = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kAaaThreads / 32;
+    const double2* fv = f + (size_t)fn * m;
+    for (int i = tid; i < m; i += kAaaThreads) {
+        Z[i] = z[i];
+        F[i] = fv[i];
+        rest[i] = 1;
+    }
+    if (tid == 0) {
+        s_k = 0;
+        s_done = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double2 acc = cz();
+        double mx = 0.0;
+        for (int i = 0; i < m; ++i) {
+            acc = cadd(acc, F[i]);
+            const double a = sqrt(cabs2(F[i]));
+            if (!(a <= mx)) mx = a;   // NaN-propagating
+            if (!cfinite(F[i])) s_bad = 1;
+        }
+        s_mean = cscal(acc, 1.0 / m);
+        s_fmax = mx;
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) atomicExch(bad, 1);
+        for (int e = tid; e < ne; e += kAaaThreads) re[(size_t)fn * ne + e] = make_double2(NAN, NAN);
+        if (tid == 0 && degree) degree[fn] = 0;
+        return;
+    }
+    for (int i = tid; i < m; i += kAaaThreads) R[i] = s_mean;
+    __syncthreads();
+    const int kcap = min(min(mmax, m), kAaaMaxK);
+    while (!s_done) {
+        // the remaining sample with the largest deviation (first index on ties)
+        double best = -1.0;
+        int bi = m;
+        for (int i = tid; i < m; i += kAaaThreads) {
+            if (!rest[i]) continue;
+            const double e = sqrt(cabs2(csub(F[i], R[i])));
+            if (e > best) {
+                best = e;
+                bi = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            s_red[warp] = best;
+            s_idx[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double b = -1.0;
+            int ix = m;
+            for (int w = 0; w < nw; ++w)
+                if (s_red[w] > b || (s_red[w] == b && s_idx[w] < ix)) {
+                    b = s_red[w];
+                    ix = s_idx[w];
+                }
+            if (ix >= m)   // no finite deviation left: the first remaining sample
+                for (ix = 0; ix < m - 1 && !rest[ix]; ++ix) {
+                }
+            sup[s_k] = ix;
+            rest[ix] = 0;
+            s_k = s_k + 1;
+        }
+        __syncthreads();
+        const int k = s_k;
+        // Loewner matrix (support rows zero) and V = 1
+        for (int t = tid; t < k * m; t += kAaaThreads) {
+            const int c = t / m, i = t - c * m;
+            const int j = sup[c];
+            A[c][i] = rest[i] ? cdiv(csub(F[i], F[j]), csub(Z[i], Z[j])) : cz();
+        }
+        for (int t = tid; t < k * k; t += kAaaThreads) {
+            const int c = t / k, r = t - c * k;
+            V[c][r] = make_double2(c == r ? 1.0 : 0.0, 0.0);
+        }
+        __syncthreads();
+        // one-sided Jacobi: round-robin pairs over K = k rounded up to even (index >= k: dummy)
+        const int K = (k + 1) & ~1;
+        for (int sweep = 0; sweep < kAaaSweeps && k > 1; ++sweep) {
+            if (tid == 0) s_rot = 0;
+            __syncthreads();
+            for (int rnd = 0; rnd < K - 1; ++rnd) {
+                for (int pi = warp; pi < K / 2; pi += nw) {
+                    // positions 0..K-1: 0 fixed, the others rotated by rnd
+                    const int a0 = pi, b0 = K - 1 - pi;
+                    const int p = a0 == 0 ? 0 : 1 + (a0 - 1 + rnd) % (K - 1);
+                    const int q = 1 + (b0 - 1 + rnd) % (K - 1);
+                    if (p >= k || q >= k) continue;
+                    double al = 0.0, be = 0.0;
+                    double2 ga = cz();
+                    for (int i = lane; i < m; i += 32) {
+                        const double2 x = A[p][i], y = A[q][i];
+                        al += cabs2(x);
+                        be += cabs2(y);
+                        ga = cadd(ga, cmulc(x, y));
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        al += __shfl_xor_sync(0xffffffffu, al, o);
+                        be += __shfl_xor_sync(0xffffffffu, be, o);
+                        ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+                        ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+                    }
+                    const double g = sqrt(cabs2(ga));
+                    if (!(g > 1e-15 * sqrt(al * be)) || g == 0.0) continue;
+                    const double2 ph = make_double2(ga.x / g, ga.y / g);     // e^{i phi}
+                    const double zeta = (be - al) / (2.0 * g);
+                    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                    const double2 phc = cconj(ph);
+                    for (int i = lane; i < m; i += 32) {
+                        const double2 x = A[p][i], y = cmul(phc, A[q][i]);
+                        A[p][i] = csub(cscal(x, c), cscal(y, sn));
+                        A[q][i] = cadd(cscal(x, sn), cscal(y, c));
+                    }
+                    for (int i = lane; i < k; i += 32) {
+                        const double2 x = V[p][i], y = cmul(phc, V[q][i]);
+                        V[p][i] = csub(cscal(x, c), cscal(y, sn));
+                        V[q][i] = cadd(cscal(x, sn), cscal(y, c));
+                    }
+                    if (lane == 0) s_rot = 1;
+                }
+                __syncthreads();
+            }
+            const int rot = s_rot;
+            __syncthreads();
+            if (!rot) break;
+        }
+        // weights: the V column whose A column has the smallest norm
+        if (tid == 0) {
+            int cmin = 0;
+            double nmin = INFINITY;
+            for (int c = 0; c < k; ++c) {
+                double nrm = 0.0;
+                for (int i = 0; i < m; ++i) nrm += cabs2(A[c][i]);
+                if (nrm < nmin) {
+                    nmin = nrm;
+                    cmin = c;
+                }
+            }
+            s_idx[0] = cmin;
+        }
+        __syncthreads();
+        if (tid < k) W[tid] = V[s_idx[0]][tid];
+        __syncthreads();
+        // new approximant on the remaining samples and its largest deviation
+        double dev = 0.0;
+        for (int i = tid; i < m; i += kAaaThreads) {
+            if (!rest[i]) {
+                R[i] = F[i];
+                continue;
+            }
+            double2 num = cz(), den = cz();
+            for (int c = 0; c < k; ++c) {
+                const double2 cw = cdiv(W[c], csub(Z[i], Z[sup[c]]));
+                num = cadd(num, cmul(cw, F[sup[c]]));
+                den = cadd(den, cw);
+            }
+            R[i] = cdiv(num, den);
+            const double e = sqrt(cabs2(csub(F[i], R[i])));
+            if (!(e <= dev)) dev = e;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double od = __shfl_down_sync(0xffffffffu, dev, o);
+            if (!(od <= dev)) dev = od;
+        }
+        if (lane == 0) s_red[warp] = dev;
+        __syncthreads();
+        if (tid == 0) {
+            double d = 0.0;
+            for (int w = 0; w < nw; ++w)
+                if (!(s_red[w] <= d)) d = s_red[w];
+            if (d <= tol * s_fmax || k >= kcap || k >= m) s_done = 1;
+        }
+        __syncthreads();
+    }
+    const int k = s_k;
+    for (int e = tid; e < ne; e += kAaaThreads) {
+        const double2 x = ze[e];
+        double2 num = cz(), den = cz(), hit = cz();
+        bool on = false;
+        for (int c = 0; c < k; ++c) {
+            const double2 d = csub(x, Z[sup[c]]);
+            if (d.x == 0.0 && d.y == 0.0) {
+                on = true;
+                hit = F[sup[c]];
+                break;
+            }
+            const double2 cw = cdiv(W[c], d);
+            num = cadd(num, cmul(cw, F[sup[c]]));
+            den = cadd(den, cw);
+        }
+        re[(size_t)fn * ne + e] = on ? hit : cdiv(num, den);
+    }
+    if (tid == 0 && degree) degree[fn] = k;
+}
+
 // x[list[i]] += d[i] for the listed pairs (refinement update).
 __global__ void pair_axpy_kernel(int nlist, const int* __restrict__ list, int npw, const double2* __restrict__ d,
                                  double2* __restrict__ x) {
@@ -1230,6 +1470,15 @@ cudaError_t launch_screening(int n, int nw, const double2* dn, const double* qg,
     cudaError_t e = allow_max_smem((const void*)screening_kernel);
     if (e != cudaSuccess) return e;
     screening_kernel<<<nw, kThreads, smem, st>>>(n, nw, dn, qg, inv_vol, r_cut, einv, wbar, bad);
+    return cudaGetLastError();
+}
+cudaError_t launch_aaa(int nfun, int m, const double2* z, const double2* f, double tol, int mmax, int ne,
+                       const double2* ze, double2* re, int* degree, int* bad, cudaStream_t st) {
+    if (nfun == 0) return cudaSuccess;
+    const int smem = (int)(sizeof(double2) * (kAaaMaxK * kAaaMaxM + kAaaMaxK * kAaaMaxK));
+    cudaError_t e = allow_max_smem((const void*)aaa_kernel);
+    if (e != cudaSuccess) return e;
+    aaa_kernel<<<nfun, kAaaThreads, smem, st>>>(m, z, f, tol, mmax, ne, ze, re, degree, bad);
     return cudaGetLastError();
 }
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st) {

@@ -129,6 +129,11 @@ cudaError_t launch_density(int n_v, int n_p, int nw, int npw, const double2* R, 
 int screening_smem_bytes(int n);
 cudaError_t launch_screening(int n, int nw, const double2* dn, const double* qg, double inv_vol, double r_cut,
                              double2* einv, double2* wbar, int* bad, cudaStream_t st);
+// AAA approximation of nfun functions sampled at the m points z (f [nfun][m], m <= 128,
+// mmax <= 32), evaluated at ze [ne] into re [nfun][ne]; degree [nfun] (support points) may be
+// null; *bad is set when a function has a non-finite sample.
+cudaError_t launch_aaa(int nfun, int m, const double2* z, const double2* f, double tol, int mmax, int ne,
+                       const double2* ze, double2* re, int* degree, int* bad, cudaStream_t st);
 // rhs[c][g] = 1 if g == cols[c] else 0 ([ncol][npw]); the right-hand sides of Eq. 2.
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st);
 cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st);

@@ -24,7 +24,7 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
                 "SGW_EUNSUPPORTED"]
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
-           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_screened_coulomb", "sgw_residual", "sgw_residual_noalloc",
+           "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_density_response_w", "sgw_aaa", "sgw_screened_coulomb", "sgw_residual", "sgw_residual_noalloc",
            "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
            "sgw_mlp_forward", "sgw_mlp_grad", "sgw_mlp_train_step", "sgw_mlp_destroy", "sgw_destroy_system",
            "sgw_last_error"]
@@ -84,6 +84,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_density_response.argtypes = [vp, ip, ip, vp, vp, ip, vp, dp, dp, dp, ctypes.POINTER(_Opts), vp,
                                          ctypes.POINTER(_Report)]
     lib.sgw_screened_coulomb.argtypes = [ip, ip, vp, vp, dp, dp, vp, vp, vp]
+    lib.sgw_density_response_w.argtypes = [vp, ip, ip, vp, vp, ip, vp, dp, dp, ctypes.POINTER(_Opts), vp,
+                                           ctypes.POINTER(_Report)]
+    lib.sgw_aaa.argtypes = [ip, ip, vp, vp, dp, ip, ip, vp, vp, vp, vp]
     lib.sgw_residual.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_residual_noalloc.argtypes = [vp, ip, vp, vp, ip, vp, dp, vp, vp, vp, vp]
     lib.sgw_solve_pershift.argtypes = [vp, ip, vp, vp, vp, dp, dp, ip, vp, vp, ctypes.POINTER(_Opts), vp,
@@ -152,6 +155,24 @@ def _stream_of(x, stream):
         import torch
         return torch.cuda.current_stream(x.device).cuda_stream
     return None
+
+
+def aaa(z, f, z_eval, tol=1e-13, mmax=32, stream=None):
+    """sgw_aaa: AAA approximants of the rows of f (sampled at the points z), evaluated at
+    z_eval.  Returns (r [nfun][n_eval] like f, degree [nfun])."""
+    zc = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).ravel())
+    ze = np.ascontiguousarray(np.asarray(z_eval, dtype=np.complex128).ravel())
+    f = _c128(f)
+    if f.ndim == 1:
+        f = f.reshape(1, -1)
+    nfun, m = f.shape
+    if m != len(zc):
+        raise ValueError("f must be [nfun][len(z)]")
+    r = _like(f, (nfun, len(ze)))
+    deg = np.zeros(nfun, dtype=np.int32)
+    _check(load().sgw_aaa(nfun, m, zc.ctypes.data, _ptr(f), float(tol), int(mmax), len(ze), ze.ctypes.data, _ptr(r),
+                          deg.ctypes.data, _stream_of(f, stream)))
+    return r, deg
 
 
 def screened_coulomb(dn, qg, volume, r_cut, want_eps_inv=True, stream=None):
@@ -345,6 +366,38 @@ class System:
         s = load().sgw_density_response(self._h, n_v, n_p, _ptr(rhs), eps_v.ctypes.data, nw, omega.ctypes.data,
                                         float(eta), float(weight), float(tol), ctypes.byref(opts), _ptr(out),
                                         ctypes.byref(crep))
+        _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
+        return out, rep, s == SGW_OK
+
+    def density_response_w(self, rhs, eps_v, w, weight=1.0, tol=1e-10, precision="fp64", max_matvec=0,
+                           max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False):
+        """sgw_density_response_w: as density_response at complex frequencies w (w = 1j * omega on
+        the imaginary axis); returns (dn [n_pert][n_pert][nw], report, converged)."""
+        rhs = _c128(rhs)
+        eps_v = np.ascontiguousarray(eps_v, dtype=np.float64)
+        wc = np.asarray(w, dtype=np.complex128).ravel()
+        ww = np.ascontiguousarray(np.column_stack([wc.real, wc.imag]))
+        n_v = len(eps_v)
+        if n_v == 0 or rhs.shape[0] % n_v:
+            raise ValueError("rhs rows must be n_v * n_pert")
+        n_p, nw = rhs.shape[0] // n_v, len(wc)
+        if out is None:
+            if _is_torch(rhs):
+                import torch
+                out = torch.zeros((n_p, n_p, nw), dtype=torch.complex128, device=rhs.device)
+            else:
+                out = np.zeros((n_p, n_p, nw), dtype=np.complex128)
+        nr = rhs.shape[0]
+        rep = {"matvecs": np.zeros((nr, 2 * nw), dtype=np.int32), "est_res": np.zeros((nr, 2 * nw)),
+               "rel_res": np.zeros((nr, 2 * nw)), "cert": np.zeros((nr, 2 * nw)),
+               "status": np.zeros((nr, 2 * nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
+               "kernel_ms": np.zeros(1)}
+        opts = _Opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(rhs, stream))
+        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
+                                                        "kernel_ms")))
+        s = load().sgw_density_response_w(self._h, n_v, n_p, _ptr(rhs), eps_v.ctypes.data, nw, ww.ctypes.data,
+                                          float(weight), float(tol), ctypes.byref(opts), _ptr(out), ctypes.byref(crep))
         _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
         return out, rep, s == SGW_OK
 
