@@ -100,7 +100,9 @@ def test_green_matches_projected_sternheimer(sgw, cfg1):
     assert ok
     g, rep2, ok2 = s.solve_green(np.arange(s.n_pw), e + om + 1j * cfg1.eta, tol=TOL)
     assert ok2
-    pr = O.project_c(kp.psi_kq, rhs)
+    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, cfg1.gp_miller)[:3]
+    assert np.array_equal(rhs, rref)
+    pr = O.project_c(kp.psi_kq, rref)
     for j in range(3):
         y = (g[:, j, :].T @ pr.T).T
         assert _relerr(x[:, j], y).max() <= 1e-8

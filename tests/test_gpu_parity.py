@@ -48,6 +48,15 @@ def _systems(P, inst, ik=0):
     return skq, sk
 
 
+def _rhs_pair(skq, sk, kp, gp):
+    """The Eq. 8 right-hand sides from the library (fed to the library) and from the oracle
+    (fed to the oracle); the two are bit-identical."""
+    rhs = skq.make_rhs(sk, kp.psi_k, gp)
+    ref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, gp)
+    assert np.array_equal(rhs, ref)
+    return rhs, ref
+
+
 def _relerr(a, b):
     return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
 
@@ -121,18 +130,18 @@ def test_solve_config1_all_pairs(sgw, cfg1):
     """Full config 1 (32 rhs x 16 omega) against the oracle's LU, every pair."""
     kp = cfg1.kpoints[0]
     skq, sk = _systems(sgw, cfg1)
-    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)
+    rhs, rref = _rhs_pair(skq, sk, kp, cfg1.gp_miller)
     e_ref = cfg1.e_ref(0)
     dpsi, rep, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, tol=1e-10)
     h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
-    ref = O.solve_shifted(h, kp.psi_kq, rhs, e_ref, cfg1.omega, cfg1.eta)
+    ref = O.solve_shifted(h, kp.psi_kq, rref, e_ref, cfg1.omega, cfg1.eta)
     err = _relerr(dpsi, ref)
     assert ok, rep["status"]
     assert err.max() < TOL_SOLVE, err.max()
     assert rep["rel_res"].max() <= 1e-10
     rel, cert = skq.residual(rhs, e_ref, cfg1.omega, cfg1.eta, dpsi)
     np.testing.assert_allclose(rel, rep["rel_res"], rtol=1e-6, atol=1e-16)
-    ref_rel, _ = O.residual(h, kp.psi_kq, rhs[:4], e_ref[:4], cfg1.omega, cfg1.eta, dpsi[:4])
+    ref_rel, _ = O.residual(h, kp.psi_kq, rref[:4], e_ref[:4], cfg1.omega, cfg1.eta, dpsi[:4])
     np.testing.assert_allclose(rel[:4], ref_rel, rtol=1e-3, atol=1e-14)
     assert np.all(err <= cert * (1 + 1e-6) + 1e-15)
 
@@ -143,7 +152,7 @@ def test_solve_config2_sampled(sgw, cfg2):
     32 perturbations compared with the oracle's LU; the residual certificate on every pair."""
     kp = cfg2.kpoints[0]
     skq, sk = _systems(sgw, cfg2)
-    rhs = skq.make_rhs(sk, kp.psi_k, cfg2.gp_miller)
+    rhs, rref = _rhs_pair(skq, sk, kp, cfg2.gp_miller)
     e_ref = cfg2.e_ref(0)
     dpsi, rep, ok = skq.solve_shifted(rhs, e_ref, cfg2.omega, cfg2.eta, tol=1e-10)
     assert ok, np.unique(rep["status"], return_counts=True)
@@ -152,7 +161,7 @@ def test_solve_config2_sampled(sgw, cfg2):
     for v in (0, 15):
         rows = np.arange(v * npert, (v + 1) * npert)
         for j in (0, 21, 42, 63):
-            ref = O.solve_shifted(h, kp.psi_kq, rhs[rows], e_ref[rows], cfg2.omega[j:j + 1], cfg2.eta)[:, 0]
+            ref = O.solve_shifted(h, kp.psi_kq, rref[rows], e_ref[rows], cfg2.omega[j:j + 1], cfg2.eta)[:, 0]
             err = _relerr(dpsi[rows, j], ref)
             assert err.max() < TOL_SOLVE, (v, j, err.max())
     assert rep["rel_res"].max() <= 1e-10
@@ -180,11 +189,12 @@ def test_bicgstab_matches_oracle_where_converged(sgw, cfg1, ell):
     """The paper-cited shifted BiCGstab(ell): same answer as the LU where it converges."""
     kp = cfg1.kpoints[0]
     skq, sk = _systems(sgw, cfg1)
-    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[:8]
+    rhs, rref = _rhs_pair(skq, sk, kp, cfg1.gp_miller)
+    rhs, rref = rhs[:8], rref[:8]
     e_ref = cfg1.e_ref(0)[:8]
     d, rep, _ = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, method="bicgstab", ell=ell)
     h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
-    ref = O.solve_shifted(h, kp.psi_kq, rhs, e_ref, cfg1.omega, cfg1.eta)
+    ref = O.solve_shifted(h, kp.psi_kq, rref, e_ref, cfg1.omega, cfg1.eta)
     conv = rep["status"] == 0
     assert conv.sum() >= conv.size // 2
     assert _relerr(d, ref)[conv].max() < TOL_SOLVE
@@ -285,11 +295,11 @@ def test_apply_h_df32_matches_dense(sgw, which, request):
 def test_solve_df32_config1_all_pairs(sgw, cfg1):
     kp = cfg1.kpoints[0]
     skq, sk = _systems(sgw, cfg1)
-    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)
+    rhs, rref = _rhs_pair(skq, sk, kp, cfg1.gp_miller)
     e_ref = cfg1.e_ref(0)
     dpsi, rep, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, tol=1e-10, precision="df32")
     h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
-    ref = O.solve_shifted(h, kp.psi_kq, rhs, e_ref, cfg1.omega, cfg1.eta)
+    ref = O.solve_shifted(h, kp.psi_kq, rref, e_ref, cfg1.omega, cfg1.eta)
     assert ok
     assert rep["rel_res"].max() <= 1e-10
     assert _relerr(dpsi, ref).max() < TOL_SOLVE
@@ -300,7 +310,7 @@ def test_solve_df32_config2_sampled(sgw, cfg2):
     omega; FP64 true residual of every pair <= 1e-10; LU comparison on sampled pairs."""
     kp = cfg2.kpoints[0]
     skq, sk = _systems(sgw, cfg2)
-    rhs = skq.make_rhs(sk, kp.psi_k, cfg2.gp_miller)
+    rhs, rref = _rhs_pair(skq, sk, kp, cfg2.gp_miller)
     npert = cfg2.n_pert
     rows = np.concatenate([np.arange(v * npert, v * npert + 16) for v in (0, 5, 10, 15)])
     e_ref = cfg2.e_ref(0)[rows]
@@ -309,7 +319,7 @@ def test_solve_df32_config2_sampled(sgw, cfg2):
     assert rep["rel_res"].max() <= 1e-10
     h, _, _ = O.dense_h_inst(cfg2, kp.kq_frac)
     for j in (0, 40, 63):
-        ref = O.solve_shifted(h, kp.psi_kq, rhs[rows[:16]], e_ref[:16], cfg2.omega[j:j + 1], cfg2.eta)[:, 0]
+        ref = O.solve_shifted(h, kp.psi_kq, rref[rows[:16]], e_ref[:16], cfg2.omega[j:j + 1], cfg2.eta)[:, 0]
         assert _relerr(dpsi[:16, j], ref).max() < TOL_SOLVE
 
 

@@ -27,7 +27,10 @@ def env():
     sk = P.System.from_instance(inst, kp.k_frac)
     skq.set_occupied(kp.psi_kq, kp.eps_kq)
     rhs = skq.make_rhs(sk, kp.psi_k, inst.gp_miller)
-    return P, inst, skq, rhs
+    # the oracle's own right-hand sides and basis (bit-identical to the library's) feed the oracle
+    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, inst.gp_miller)
+    assert np.array_equal(rhs, rref)
+    return P, inst, skq, rhs, rref
 
 
 def _theta(seed=3):
@@ -98,15 +101,15 @@ def test_training_reduces_loss(env):
 
 
 def test_diagonals_match_oracle(env):
-    P, inst, skq, rhs = env
+    P, inst, skq, rhs, rref = env
     kp = inst.kpoints[0]
-    mil, kin = skq.gvectors
+    mil, kin = O.gsphere(inst.a, kp.kq_frac, inst.ecut_ry)   # the oracle's basis
     rows = [0, 7, 19]
     e = inst.e_ref(0)[rows]
     om = inst.omega[[2, 9, 15]]
     d = skq.precond_diag(rhs[rows], e, om, inst.eta, "plain")
     for i, r in enumerate(rows):
-        np.testing.assert_allclose(d[i], M.plain_scaling(kin, rhs[r]), rtol=1e-13)
+        np.testing.assert_allclose(d[i], M.plain_scaling(kin, rref[r]), rtol=1e-13)
     beta = O.kb_beta(inst.a, inst.tau, kp.kq_frac, mil, inst.kb_atom, inst.kb_width)
     hd = M.h_diag(kin, inst.vloc_r.mean(), beta, inst.kb_d)
     dj = skq.precond_diag(rhs[rows], e, om, inst.eta, "jacobi", delta=[0.1, 0.3, 1.0])
@@ -118,15 +121,15 @@ def test_diagonals_match_oracle(env):
     dl = skq.precond_diag(rhs[rows], e, om, inst.eta, "learned", mlp=mlp)
     for i, r in enumerate(rows):
         f = M.features(kin, inst.ecut_ry, om[i], e[i], inst.vloc_r.mean())
-        ref = M.plain_scaling(kin, rhs[r]) * np.exp(M.forward(M.bf16_round(th), f))
+        ref = M.plain_scaling(kin, rref[r]) * np.exp(M.forward(M.bf16_round(th), f))
         np.testing.assert_allclose(dl[i], ref, rtol=2e-4)
 
 
 def test_training_rows_match_oracle(env):
     import torch
-    P, inst, skq, rhs = env
+    P, inst, skq, rhs, rref = env
     kp = inst.kpoints[0]
-    mil, kin = skq.gvectors
+    mil, kin = O.gsphere(inst.a, kp.kq_frac, inst.ecut_ry)   # the oracle's basis
     rows = [3, 11]
     e = inst.e_ref(0)[rows]
     om = inst.omega[[4, 12]]
@@ -137,7 +140,7 @@ def test_training_rows_match_oracle(env):
     hd = M.h_diag(kin, inst.vloc_r.mean(), beta, inst.kb_d)
     for i, r in enumerate(rows):
         np.testing.assert_allclose(f[i], M.features(kin, inst.ecut_ry, om[i], e[i], inst.vloc_r.mean()), rtol=1e-6)
-        m = M.plain_scaling(kin, rhs[r])
+        m = M.plain_scaling(kin, rref[r])
         j = M.jacobi_scaling(hd, e[i] + om[i] + 1j * inst.eta, delta[i]) if delta[i] > 0 else None
         np.testing.assert_allclose(t[i], M.targets(m, j), atol=1e-6)
 
@@ -145,7 +148,7 @@ def test_training_rows_match_oracle(env):
 @pytest.mark.parametrize("precond", ["none", "plain", "jacobi", "learned"])
 def test_pershift_solve_matches_lu(env, precond):
     """Preconditioning changes the route, not the answer: per-shift solves vs the oracle LU."""
-    P, inst, skq, rhs = env
+    P, inst, skq, rhs, rref = env
     kp = inst.kpoints[0]
     rows = np.array([0, 5, 13, 20, 27, 31])
     cols = np.array([0, 3, 8, 11, 14, 15])
@@ -158,5 +161,5 @@ def test_pershift_solve_matches_lu(env, precond):
     assert rep["rel_res"].max() <= 1e-10
     h, _, _ = O.dense_h_inst(inst, kp.kq_frac)
     for i, (r, j) in enumerate(zip(rows, cols)):
-        ref = O.solve_shifted(h, kp.psi_kq, rhs[r:r + 1], e[i:i + 1], om[i:i + 1], inst.eta)[0, 0]
+        ref = O.solve_shifted(h, kp.psi_kq, rref[r:r + 1], e[i:i + 1], om[i:i + 1], inst.eta)[0, 0]
         assert np.linalg.norm(x[i] - ref) / np.linalg.norm(ref) < 1e-8
