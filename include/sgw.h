@@ -144,7 +144,7 @@ typedef struct {
                          Lanczos, whose basis it sizes, 40000 for BiCGstab); the Lanczos basis is also
                          capped by free device memory */
     int max_refine;   /* rounds of per-shift correction solves (0 -> 3, negative -> none) */
-    int threads;      /* CTA size of the Lanczos kernel: 256, 384 or 512 (0 -> 384) */
+    int threads;      /* CTA size of the Lanczos kernel: 256, 384 or 512 (0 -> 512 float-float, 384 FP64) */
     void* stream;     /* cudaStream_t, NULL = default stream */
 } sgw_solve_opts;
 

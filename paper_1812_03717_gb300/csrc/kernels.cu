@@ -1504,15 +1504,20 @@ const void* lanczos_ptr(int nt) {
     if (nt == 384) return (const void*)lanczos_solve_kernel<Ar, 384>;
     return (const void*)lanczos_solve_kernel<Ar, 256>;
 }
-int lanczos_threads(int requested) { return requested == 256 || requested == 512 ? requested : 384; }
+// CTA size: the requested 256 / 384 / 512, else the measured best for the precision (512 for
+// float-float, 384 for FP64 on the config-2 workload)
+int lanczos_threads(int requested, bool df) {
+    if (requested == 256 || requested == 384 || requested == 512) return requested;
+    return df ? 512 : 384;
+}
 }  // namespace
 
 cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int threads, int* grid) {
-    const int nt = lanczos_threads(threads);
+    const int nt = lanczos_threads(threads, false), nt2 = lanczos_threads(threads, true);
     int g = 0, g2 = 0;
     cudaError_t e = resident_grid(lanczos_ptr<ArF64>(nt), lanczos_smem_bytes(P, nshift), &g, nt);
     if (e != cudaSuccess) return e;
-    e = resident_grid(lanczos_ptr<ArDF>(nt), lanczos_smem_bytes(P, nshift), &g2, nt);
+    e = resident_grid(lanczos_ptr<ArDF>(nt2), lanczos_smem_bytes(P, nshift), &g2, nt2);
     if (e != cudaSuccess) return e;
     g = g < g2 ? g : g2;
     *grid = g < nrhs ? g : nrhs;
@@ -1525,7 +1530,7 @@ cudaError_t launch_lanczos(const Plan& P0, const LanczosArgs& a, int grid, int p
     const Plan P = tuned_plan(P0, lanczos_extra(a.nshift));
     const int smem = lanczos_smem_bytes(P0, a.nshift);
     const bool df = precision == SGW_PREC_DF32;
-    const int nt = lanczos_threads(threads);
+    const int nt = lanczos_threads(threads, df);
     const void* k = df ? lanczos_ptr<ArDF>(nt) : lanczos_ptr<ArF64>(nt);
     cudaError_t e = allow_max_smem(k);
     if (e != cudaSuccess) return e;
