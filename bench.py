@@ -66,7 +66,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070   # 80.5 TFLOP/s
 # DRAM bytes (read + write) per 512-right-hand-side launch of the multishift kernel, from the
 # ncu captures in profiles/ (16 right-hand sides, scaled by right-hand sides); None once the
 # kernel has changed since the capture.
-TRAFFIC_PER_LAUNCH = {"df32": 24.7e9, "fp64": 33.2e9}
+TRAFFIC_PER_LAUNCH = {"df32": 22.5e9, "fp64": 33.2e9}
 
 
 def radix_plan(n):
