@@ -19,6 +19,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -167,7 +168,9 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $SGW_CLOCKS_DIR (default: the temporary directory)
+        d = os.environ.get("SGW_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"sgw_clocks_rank{index}.csv")
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
