@@ -840,6 +840,7 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
     const size_t o_st = c.take(sizeof(int) * np);
     const size_t o_rscr = c.take(2 * vb * grid_r);
     const size_t o_rel = c.take(sizeof(double) * np);
+    const size_t o_bvec = c.take(vb * nrhs);
     const size_t o_cert = c.take(sizeof(double) * np);
     const size_t o_list = c.take(sizeof(int) * chunk);
     const size_t o_rvec = c.take(vb * chunk);
@@ -936,10 +937,13 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
     double* d_cert = (double*)(w + o_cert);
     const double* d_eref = (const double*)(w + o_eref);
     const double* d_om = (const double*)(w + o_om);
+    // b = -P_c rhs once per right-hand side, shared by every residual check of its shifts
+    const double2* d_b = (const double2*)(w + o_bvec);
+    SGW_CUDA(launch_project_rhs(plan, nrhs, rhs_d, (double2*)(w + o_bvec), st), "projection kernel");
     SGW_CUDA(launch_residual(plan, nrhs, nomega, nullptr, 0, rhs_d, d_eref, d_om, eta, X,
-                             (double2*)(w + o_rscr), d_rel, d_cert, nullptr, grid_r, st, d_etas),
+                             (double2*)(w + o_rscr), d_rel, d_cert, nullptr, grid_r, st, d_etas, d_b),
              "residual kernel");
-    ++launches;
+    launches += 2;
     std::vector<int> stv(np), mvv(np);
     std::vector<double> estv(np), relv(np), certv(np);
     SGW_CUDA(cudaMemcpyAsync(stv.data(), w + o_st, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
@@ -981,7 +985,7 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
             const int* d_list = (const int*)(w + o_list);
             SGW_CUDA(launch_residual(plan, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
                                      (double2*)(w + o_rscr), d_rel, d_cert, (double2*)(w + o_rvec),
-                                     std::min(grid_r, nc), st, d_etas),
+                                     std::min(grid_r, nc), st, d_etas, d_b),
                      "residual kernel");
             const double tl = std::min(0.5, std::max(1e-13, 0.3 * tol / worst));
             SGW_CUDA(run(true, nc, 1, (const double2*)(w + o_rvec), (const double*)(w + o_eref1), (const double*)(w + o_zero),
@@ -991,7 +995,8 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
                      "correction solve");
             SGW_CUDA(launch_pair_axpy(nc, d_list, s->npw, (const double2*)(w + o_dbuf), X, st), "refinement update");
             SGW_CUDA(launch_residual(plan, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
-                                     (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(grid_r, nc), st, d_etas),
+                                     (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(grid_r, nc), st, d_etas,
+                                     d_b),
                      "residual kernel");
             launches += 4;
             SGW_CUDA(cudaMemcpyAsync(mv1.data(), w + o_mv1, sizeof(int) * nc, cudaMemcpyDeviceToHost, st), "report");

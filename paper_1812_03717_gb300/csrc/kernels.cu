@@ -787,7 +787,8 @@ __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nr
                                                                const double2* __restrict__ x,
                                                                double2* __restrict__ scratch, double* __restrict__ rel,
                                                                double* __restrict__ cert, double2* __restrict__ store,
-                                                               const double* __restrict__ eta_s) {
+                                                               const double* __restrict__ eta_s,
+                                                               const double2* __restrict__ bvec) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double2 s_dot[kRedSlots];
     load_twiddles<ArF64>(P, smem);
@@ -812,12 +813,18 @@ __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nr
         }
         __syncthreads();
         apply_h_block<ArF64>(P, smem, xs, ys, cz(), APPLY_PROJ_OUT);
-        block_dots(P.psi, P.nocc, npw, rv, npw, red, coef);
+        const double2* bv = bvec ? bvec + (size_t)r * npw : nullptr;   // -P_c rhs, when precomputed
+        if (!bv) block_dots(P.psi, P.nocc, npw, rv, npw, red, coef);
         double2 acc[3] = {cz(), cz(), cz()};
         for (int g = tid; g < npw; g += nt) {
-            double2 h = rv[g];
-            for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
-            const double2 b = make_double2(-h.x, -h.y);
+            double2 b;
+            if (bv) {
+                b = bv[g];
+            } else {
+                double2 h = rv[g];
+                for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
+                b = make_double2(-h.x, -h.y);
+            }
             const double2 ax = csub(ys[g], cmul(z, xv[g]));
             const double2 res = csub(b, ax);
             if (store) store[(size_t)i * npw + g] = make_double2(-res.x, -res.y);
@@ -835,6 +842,25 @@ __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nr
                 rel[q] = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
                 cert[q] = xn > 0.0 ? rn / (fabs(z.y) * xn) : (rn > 0.0 ? INFINITY : 0.0);
             }
+        }
+        __syncthreads();
+    }
+}
+
+// b[r] = -P_c rhs[r] in FP64 (the right-hand sides of the shifted systems), one CTA per vector.
+__global__ void __launch_bounds__(kThreads) project_rhs_kernel(Plan P, int nrhs, const double2* __restrict__ rhs,
+                                                               double2* __restrict__ b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double2* red = reinterpret_cast<double2*>(smem);
+    double2* coef = red + (kMaxThreads / 32) * kRedSlots;
+    const int npw = P.npw;
+    for (int r = blockIdx.x; r < nrhs; r += gridDim.x) {
+        const double2* rv = rhs + (size_t)r * npw;
+        block_dots(P.psi, P.nocc, npw, rv, npw, red, coef);
+        for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+            double2 h = rv[g];
+            for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
+            b[(size_t)r * npw + g] = make_double2(-h.x, -h.y);
         }
         __syncthreads();
     }
@@ -1446,13 +1472,13 @@ cudaError_t launch_apply(const Plan& P0, int nvec, const double2* x, double2* y,
 cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int grid, cudaStream_t st,
-                            const double* eta_s) {
+                            const double* eta_s, const double2* bvec) {
     const Plan P = tuned_plan(P0, 0);
     const int smem = apply_smem_bytes(P0);
     cudaError_t e = allow_max_smem((const void*)residual_kernel);
     if (e != cudaSuccess) return e;
     residual_kernel<<<grid, kResThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
-                                                  cert, store, eta_s);
+                                                  cert, store, eta_s, bvec);
     return cudaGetLastError();
 }
 
@@ -1479,6 +1505,14 @@ cudaError_t launch_aaa(int nfun, int m, const double2* z, const double2* f, doub
     cudaError_t e = allow_max_smem((const void*)aaa_kernel);
     if (e != cudaSuccess) return e;
     aaa_kernel<<<nfun, kAaaThreads, smem, st>>>(m, z, f, tol, mmax, ne, ze, re, degree, bad);
+    return cudaGetLastError();
+}
+cudaError_t launch_project_rhs(const Plan& P, int nrhs, const double2* rhs, double2* b, cudaStream_t st) {
+    if (nrhs == 0) return cudaSuccess;
+    const int smem = (int)(sizeof(double2) * ((kMaxThreads / 32) * kRedSlots + ((P.nocc + 7) / 8 * 8 + 8)));
+    cudaError_t e = allow_max_smem((const void*)project_rhs_kernel);
+    if (e != cudaSuccess) return e;
+    project_rhs_kernel<<<nrhs < 1024 ? nrhs : 1024, kThreads, smem, st>>>(P, nrhs, rhs, b);
     return cudaGetLastError();
 }
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st) {

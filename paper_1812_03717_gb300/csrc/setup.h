@@ -115,11 +115,14 @@ cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid);
 cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
                          double2* scratch, int grid, int precision, cudaStream_t st);
-// Im z_rj = eta_s[j] when eta_s is given, else eta; the certificate divides by |Im z|.
+// Im z_rj = eta_s[j] when eta_s is given, else eta; the certificate divides by |Im z|;
+// bvec [nrhs][npw] = -P_c rhs when given (else the kernel projects rhs itself).
 cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int grid, cudaStream_t st,
-                            const double* eta_s = nullptr);
+                            const double* eta_s = nullptr, const double2* bvec = nullptr);
+// b[r] = -P_c rhs[r] (FP64) for r < nrhs; a precomputed bvec lets the residual kernel skip it.
+cudaError_t launch_project_rhs(const Plan& P, int nrhs, const double2* rhs, double2* b, cudaStream_t st);
 // dn[po][pi][j] += weight sum_v sum_g conj(R[v n_p + po][g]) (X[v n_p + pi][j][g] + X[v n_p + pi][nw + j][g])
 // (Eq. 5 in reciprocal space); R [n_v n_p][npw], X [n_v n_p][2 nw][npw], dn [n_p][n_p][nw].
 cudaError_t launch_density(int n_v, int n_p, int nw, int npw, const double2* R, const double2* X, double weight,
