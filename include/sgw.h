@@ -11,6 +11,11 @@
  * H + alpha P_occ - z for any alpha > 0), and the driving field of Eq. 8 given by the
  * caller as rhs_r = dV psi_v expressed in this system's plane-wave basis.  All shifts
  * of one right-hand side share one Krylov space (Sec. 2.2): one seed system carries them.
+ * The same machinery gives the columns of the Green's function of Eq. 2-3
+ * (sgw_solve_green), the density response of Eq. 5 on the real or imaginary frequency axis
+ * (sgw_density_response, sgw_density_response_w); sgw_screened_coulomb turns the response
+ * into epsilon^-1 and W-bar (Eq. 4, 9) and sgw_aaa continues sampled functions by AAA
+ * (Sec. 2.7).
  *
  * Units: Hartree atomic units (Ha, bohr).  E_cut is in Ry: the basis of Eq. 1 is the
  * sphere |k+G|^2 <= E_cut[Ry] (bohr^-2).  Complex numbers are interleaved FP64 pairs
