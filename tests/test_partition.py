@@ -1,5 +1,6 @@
-"""Host logic of the multi-rank path: sharding covers every unit once, and a two-rank gloo
-group reduces the per-rank timings with a max, as bench.py does."""
+"""Host logic of the multi-rank path: sharding covers every unit once, a two-rank gloo group
+reduces the per-rank timings with a max, as bench.py does, and the k-point sum of the
+density response (Eq. 5) over ranks equals the single-process sum."""
 import os
 import socket
 
@@ -8,7 +9,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_1812_03717_gb300.partition import block_range, units_for_step
+from paper_1812_03717_gb300.partition import allreduce_density, block_range, units_for_step
 
 
 @pytest.mark.parametrize("n,world", [(0, 1), (7, 1), (7, 2), (2048, 3), (5, 8)])
@@ -66,3 +67,49 @@ def test_two_rank_gloo_sharding_and_max_time():
     assert tmax == 20.0
     flat = sorted(u for us in units for u in us)
     assert flat == [0, 1, 2, 3]
+
+
+def _density_contribution(k):
+    """A seeded stand-in for one k-point's contribution dn_k[G][G'][omega]."""
+    g = torch.Generator().manual_seed(100 + k)
+    re = torch.randn(5, 5, 3, generator=g, dtype=torch.float64)
+    im = torch.randn(5, 5, 3, generator=g, dtype=torch.float64)
+    return torch.complex(re, im)
+
+
+def _density_worker(rank, world, port, nk, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    dn = torch.zeros(5, 5, 3, dtype=torch.complex128)
+    lo, hi = block_range(nk, world, rank)
+    for k in range(lo, hi):
+        dn += _density_contribution(k)
+    allreduce_density(dn)
+    q.put((rank, dn.numpy()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_density_allreduce_equals_serial_sum():
+    nk, world = 5, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_density_worker, args=(r, world, port, nk, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    serial = sum(_density_contribution(k) for k in range(nk)).numpy()
+    for r in range(world):
+        assert abs(got[r] - serial).max() <= 1e-12 * abs(serial).max()
+
+
+def test_density_allreduce_single_process_is_identity():
+    dn = _density_contribution(0)
+    before = dn.clone()
+    assert allreduce_density(dn) is dn
+    assert torch.equal(dn, before)
