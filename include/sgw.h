@@ -287,8 +287,11 @@ sgw_status sgw_residual(sgw_system* sys, int nrhs, const void* rhs, const double
  * callers that cannot let a library allocate device memory, e.g. a framework whose caching
  * allocator or fixed arena owns all device memory, or a code path that must not pay the
  * device-wide synchronisation cudaFree can imply).  Same results as sgw_residual, but:
- *   - every array argument (rhs, e_ref, omega, dpsi, rel_res, cert) must be a device pointer
- *     of the system's device (else SGW_EINVAL); rel_res and cert are written on the device;
+ *   - every array argument (rhs, e_ref, omega, dpsi, rel_res, cert) must be device memory of
+ *     the system's device, or managed memory (else SGW_EINVAL: host memory and other GPUs'
+ *     memory are refused before anything is launched); rel_res and cert are written on the
+ *     device; nrhs * nomega must not exceed INT_MAX (else SGW_EUNSUPPORTED);
+ *   - the calling thread's current device is the same after the call as before it;
  *   - it calls no cudaMalloc / cudaFree: its scratch (2 * n_pw complex values per CTA) is a
  *     built-in device array of SGW_NOALLOC_SCRATCH_BYTES, held by every GPU that loads the
  *     library until the process exits; n_pw > SGW_NOALLOC_SCRATCH_BYTES / 32 gives

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <mutex>
 
@@ -35,15 +36,35 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double2* g_scratch_ptr[kMaxDevices] = {};   // device address of g_scratch on each device, once looked up
 
-bool device_ptr(const void* p) {
+// Device memory of device `dev` (cudaMalloc, a memory pool of that device), or managed
+// memory (reachable from every device).  Host memory, registered or not, and device memory of
+// any other GPU are refused: the kernel would read another device's memory over the
+// interconnect, or fault.
+bool device_ptr(const void* p, int dev) {
     if (!p) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
+
+// Makes `dev` current for the lifetime of the guard and then restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+        if (err != cudaSuccess) prev = -1;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -59,9 +80,13 @@ extern "C" sgw_status sgw_residual_noalloc(sgw_system* sys, int nrhs, const void
     if (P->nocc == 0) return noalloc_fail(SGW_ESTATE, "sgw_set_occupied has not been called");
     const size_t np = (size_t)nrhs * nomega;
     if (np == 0) return SGW_OK;
-    if (!device_ptr(rhs) || !device_ptr(e_ref) || !device_ptr(omega) || !device_ptr(dpsi) || !device_ptr(rel_res) ||
-        !device_ptr(cert))
-        return noalloc_fail(SGW_EINVAL, "sgw_residual_noalloc takes device pointers only (it stages nothing)");
+    if (np > (size_t)INT_MAX) return noalloc_fail(SGW_EUNSUPPORTED, "nrhs * nomega above INT_MAX");
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(SGW_EUNSUPPORTED, "device index above 63");
+    if (!device_ptr(rhs, dev) || !device_ptr(e_ref, dev) || !device_ptr(omega, dev) || !device_ptr(dpsi, dev) ||
+        !device_ptr(rel_res, dev) || !device_ptr(cert, dev))
+        return noalloc_fail(SGW_EINVAL,
+                            "sgw_residual_noalloc takes device memory of the system's device (or managed memory) "
+                            "only: it stages nothing");
     const size_t per_cta = 2 * (size_t)P->npw;
     if (per_cta > kScratchElems) {
         char buf[200];
@@ -71,14 +96,14 @@ extern "C" sgw_status sgw_residual_noalloc(sgw_system* sys, int nrhs, const void
                       P->npw, per_cta * sizeof(double2), (size_t)SGW_NOALLOC_SCRATCH_BYTES, kScratchElems / 2);
         return noalloc_fail(SGW_EUNSUPPORTED, buf);
     }
-    cudaError_t e = cudaSetDevice(dev);
+    DeviceGuard guard(dev);   // the caller's current device is restored on return
+    cudaError_t e = guard.err;
     if (e != cudaSuccess) return noalloc_fail(SGW_ECUDA, cudaGetErrorString(e));
     double2* scratch = nullptr;
     {
         // First call on this device: look up the device address of the scratch array (the
         // host-side name g_scratch is only a stand-in for it).
         std::lock_guard<std::mutex> lock(g_mu);
-        if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(SGW_EUNSUPPORTED, "device index above 63");
         if (!g_scratch_ptr[dev]) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_scratch);

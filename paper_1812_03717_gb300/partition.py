@@ -31,13 +31,16 @@ def allreduce_density(dn, group=None):
     device, holding this rank's k-point contributions) over the ranks of `group`, in place,
     so every rank ends with the full k-point sum of Eq. 5.  A no-op without an initialised
     process group or with one rank.  The backend must support the tensor's device (gloo for
-    host tensors, NCCL for CUDA tensors); complex values travel as their real pairs."""
+    host tensors, NCCL for CUDA tensors); complex values travel as their real pairs, so dn must
+    be contiguous (a ValueError otherwise)."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
         return dn
     if not dn.is_complex():
         raise TypeError("dn must be a complex tensor")
+    if not dn.is_contiguous():
+        raise ValueError("dn must be contiguous (reduce a contiguous copy and copy it back)")
     view = torch.view_as_real(dn)
     dist.all_reduce(view, op=dist.ReduceOp.SUM, group=group)
     return dn

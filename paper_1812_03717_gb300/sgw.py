@@ -416,10 +416,27 @@ class System:
     def residual_noalloc(self, rhs, e_ref, omega, eta, dpsi, rel_res, cert, stream=None):
         """sgw_residual_noalloc: every argument a CUDA tensor (float64 e_ref / omega / rel_res /
         cert, complex128 rhs / dpsi); writes rel_res and cert on the device; allocates nothing."""
+        import torch
         for t in (rhs, e_ref, omega, dpsi, rel_res, cert):
             if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
                 raise ValueError("residual_noalloc takes contiguous CUDA tensors only")
-        nrhs, nw = rhs.shape[0], omega.shape[0]
+        dev = rhs.device
+        if any(t.device != dev for t in (e_ref, omega, dpsi, rel_res, cert)):
+            raise ValueError("residual_noalloc: every tensor must be on the same device")
+        for t, dt, name in ((rhs, torch.complex128, "rhs"), (dpsi, torch.complex128, "dpsi"),
+                            (e_ref, torch.float64, "e_ref"), (omega, torch.float64, "omega"),
+                            (rel_res, torch.float64, "rel_res"), (cert, torch.float64, "cert")):
+            if t.dtype != dt:
+                raise TypeError(f"residual_noalloc: {name} must be {dt}")
+        if rhs.ndim != 2 or rhs.shape[1] != self.n_pw:
+            raise ValueError("residual_noalloc: rhs must be [nrhs][n_pw]")
+        nrhs, nw = rhs.shape[0], omega.numel()
+        if omega.ndim != 1 or e_ref.shape != (nrhs,):
+            raise ValueError("residual_noalloc: omega must be [nomega], e_ref [nrhs]")
+        if tuple(dpsi.shape) != (nrhs, nw, self.n_pw):
+            raise ValueError("residual_noalloc: dpsi must be [nrhs][nomega][n_pw]")
+        if tuple(rel_res.shape) != (nrhs, nw) or tuple(cert.shape) != (nrhs, nw):
+            raise ValueError("residual_noalloc: rel_res and cert must be [nrhs][nomega]")
         _check(load().sgw_residual_noalloc(self._h, nrhs, rhs.data_ptr(), e_ref.data_ptr(), nw, omega.data_ptr(),
                                            float(eta), dpsi.data_ptr(), rel_res.data_ptr(), cert.data_ptr(),
                                            _stream_of(rhs, stream)))

@@ -6,6 +6,7 @@ import pytest
 
 import instances as I
 import oracle as O
+from parity import assert_columns_close
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +37,7 @@ def test_imaginary_axis_density_config1(sgw):
     h, _, _ = O.dense_h_inst(inst, kp.kq_frac)
     ref = O.density_response_w(h, kp.psi_kq, kp.psi_k, kp.miller_k, kp.miller_kq, kp.eps_k, inst.gp_miller, w,
                                inst.fft_dims, 2.0)
-    assert np.abs(dn - ref).max() <= 1e-8 * np.abs(ref).max()
+    assert_columns_close(dn, ref, 1e-8)
     with pytest.raises(sgw.SgwError, match="EINVAL"):
         skq.density_response_w(rhs, kp.eps_k, [0.3 + 0.0j], tol=1e-10)
 

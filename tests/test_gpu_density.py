@@ -7,6 +7,7 @@ import pytest
 
 import instances as I
 import oracle as O
+from parity import assert_columns_close
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +56,7 @@ def test_density_config1_full(sgw, cfg1, precision):
     assert ok and rep["rel_res"].max() <= TOL
     assert rep["status"].shape == (32, 32)
     ref = _oracle(cfg1, kp, np.arange(4), np.arange(8), cfg1.omega, 2.0)
-    assert np.abs(dn - ref).max() <= 1e-8 * np.abs(ref).max(), np.abs(dn - ref).max() / np.abs(ref).max()
+    assert_columns_close(dn, ref, 1e-8)
 
 
 def test_density_config2_sampled(sgw):
@@ -72,7 +73,7 @@ def test_density_config2_sampled(sgw):
                                        precision="df32")
     assert ok
     ref = _oracle(inst, kp, v_rows, p_rows, om, 0.5)
-    assert np.abs(dn - ref).max() <= 1e-8 * np.abs(ref).max()
+    assert_columns_close(dn, ref, 1e-8)
 
 
 def test_density_minus_omega_adjoint_and_accumulation(sgw, cfg1):

@@ -10,6 +10,7 @@ import pytest
 
 import instances as I
 import oracle as O
+from parity import assert_columns_close
 
 pytestmark = pytest.mark.gpu
 
@@ -62,8 +63,8 @@ def test_screening_matches_oracle_config2_shape(sgw, cfg2, r_cut):
     dn = _synthetic_dn(len(qg), 64, 1)
     einv, wbar = sgw.screened_coulomb(dn, qg, inst.volume, r_cut)
     re, rw = O.screened_coulomb(dn, qg, inst.volume, r_cut)
-    assert np.abs(einv - re).max() <= 1e-10 * np.abs(re).max()
-    assert np.abs(wbar - rw).max() <= 1e-10 * np.abs(rw).max()
+    assert_columns_close(einv, re, 1e-10)
+    assert_columns_close(wbar, rw, 1e-10)
 
 
 def test_screening_chain_config1(sgw):
@@ -83,8 +84,8 @@ def test_screening_chain_config1(sgw):
     dref = O.density_response(h, kp.psi_kq, kp.psi_k, kp.miller_k, kp.miller_kq, kp.eps_k, inst.gp_miller,
                               inst.omega, inst.eta, inst.fft_dims, 2.0)
     re, rw = O.screened_coulomb(dref, qg, inst.volume, 8.0)
-    assert np.abs(einv - re).max() <= 1e-8 * np.abs(re).max()
-    assert np.abs(wbar - rw).max() <= 1e-8 * np.abs(rw).max()
+    assert_columns_close(einv, re, 1e-8)
+    assert_columns_close(wbar, rw, 1e-8)
 
 
 def test_screening_device_buffers_and_zero_wavevector(sgw, cfg2):
@@ -99,7 +100,7 @@ def test_screening_device_buffers_and_zero_wavevector(sgw, cfg2):
     np.testing.assert_allclose(w_dev.cpu().numpy(), w_host, rtol=0, atol=1e-13 * np.abs(w_host).max())
     assert np.all(e_host[3, [0, 1, 2, 4, 5, 6, 7]] == 0) and np.all(e_host[[0, 1, 2, 4, 5, 6, 7], 3] == 0)
     re, rw = O.screened_coulomb(dn, qg, inst.volume, 5.0)
-    assert np.abs(w_host - rw).max() <= 1e-10 * np.abs(rw).max()
+    assert_columns_close(w_host, rw, 1e-10)
 
 
 def test_screening_edge_cases(sgw, cfg2):

@@ -76,3 +76,21 @@ def test_scalings_on_a_known_case():
     j = M.jacobi_scaling(hd, 0.4 + 0.01j, 0.1)
     np.testing.assert_allclose(j, [10.0, 1 / abs(1.9 - 0.01j), 1 / abs(1.4 - 0.01j), 1 / abs(7.9 - 0.01j)])
     np.testing.assert_allclose(M.targets(np.array([1.0, 0.01]), np.array([math.e, 1.0])), [1.0, 3.0])
+
+
+def test_features_on_a_hand_worked_row():
+    """The feature normalisation: T_G / (E_cut / 2) is 1 on the sphere surface |k+G|^2 = E_cut[Ry]
+    (T_G = |k+G|^2 / 2 Ha), the top of the 60 eV frequency window maps to 1 (60 eV = 2.20496 Ha),
+    and e_ref, <V_loc> pass through in Ha.  A Ry/Ha slip in either scale fails this."""
+    ha_ev = 27.211386245988
+    f = M.features(np.array([0.0, 2.5, 5.0]), 10.0, 60.0 / ha_ev, -0.3, -0.7)
+    np.testing.assert_allclose(f[:, 0], [0.0, 0.5, 1.0], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(f[:, 1], 1.0, rtol=0, atol=3e-5)
+    assert np.all(f[:, 2] == -0.3) and np.all(f[:, 3] == -0.7)
+    # on a real basis every kinetic feature lies in (0, 1], the largest close to 1
+    import instances as I
+    inst = I.config1()
+    from instances.generate import sphere
+    mil, n2 = sphere(inst.a, inst.kpoints[0].kq_frac, inst.ecut_ry)
+    k = M.features(0.5 * n2, inst.ecut_ry, 0.0, 0.0, 0.0)[:, 0]
+    assert k.max() <= 1.0 and k.max() > 0.9

@@ -86,7 +86,14 @@ def _density_worker(rank, world, port, nk, q):
     for k in range(lo, hi):
         dn += _density_contribution(k)
     allreduce_density(dn)
-    q.put((rank, dn.numpy()))
+    # a non-contiguous slice is refused before any communication
+    wide = torch.zeros(5, 10, 3, dtype=torch.complex128)
+    try:
+        allreduce_density(wide[:, ::2])
+        refused = False
+    except ValueError:
+        refused = True
+    q.put((rank, dn.numpy(), refused))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -99,10 +106,12 @@ def test_two_rank_density_allreduce_equals_serial_sum():
     procs = [ctx.Process(target=_density_worker, args=(r, world, port, nk, q)) for r in range(world)]
     for p in procs:
         p.start()
-    got = dict(q.get(timeout=120) for _ in range(world))
+    items = [q.get(timeout=120) for _ in range(world)]
+    got = {r: d for r, d, _ in items}
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
+    assert all(refused for _, _, refused in items)
     serial = sum(_density_contribution(k) for k in range(nk)).numpy()
     for r in range(world):
         assert abs(got[r] - serial).max() <= 1e-12 * abs(serial).max()
