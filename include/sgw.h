@@ -102,6 +102,18 @@ sgw_status sgw_get_gvectors(const sgw_system* sys, int* n_pw, int* miller, doubl
 /* Sphere -> box map, entry g = ((m1 mod N1) N2 + (m2 mod N2)) N3 + (m3 mod N3), host int[n_pw]. */
 sgw_status sgw_get_box_map(const sgw_system* sys, int* map);
 
+/* Split of the on-chip FFT box (an implementation choice the paper has no counterpart for:
+ * how the Sec. 2.1 H application is laid out on this GPU).  A box whose sticks and planes do
+ * not fit one CTA's shared memory is shared by a thread-block cluster of csize CTAs, each
+ * holding a contiguous range of sticks and owning their plane waves; the library picks csize
+ * (1..16) at sgw_create_system / sgw_set_occupied as the size that keeps the most SMs busy.
+ * sgw_set_split forces csize (0 restores the automatic choice; SGW_EUNSUPPORTED if the box
+ * cannot be split that way) -- a test and tuning hook; it synchronises the device.
+ * sgw_get_split reports the sizes in use for the 16-byte policies (FP64, float-float) and for
+ * FP32 (0: FP32 does not fit). */
+sgw_status sgw_set_split(sgw_system* sys, int csize);
+sgw_status sgw_get_split(const sgw_system* sys, int* csize, int* csize_fp32);
+
 /* Occupied manifold of this basis (Eq. 7-8: P_occ): psi_v complex [n_occ][n_pw] (host or
  * device) and eps_v [n_occ] (host, Ha).  Rejected with SGW_EINVAL unless
  * max |psi^H psi - I| <= 1e-10.  May be called again to replace the manifold. */
@@ -115,12 +127,18 @@ sgw_status sgw_set_occupied(sgw_system* sys, int n_occ, const void* psi_v, const
 sgw_status sgw_make_rhs(const sgw_system* sys_kq, const sgw_system* sys_k, int n_v, const void* psi_k,
                         int n_pert, const int* gp_miller, void* rhs, void* stream);
 
-/* Arithmetic of the FFT part of an H application (the reciprocal-space parts, the
- * projections, the Krylov recurrences and the true residual are FP64 in every mode). */
+/* Arithmetic of the H application and of the Krylov vectors of the multishift pass.  The
+ * Krylov recurrence scalars, the right-hand side b = -P_c rhs, its norm and the true
+ * residual judging every pair are FP64 in every mode (the problem statement's "FP64" and
+ * "mixed" modes: FP64 is SGW_PREC_FP64; SGW_PREC_DF32 and SGW_PREC_FP32 are two mixed forms). */
 enum {
-    SGW_PREC_FP64 = 0,   /* FP64 FFT (the FP64 pipe) */
-    SGW_PREC_DF32 = 1    /* float-float FFT: value = hi + lo in two FP32 numbers (~48-bit
-                            significand) on the FP32 pipes */
+    SGW_PREC_FP64 = 0,   /* FP64 throughout (the FP64 pipe) */
+    SGW_PREC_DF32 = 1,   /* float-float: value = hi + lo in two FP32 numbers (~48-bit significand)
+                            on the FP32 pipes; one multishift pass reaches FP64-level residuals */
+    SGW_PREC_FP32 = 2    /* FP32 (complex64) inner solve with FP32 accumulation inside FP64
+                            iterative refinement: the multishift pass runs in FP32, every pair's
+                            true residual is formed in FP64 and the pairs above tolerance get
+                            correction solves in float-float until the FP64 check passes */
 };
 
 /* y = H x for nvec vectors [nvec][n_pw] (host or device): kinetic + non-local in
@@ -139,18 +157,35 @@ enum {
     SGW_METHOD_BICGSTAB = 1   /* shifted BiCGstab(ell) (Frommer 2003) */
 };
 
+typedef struct sgw_mlp sgw_mlp;   /* learned preconditioner (below) */
+
 typedef struct {
     int method;       /* SGW_METHOD_* */
-    int precision;    /* SGW_PREC_* of the multishift pass (Lanczos only; corrections and the
-                         true residual are FP64) */
+    int precision;    /* SGW_PREC_* of the multishift pass (Lanczos only; the true residual is
+                         assembled in FP64, with H applied in FP64 for SGW_PREC_FP64 and in
+                         float-float otherwise) */
     int ell;          /* BiCGstab(ell) degree 1..4 (0 -> 4); unused by Lanczos */
     int seed_index;   /* BiCGstab seed shift; -1 -> the largest omega; unused by Lanczos */
     int max_matvec;   /* H applications per right-hand side and per correction solve (0 -> 4096 for
                          Lanczos, whose basis it sizes, 40000 for BiCGstab); the Lanczos basis is also
                          capped by free device memory */
     int max_refine;   /* rounds of per-shift correction solves (0 -> 3, negative -> none) */
-    int threads;      /* CTA size of the Lanczos kernel: 256, 384 or 512 (0 -> 512 float-float, 384 FP64) */
+    int threads;      /* CTA size of the Lanczos kernel: 256, 384 or 512 (0 -> 384 FP64, else 512) */
     void* stream;     /* cudaStream_t, NULL = default stream */
+    double cert_tol;  /* a pair is converged when rel_res <= tol and its error certificate
+                         |r| / (|Im z| |x|) <= cert_tol (0 -> 1e-8; negative -> not checked) */
+    const void* x0;   /* NULL, or initial solutions [nrhs][nomega][n_pw] (host or device; e.g. a
+                         previous call's dpsi, to resume): the multishift pass is skipped, every
+                         pair's true residual is checked from x0 and only the pairs above the
+                         tolerances get per-shift correction solves */
+    int precond;      /* SGW_PRECOND_* of the per-shift correction solves: NONE -> shifted Lanczos
+                         (one shift), PLAIN / LEARNED -> right-preconditioned BiCGstab(ell)
+                         (one CTA per vector systems only; else SGW_EUNSUPPORTED) */
+    const sgw_mlp* mlp;  /* the perceptron of SGW_PRECOND_LEARNED */
+    int plain_budget; /* SGW_PRECOND_LEARNED: the plain preconditioner's typical (median) H
+                         applications for systems of this size; the learned round stops at twice
+                         it and its unconverged pairs restart from their current x with the plain
+                         preconditioner (0 -> no such cap: only max_matvec) */
 } sgw_solve_opts;
 
 /* Per-pair outputs, each [nrhs][nomega] host arrays (any may be NULL). */
@@ -160,9 +195,11 @@ typedef struct {
     double* est_res;    /* recursive residual estimate |r| / |b| when the multishift pass stopped */
     double* rel_res;    /* true FP64 residual |b - A x| / |b| of the returned solution */
     double* cert;       /* error certificate |b - A x| / (eta |x|) >= |x - x*| / |x| */
-    int* status;        /* SGW_PAIR_*: CONVERGED iff rel_res <= tol */
+    int* status;        /* SGW_PAIR_*: CONVERGED iff rel_res <= tol and cert <= cert_tol */
     int* launches;      /* one int: library kernels launched by this call */
     double* kernel_ms;  /* one double: CUDA-event time of the multishift kernel launch on the stream */
+    int* fallbacks;     /* one int: pairs that restarted with the plain preconditioner after the
+                           learned round (SGW_PRECOND_LEARNED) */
 } sgw_report;
 
 /* Multishift solve (the hot path).  For every r < nrhs and j < nomega solves
@@ -183,8 +220,11 @@ typedef struct {
  *   tol    relative residual target (e.g. 1e-10).
  *   dpsi   complex [nrhs][nomega][n_pw] (host or device), overwritten.
  *   report optional per-pair report.
+ * A pair is converged when rel_res <= tol and cert <= opts.cert_tol (default 1e-8): the
+ * multishift pass keeps a shift going until its estimated certificate also holds, and the
+ * corrections of step 3 cover both targets.  With opts.x0 the pass is skipped (resume).
  * A zero right-hand side gives dpsi = 0 with status CONVERGED.  Returns SGW_ENOCONV if any
- * pair's true residual stays above tol (results and report are still written). */
+ * pair misses tol or the certificate (results and report are still written). */
 sgw_status sgw_solve_shifted(sgw_system* sys, int nrhs, const void* rhs, const double* e_ref,
                              int nomega, const double* omega, double eta, double tol,
                              const sgw_solve_opts* opts, void* dpsi, sgw_report* report);
@@ -328,7 +368,6 @@ enum { SGW_PRECOND_NONE = 0, SGW_PRECOND_PLAIN = 1, SGW_PRECOND_LEARNED = 2, SGW
  * packed w1[64][4], b1[64], w2[64][64], b2[64], w3[64], b3), evaluated with bfloat16 weights
  * and FP32 accumulation; trained with Adam (beta 0.9 / 0.999, eps 1e-8) on a mean squared
  * error.  Row arrays (feats [n][4], targets [n], weight [n], out [n]) are FP32 device buffers. */
-typedef struct sgw_mlp sgw_mlp;
 #define SGW_MLP_PARAMS 4545
 sgw_status sgw_mlp_create(const float* params /* host [4545] */, sgw_mlp** out);
 sgw_status sgw_mlp_get_params(const sgw_mlp* mlp, float* params /* host [4545] */);

@@ -11,7 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsgw.so")
-SOURCES = ["setup.cu", "kernels.cu", "api.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["setup.cu", "kernels.cu", "lanczos_f64.cu", "lanczos_df.cu", "lanczos_f32.cu", "api.cu", "noalloc.cu",
+           "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

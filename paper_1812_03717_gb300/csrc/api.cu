@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -21,8 +22,6 @@
 
 namespace sgw {
 const void* solve_kernel_ptr();
-const void* apply_kernel_ptr();
-const void* residual_kernel_ptr();
 }  // namespace sgw
 
 using namespace sgw;
@@ -45,7 +44,6 @@ struct sgw_system {
     // device
     int* d_miller = nullptr;
     double* d_kin = nullptr;
-    int* d_g2s = nullptr;
     int* d_stick_xy = nullptr;
     int* d_xbase = nullptr;
     double* d_vloc = nullptr;
@@ -58,9 +56,21 @@ struct sgw_system {
     float4* d_beta_dd = nullptr;
     float4* d_psi_dd = nullptr;
     int* d_lut = nullptr;
+    float* d_vloc_f = nullptr;   // FP32 mirrors of V_loc(r), T_G, beta_p(G), psi_v(G)
+    float* d_kin_f = nullptr;
+    float2* d_beta_f = nullptr;
+    float2* d_psi_f = nullptr;
+    // sticks in canonical order (first plane wave of each), their plane-wave counts and places
+    std::vector<int> stick_g0, stick_cnt, stick_xy, stick_of;   // stick_of: [npw]
+    // the two cluster splits of the box: [0] 16-byte complex policies, [1] FP32
+    int* d_g2s_s[2] = {nullptr, nullptr};
+    int* d_stick_loc[2] = {nullptr, nullptr};
+    int* d_part[2] = {nullptr, nullptr};
     void* d_ws = nullptr;        // solver workspace, grown on demand
     size_t ws_bytes = 0;
-    Plan plan;
+    Plan plan;                   // 16-byte policies (FP64, float-float)
+    Plan plan8;                  // FP32 policy
+    int forced_csize = 0;        // sgw_set_split: cluster size chosen by the caller (0: automatic)
 };
 
 namespace {
@@ -234,7 +244,6 @@ void free_system(sgw_system* s) {
     if (!s) return;
     cudaFree(s->d_miller);
     cudaFree(s->d_kin);
-    cudaFree(s->d_g2s);
     cudaFree(s->d_stick_xy);
     cudaFree(s->d_xbase);
     cudaFree(s->d_vloc);
@@ -247,6 +256,15 @@ void free_system(sgw_system* s) {
     cudaFree(s->d_beta_dd);
     cudaFree(s->d_psi_dd);
     cudaFree(s->d_lut);
+    cudaFree(s->d_vloc_f);
+    cudaFree(s->d_kin_f);
+    cudaFree(s->d_beta_f);
+    cudaFree(s->d_psi_f);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(s->d_g2s_s[i]);
+        cudaFree(s->d_stick_loc[i]);
+        cudaFree(s->d_part[i]);
+    }
     cudaFree(s->d_ws);
     delete s;
 }
@@ -266,6 +284,142 @@ int max_optin_smem() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return v;
+}
+
+// Shifts whose per-shift state every split reserves shared memory for; solves with more
+// shifts run only where the box leaves room for them.
+constexpr int kPlanShifts = 256;
+
+// A split of the sticks over csize ranks: rank r holds sticks [bs[r], bs[r+1]) and owns
+// plane waves [bg[r], bg[r+1]).
+struct Split {
+    int csize = 0;
+    int nstick_loc = 0;
+    std::vector<int> bs, bg;
+};
+
+// Contiguous stick ranges (canonical order) for C ranks that minimise the largest plane-wave
+// count of a rank while no rank holds more than `cap` sticks: binary search on that count,
+// greedy fill.  false when no such split exists.
+bool split_sticks(const std::vector<int>& cnt, int C, int cap, Split& out) {
+    const int N = (int)cnt.size();
+    if (cap < 1 || (long long)cap * C < N) return false;
+    long long tot = 0;
+    for (int c : cnt) tot += c;
+    std::vector<int> b;
+    auto fill = [&](long long T) -> bool {
+        b.assign(1, 0);
+        int j = 0;
+        for (int r = 0; r < C; ++r) {
+            long long g = 0;
+            int n = 0;
+            while (j < N && g + cnt[j] <= T && n < cap) {
+                g += cnt[j];
+                ++n;
+                ++j;
+            }
+            b.push_back(j);
+        }
+        return j == N;
+    };
+    if (!fill(tot)) return false;
+    long long lo = (tot + C - 1) / C, hi = tot;
+    while (lo < hi) {
+        const long long m = (lo + hi) / 2;
+        if (fill(m)) hi = m;
+        else lo = m + 1;
+    }
+    fill(lo);
+    out.csize = C;
+    out.bs = b;
+    out.nstick_loc = 0;
+    for (int r = 0; r < C; ++r) out.nstick_loc = std::max(out.nstick_loc, b[r + 1] - b[r]);
+    return true;
+}
+
+// The split of the box for es-byte complex values: the cluster size (1 .. kMaxCluster) whose
+// Lanczos kernel keeps the most SMs busy (resident clusters x size, as the occupancy
+// calculator reports for this GPU), the smaller size on ties; csize 0 when none fits.
+Split choose_split(const sgw_system* s, const Plan& base, int es) {
+    const int budget = max_optin_smem() - 1024;   // static shared memory of the kernels
+    Split best;
+    long long best_score = -1;
+    for (int C = 1; C <= kMaxCluster; ++C) {
+        if (s->forced_csize > 0 && C != s->forced_csize) continue;
+        Plan Q = base;
+        Q.csize = C;
+        Q.nstick_loc = 0;
+        Q.nplanes = 1;
+        const int fixed = apply_smem_layout(Q, es).end + lanczos_extra(kPlanShifts);
+        const int cap = (budget - fixed) / (Q.n3p * es);
+        Split sp;
+        if (!split_sticks(s->stick_cnt, C, cap, sp)) continue;
+        if (C == 1 || s->forced_csize > 0) return sp;   // one CTA per vector: no cluster overhead at all
+        Q.nstick_loc = sp.nstick_loc;
+        int owners = 0;
+        if (lanczos_capacity(Q, 128, 0, es == 8 ? SGW_PREC_FP32 : SGW_PREC_DF32, &owners) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const long long score = (long long)owners * C;
+        if (score > best_score) {
+            best_score = score;
+            best = sp;
+        }
+    }
+    return best;
+}
+
+// (Re)builds both splits of the box for the current occupied states and uploads their tables.
+sgw_status build_plans(sgw_system* s) {
+    const int npw = s->npw, n3 = s->dims[2], n3p = s->plan.n3p;
+    Plan* plans[2] = {&s->plan, &s->plan8};
+    for (int c = 0; c < 2; ++c) {
+        const int es = c == 0 ? 16 : 8;
+        const Split sp = choose_split(s, *plans[c], es);
+        plans[c]->csize = sp.csize;
+        cudaFree(s->d_g2s_s[c]);
+        cudaFree(s->d_stick_loc[c]);
+        cudaFree(s->d_part[c]);
+        s->d_g2s_s[c] = s->d_stick_loc[c] = s->d_part[c] = nullptr;
+        if (sp.csize == 0) {
+            if (c == 0) {
+                char buf[200];
+                std::snprintf(buf, sizeof buf,
+                              "the pruned FFT box (%d sticks x %d) does not fit the shared memory of a cluster of %d "
+                              "CTAs",
+                              s->nstick, n3, kMaxCluster);
+                return fail(SGW_EUNSUPPORTED, buf);
+            }
+            continue;   // FP32 solves of this system report SGW_EUNSUPPORTED
+        }
+        std::vector<int> g2s(npw), loc(s->nstick), part(2 * (kMaxCluster + 1), 0);
+        std::vector<int> owner(s->nstick);
+        for (int r = 0; r < sp.csize; ++r)
+            for (int st = sp.bs[r]; st < sp.bs[r + 1]; ++st) {
+                owner[st] = r;
+                loc[st] = (r << 16) | (st - sp.bs[r]);
+            }
+        for (int g = 0; g < npw; ++g) {
+            const int st = s->stick_of[g];
+            g2s[g] = (st - sp.bs[owner[st]]) * n3p + s->map[g] % n3;
+        }
+        for (int r = 0; r <= kMaxCluster; ++r) {
+            const int b = sp.bs[std::min(r, sp.csize)];
+            part[r] = b < s->nstick ? s->stick_g0[b] : npw;
+            part[kMaxCluster + 1 + r] = b;
+        }
+        sgw_status rs;
+        if ((rs = upload(&s->d_g2s_s[c], g2s.data(), g2s.size(), "upload g2s")) != SGW_OK ||
+            (rs = upload(&s->d_stick_loc[c], loc.data(), loc.size(), "upload stick owners")) != SGW_OK ||
+            (rs = upload(&s->d_part[c], part.data(), part.size(), "upload split")) != SGW_OK)
+            return rs;
+        plans[c]->g2s = s->d_g2s_s[c];
+        plans[c]->stick_loc = s->d_stick_loc[c];
+        plans[c]->part = s->d_part[c];
+        plans[c]->nstick_loc = sp.nstick_loc;
+    }
+    return SGW_OK;
 }
 
 }  // namespace
@@ -430,6 +584,8 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     if (e == cudaSuccess) e = cudaMemcpy(s->d_kin, d_kin, sizeof(double) * npw, cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_kin_dd, sizeof(float2) * npw);
     if (e == cudaSuccess) e = launch_to_dd(s->d_kin, npw, s->d_kin_dd, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_kin_f, sizeof(float) * npw);
+    if (e == cudaSuccess) e = launch_to_f32(s->d_kin, npw, s->d_kin_f, 0);
     cleanup_tmp();
     if (e != cudaSuccess) {
         free_system(s);
@@ -449,27 +605,28 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
         }
     }
     const int n1 = fft_dims[0], n2 = fft_dims[1], n3 = fft_dims[2];
-    std::map<int, int> stick_of;   // xy -> stick id (sorted by xy)
+    // sticks (z-columns holding plane waves) in canonical order: the plane waves of one stick,
+    // fixed (m1, m2), are consecutive in the Miller-lexicographic order, so each stick is a
+    // range [stick_g0, stick_g0 + stick_cnt) of the coefficient arrays
+    const int n2p = n2 | 1;   // odd row stride: strided (x-direction) FFT lines spread over all banks
     std::vector<int> xs_used(n1, 0);
+    s->stick_of.resize(npw);
     for (int g = 0; g < npw; ++g) {
         const int xy = s->map[g] / n3;
-        stick_of.emplace(xy, 0);
+        if (g == 0 || xy != s->map[g - 1] / n3) {
+            s->stick_g0.push_back(g);
+            s->stick_cnt.push_back(0);
+            s->stick_xy.push_back((xy / n2) * n2p + xy % n2);
+        }
+        ++s->stick_cnt.back();
+        s->stick_of[g] = (int)s->stick_g0.size() - 1;
         xs_used[xy / n2] = 1;
     }
-    std::vector<int> stick_xy;
-    for (auto& kv : stick_of) {
-        kv.second = (int)stick_xy.size();
-        stick_xy.push_back(kv.first);
-    }
     const int n3p = n3 | 1;   // odd stick stride
-    std::vector<int> g2s(npw);
-    for (int g = 0; g < npw; ++g) g2s[g] = stick_of[s->map[g] / n3] * n3p + s->map[g] % n3;
-    const int n2p = n2 | 1;   // odd row stride: strided (x-direction) FFT lines spread over all banks
-    for (auto& xy : stick_xy) xy = (xy / n2) * n2p + xy % n2;
     std::vector<int> xbase;
     for (int x = 0; x < n1; ++x)
         if (xs_used[x]) xbase.push_back(x * n2p);
-    s->nstick = (int)stick_xy.size();
+    s->nstick = (int)s->stick_xy.size();
     s->nxcol = (int)xbase.size();
     // potential, one contiguous (padded) plane per z: [z][x][y < n2p], every axis in the
     // order in which the inverse FFTs leave real space
@@ -481,17 +638,19 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
             for (int pz = 0; pz < n3; ++pz)
                 vz[((size_t)pz * n1 + px) * n2p + py] = vloc_r[((size_t)ox[px] * n2 + oy[py]) * n3 + oz[pz]];
     std::vector<float2> vzdd(nboxp);
+    std::vector<float> vzf(nboxp);
     for (size_t i = 0; i < nboxp; ++i) {
         const float h = (float)vz[i];
         vzdd[i] = make_float2(h, (float)(vz[i] - (double)h));
+        vzf[i] = h;
     }
     sgw_status rs;
-    if ((rs = upload(&s->d_vloc_dd, vzdd.data(), vzdd.size(), "upload V_loc")) != SGW_OK) {
+    if ((rs = upload(&s->d_vloc_dd, vzdd.data(), vzdd.size(), "upload V_loc")) != SGW_OK ||
+        (rs = upload(&s->d_vloc_f, vzf.data(), vzf.size(), "upload V_loc")) != SGW_OK) {
         free_system(s);
         return rs;
     }
-    if ((rs = upload(&s->d_g2s, g2s.data(), g2s.size(), "upload g2s")) != SGW_OK ||
-        (rs = upload(&s->d_stick_xy, stick_xy.data(), stick_xy.size(), "upload sticks")) != SGW_OK ||
+    if ((rs = upload(&s->d_stick_xy, s->stick_xy.data(), s->stick_xy.size(), "upload sticks")) != SGW_OK ||
         (rs = upload(&s->d_xbase, xbase.data(), xbase.size(), "upload xbase")) != SGW_OK ||
         (rs = upload(&s->d_vloc, vz.data(), vz.size(), "upload V_loc")) != SGW_OK) {
         free_system(s);
@@ -522,6 +681,10 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
         if (e == cudaSuccess)
             e = launch_to_dd(reinterpret_cast<const double*>(s->d_beta), 2 * (size_t)nproj * npw,
                              reinterpret_cast<float2*>(s->d_beta_dd), 0);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_beta_f, sizeof(float2) * (size_t)nproj * npw);
+        if (e == cudaSuccess)
+            e = launch_to_f32(reinterpret_cast<const double*>(s->d_beta), 2 * (size_t)nproj * npw,
+                              reinterpret_cast<float*>(s->d_beta_f), 0);
         if (e != cudaSuccess) {
             free_system(s);
             return cuda_fail(e, "projector kernel");
@@ -566,7 +729,7 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     P.npw = npw;
     P.nstick = s->nstick;
     P.nxcol = s->nxcol;
-    P.g2s = s->d_g2s;
+    P.g2s = nullptr;   // per split (build_plans)
     P.stick_xy = s->d_stick_xy;
     P.xbase = s->d_xbase;
     P.vloc = s->d_vloc;
@@ -582,14 +745,18 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
     P.psi = nullptr;
     P.psi_dd = nullptr;
     P.inv_nbox = 1.0 / (double)nbox;
-    if (apply_smem_bytes(P) > max_optin_smem()) {
-        char buf[200];
-        std::snprintf(buf, sizeof buf,
-                      "the pruned FFT box (%d sticks x %d) needs %d B of shared memory per CTA, more than the %d B "
-                      "this build keeps on chip",
-                      s->nstick, n3, apply_smem_bytes(P), max_optin_smem());
+    P.vloc_f = s->d_vloc_f;
+    P.kin_f = s->d_kin_f;
+    P.beta_f = s->d_beta_f;
+    P.psi_f = nullptr;
+    P.csize = 1;
+    P.nstick_loc = s->nstick;
+    P.part = nullptr;
+    P.stick_loc = nullptr;
+    s->plan8 = P;
+    if ((rs = build_plans(s)) != SGW_OK) {
         free_system(s);
-        return fail(SGW_EUNSUPPORTED, buf);
+        return rs;
     }
     SGW_CUDA(cudaDeviceSynchronize(), "create_system");
     *out = s;
@@ -607,6 +774,36 @@ sgw_status sgw_get_gvectors(const sgw_system* s, int* n_pw, int* miller, double*
 sgw_status sgw_get_box_map(const sgw_system* s, int* map) {
     if (!s || !map) return fail(SGW_EINVAL, "NULL argument");
     std::memcpy(map, s->map.data(), sizeof(int) * s->npw);
+    return SGW_OK;
+}
+
+sgw_status sgw_set_split(sgw_system* s, int csize) {
+    g_err.clear();
+    if (!s) return fail(SGW_EINVAL, "NULL system");
+    if (csize < 0 || csize > kMaxCluster) return fail(SGW_EINVAL, "csize must be in [0, 16]");
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    SGW_CUDA(cudaDeviceSynchronize(), "set_split");   // the tables may be in use by queued work
+    const int prev = s->forced_csize;
+    s->forced_csize = csize;
+    sgw_status r = build_plans(s);
+    if (r != SGW_OK) {
+        const std::string msg = g_err;
+        s->forced_csize = prev;
+        build_plans(s);
+        return fail(r, msg);
+    }
+    if (csize > 0 && s->plan.csize != csize) {
+        s->forced_csize = prev;
+        build_plans(s);
+        return fail(SGW_EUNSUPPORTED, "the box does not split over that many CTAs");
+    }
+    return SGW_OK;
+}
+
+sgw_status sgw_get_split(const sgw_system* s, int* csize, int* csize_fp32) {
+    if (!s) return fail(SGW_EINVAL, "NULL system");
+    if (csize) *csize = s->plan.csize;
+    if (csize_fp32) *csize_fp32 = s->plan8.csize;
     return SGW_OK;
 }
 
@@ -653,29 +850,40 @@ sgw_status sgw_set_occupied(sgw_system* s, int n_occ, const void* psi_v, const d
         }
     }
     float4* d_new_dd = nullptr;
+    float2* d_new_f = nullptr;
     if (n_occ > 0) {
         cudaError_t e = cudaMalloc(&d_new_dd, sizeof(float4) * (size_t)n_occ * s->npw);
         if (e == cudaSuccess)
             e = launch_to_dd(reinterpret_cast<const double*>(d_new), 2 * (size_t)n_occ * s->npw,
                              reinterpret_cast<float2*>(d_new_dd), 0);
+        if (e == cudaSuccess) e = cudaMalloc(&d_new_f, sizeof(float2) * (size_t)n_occ * s->npw);
+        if (e == cudaSuccess)
+            e = launch_to_f32(reinterpret_cast<const double*>(d_new), 2 * (size_t)n_occ * s->npw,
+                              reinterpret_cast<float*>(d_new_f), 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) {
             cudaFree(d_new);
             cudaFree(d_new_dd);
+            cudaFree(d_new_f);
             return cuda_fail(e, "psi_v float-float copy");
         }
     }
     cudaFree(s->d_psi);
     cudaFree(s->d_psi_dd);
+    cudaFree(s->d_psi_f);
     s->d_psi = d_new;
     s->d_psi_dd = d_new_dd;
+    s->d_psi_f = d_new_f;
     s->nocc = n_occ;
     s->eps.assign(eps_v, eps_v + n_occ);
-    s->plan.nocc = n_occ;
-    s->plan.psi = d_new;
-    s->plan.psi_dd = d_new_dd;
-    if (apply_smem_bytes(s->plan) > max_optin_smem()) return fail(SGW_EUNSUPPORTED, "too many occupied states");
-    return SGW_OK;
+    for (Plan* p : {&s->plan, &s->plan8}) {
+        p->nocc = n_occ;
+        p->psi = d_new;
+        p->psi_dd = d_new_dd;
+        p->psi_f = d_new_f;
+    }
+    // the coefficient slots grow with n_occ: the split of the box is chosen again
+    return build_plans(s);
 }
 
 sgw_status sgw_make_rhs(const sgw_system* kq, const sgw_system* k, int n_v, const void* psi_k, int n_pert,
@@ -726,17 +934,20 @@ static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const dou
     sgw_status r;
     if ((r = stage_in(x, vb, in, st, "x")) != SGW_OK) return r;
     if ((r = stage_out(y, vb, out, "y", st)) != SGW_OK) return r;
-    int grid = 0;
-    SGW_CUDA(resident_grid(apply_kernel_ptr(), apply_smem_bytes(s->plan), &grid), "apply occupancy");
-    grid = std::min(grid, nvec);
-    const size_t scratch = 3 * sizeof(double2) * (size_t)grid * s->npw;
+    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32 && precision != SGW_PREC_FP32)
+        return fail(SGW_EINVAL, "unknown precision");
+    const Plan& plan = precision == SGW_PREC_FP32 ? s->plan8 : s->plan;
+    if (plan.csize == 0) return fail(SGW_EUNSUPPORTED, "the FFT box does not fit on chip in this precision");
+    int owners = 0;
+    SGW_CUDA(apply_owners(plan, precision, &owners), "apply occupancy");
+    owners = std::min(owners, nvec);
+    const size_t scratch = 2 * sizeof(double2) * (size_t)owners * s->npw;
     const size_t zb = project ? sizeof(double2) * nvec : 0;
     if ((r = ensure_ws(s, scratch + zb + 256)) != SGW_OK) return r;
     double2* d_scr = (double2*)s->d_ws;
     double2* d_z = (double2*)((char*)s->d_ws + ((scratch + 255) / 256) * 256);
     if (project) SGW_CUDA(cudaMemcpyAsync(d_z, z, zb, cudaMemcpyHostToDevice, st), "z copy");
-    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32) return fail(SGW_EINVAL, "unknown precision");
-    SGW_CUDA(launch_apply(s->plan, nvec, (const double2*)in.dev, (double2*)out.dev, d_z, project, d_scr, grid,
+    SGW_CUDA(launch_apply(plan, nvec, (const double2*)in.dev, (double2*)out.dev, d_z, project, d_scr, owners,
                           precision, st),
              "apply kernel");
     if ((r = finish_out(out, st, "y copy")) != SGW_OK) return r;
@@ -769,19 +980,33 @@ struct Carve {
 
 // The multishift solve of every (rhs, shift) pair with its FP64 true-residual check and
 // per-shift corrections: z_rj = e_ref[r] + omega[j] + i Im z_j, Im z_j = eta_s[j] when
-// eta_s (host) is given, else eta.  rhs_d and X are device buffers; plan fixes the operator
-// (P_c H P_c with the occupied states of the plan; H itself when it has none).  Returns
-// SGW_ENOCONV, with X and the report written, when a pair misses tol.
-static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const double2* rhs_d, const double* e_ref,
+// eta_s (host) is given, else eta.  rhs_d and X are device buffers; `project` selects the
+// operator (P_c H P_c with the system's occupied states, else H itself).  A pair is
+// converged when rel_res <= tol and its certificate <= cert_tol.  Returns SGW_ENOCONV, with X
+// and the report written, when a pair misses either.
+static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double2* rhs_d, const double* e_ref,
                              int nomega, const double* omega, const double* eta_s, double eta, double tol,
                              const sgw_solve_opts* opts, double2* X, sgw_report* report, cudaStream_t st) {
     const int method = opts ? opts->method : SGW_METHOD_LANCZOS;
     const int precision = opts ? opts->precision : SGW_PREC_FP64;
     const int threads = opts ? opts->threads : 0;
-    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32) return fail(SGW_EINVAL, "unknown precision");
+    const int precond = opts ? opts->precond : SGW_PRECOND_NONE;
+    const sgw_mlp* mlp = opts ? opts->mlp : nullptr;
+    const double cert_tol = !opts || opts->cert_tol == 0.0 ? 1e-8 : opts->cert_tol;   // < 0: not checked
+    const bool use_cert = cert_tol > 0.0;
+    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32 && precision != SGW_PREC_FP32)
+        return fail(SGW_EINVAL, "unknown precision");
     if (method != SGW_METHOD_LANCZOS && method != SGW_METHOD_BICGSTAB) return fail(SGW_EINVAL, "unknown method");
+    if (precision == SGW_PREC_FP32 && method != SGW_METHOD_LANCZOS)
+        return fail(SGW_EUNSUPPORTED, "the FP32 inner solve is the Lanczos method");
     if (eta_s && method != SGW_METHOD_LANCZOS)
         return fail(SGW_EUNSUPPORTED, "shifts with different imaginary parts need the Lanczos method");
+    if (precond != SGW_PRECOND_NONE && precond != SGW_PRECOND_PLAIN && precond != SGW_PRECOND_LEARNED)
+        return fail(SGW_EINVAL, "precond must be SGW_PRECOND_NONE, _PLAIN or _LEARNED");
+    if (precond == SGW_PRECOND_LEARNED && !mlp) return fail(SGW_EINVAL, "the learned preconditioner needs opts.mlp");
+    if (precond != SGW_PRECOND_NONE && !project)
+        return fail(SGW_EUNSUPPORTED, "preconditioned corrections solve the projected Sternheimer operator only");
+    if (!std::isfinite(cert_tol)) return fail(SGW_EINVAL, "non-finite cert_tol");
     const int ell = opts && opts->ell ? opts->ell : 4;
     if (ell < 1 || ell > kMaxEll) return fail(SGW_EINVAL, "ell must be 1, 2, 3 or 4");
     int seed = opts ? opts->seed_index : -1;
@@ -792,43 +1017,75 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
     }
     if (seed >= nomega) return fail(SGW_EINVAL, "seed_index out of range");
     const bool lanczos = method == SGW_METHOD_LANCZOS;
+    const bool have_x0 = opts && opts->x0;
+    // plans: the pass in its precision; the FP64 check and the corrections in the 16-byte split
+    // (corrections of an FP32 pass run in float-float: FP64 iterative refinement)
+    Plan plan = precision == SGW_PREC_FP32 ? s->plan8 : s->plan;
+    Plan plan16 = s->plan;
+    if (plan.csize == 0) return fail(SGW_EUNSUPPORTED, "the FFT box does not fit on chip in FP32");
+    if (!project) {
+        for (Plan* p : {&plan, &plan16}) {
+            p->nocc = 0;
+            p->psi = nullptr;
+            p->psi_dd = nullptr;
+            p->psi_f = nullptr;
+        }
+    }
+    const int res_prec = precision == SGW_PREC_FP64 ? SGW_PREC_FP64 : SGW_PREC_DF32;
+    const int corr_prec = precision == SGW_PREC_FP32 ? SGW_PREC_DF32 : precision;
+    if (precond != SGW_PRECOND_NONE && plan16.csize > 1)
+        return fail(SGW_EUNSUPPORTED, "preconditioned corrections need a box that fits one CTA");
     // Lanczos keeps its basis: the default budget of 4096 steps bounds its memory
     const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : (lanczos ? 4096 : 40000);
     const int max_refine = !opts || opts->max_refine == 0 ? 3 : std::max(0, opts->max_refine);
-    const int smem_main = lanczos ? lanczos_smem_bytes(plan, nomega) : solve_smem_bytes(plan, nomega);
-    if (smem_main > max_optin_smem()) return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
+    const int plain_budget = opts && opts->plain_budget > 0 ? opts->plain_budget : 0;
+    if (lanczos && !have_x0 && lanczos_smem_bytes(plan, nomega, precision) > max_optin_smem())
+        return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
+    if (!lanczos && solve_smem_bytes(plan, nomega) > max_optin_smem())
+        return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     const size_t np = (size_t)nrhs * nomega;
+    if (np > (size_t)INT_MAX) return fail(SGW_EUNSUPPORTED, "nrhs * nomega above INT_MAX");
     sgw_status r;
     const int chunk = (int)std::min<size_t>(np, 4096);
-    int grid = 0, grid1 = 0, grid_r = 0;
+    int own = 0, own1 = 0, own_r = 0, grid_b = 0;
     if (lanczos) {
-        SGW_CUDA(lanczos_grid(plan, nomega, nrhs, threads, &grid), "solver occupancy");
-        SGW_CUDA(lanczos_grid(plan, 1, chunk, threads, &grid1), "solver occupancy");
+        SGW_CUDA(lanczos_capacity(plan, nomega, threads, precision, &own), "solver occupancy");
+        own = std::min(own, nrhs);
     } else {
-        SGW_CUDA(solve_grid(plan, nomega, nrhs, &grid), "solver occupancy");
-        SGW_CUDA(solve_grid(plan, 1, chunk, &grid1), "solver occupancy");
+        SGW_CUDA(solve_grid(plan, nomega, nrhs, &own), "solver occupancy");
     }
-    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(plan), &grid_r, kResThreads), "residual occupancy");
-    grid_r = (int)std::min<size_t>(grid_r, np);
-    // Krylov workspace of one launch (reused by the correction solves)
+    SGW_CUDA(lanczos_capacity(plan16, 1, threads, corr_prec, &own1), "solver occupancy");
+    own1 = std::min(own1, chunk);
+    if (precond != SGW_PRECOND_NONE) SGW_CUDA(solve_grid(plan16, 1, chunk, &grid_b), "solver occupancy");
+    SGW_CUDA(residual_owners(plan16, res_prec, &own_r), "residual occupancy");
+    own_r = (int)std::min<size_t>(own_r, np);
+    // Krylov workspace of one launch (reused by the correction solves); the basis per owner
     int maxk = max_mv;
-    auto solver_bytes = [&](int g, int ns, int mk) -> size_t {
-        if (lanczos)
-            return (size_t)g * ((size_t)(mk + 1) * vb + 2 * (size_t)(mk + 1) * 8 + 2 * (size_t)mk * ns * 16) + 4096;
-        return (size_t)g * (vb * (2 * ell + 3) + vb * (size_t)ns) + 4096;
+    const size_t eb = (size_t)prec_bytes(precision) * s->npw;   // basis vector of the pass
+    auto lanczos_bytes = [&](int owners, int ctas, int ns, int mk, size_t vbytes) -> size_t {
+        return (size_t)owners * (size_t)(mk + 1) * vbytes +
+               (size_t)ctas * (2 * (size_t)(mk + 1) * 8 + 2 * (size_t)mk * ns * 16) + 4096;
     };
     if (lanczos) {
         size_t free_b = 0, total_b = 0;
         SGW_CUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-        const size_t budget = std::min<size_t>(free_b / 2, (size_t)64 << 30);
-        const size_t per_k = std::max<size_t>((size_t)grid * (vb + 16 + 32 * (size_t)nomega),
-                                              (size_t)grid1 * (vb + 16 + 32));
+        const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+        const size_t per_k = std::max<size_t>((size_t)own * (eb + 16 * plan.csize) + (size_t)own * plan.csize * 32 *
+                                                  (size_t)nomega,
+                                              (size_t)own1 * (vb + 16 * plan16.csize + 32 * plan16.csize));
         const size_t cap = budget / std::max<size_t>(per_k, 1);
         if (cap < 8) return fail(SGW_ENOMEM, "not enough device memory for a Lanczos basis");
         maxk = (int)std::min<size_t>((size_t)max_mv, cap - 2);
     }
-    const size_t wsb = std::max(solver_bytes(grid, nomega, maxk), solver_bytes(grid1, 1, maxk));
+    size_t wsb;
+    if (lanczos)
+        wsb = std::max(have_x0 ? 0 : lanczos_bytes(own, own * plan.csize, nomega, maxk, eb),
+                       lanczos_bytes(own1, own1 * plan16.csize, 1, maxk, vb));
+    else
+        wsb = (size_t)own * (vb * (2 * ell + 3) + vb * (size_t)nomega) + 4096;
+    if (precond != SGW_PRECOND_NONE)
+        wsb = std::max(wsb, (size_t)grid_b * vb * (2 * ell + 6) + 4096);   // BiCGstab seeds, directions, scratch
     Carve c;
     const size_t o_solver = c.take(wsb);
     const size_t o_eref = c.take(sizeof(double) * nrhs);
@@ -838,9 +1095,9 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
     const size_t o_mv = c.take(sizeof(int) * np);
     const size_t o_est = c.take(sizeof(double) * np);
     const size_t o_st = c.take(sizeof(int) * np);
-    const size_t o_rscr = c.take(2 * vb * grid_r);
+    const size_t o_rscr = c.take(2 * vb * own_r);
     const size_t o_rel = c.take(sizeof(double) * np);
-    const size_t o_bvec = c.take(vb * nrhs);
+    const size_t o_bvec = project ? c.take(vb * nrhs) : 0;
     const size_t o_cert = c.take(sizeof(double) * np);
     const size_t o_list = c.take(sizeof(int) * chunk);
     const size_t o_rvec = c.take(vb * chunk);
@@ -852,6 +1109,9 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
     const size_t o_mv1 = c.take(sizeof(int) * chunk);
     const size_t o_est1 = c.take(sizeof(double) * chunk);
     const size_t o_st1 = c.take(sizeof(int) * chunk);
+    const size_t o_pe = precond != SGW_PRECOND_NONE ? c.take(sizeof(double) * chunk) : 0;
+    const size_t o_po = precond != SGW_PRECOND_NONE ? c.take(sizeof(double) * chunk) : 0;
+    const size_t o_pre = precond != SGW_PRECOND_NONE ? c.take(sizeof(double) * s->npw * (size_t)chunk) : 0;
     if ((r = ensure_ws(s, c.off)) != SGW_OK) return r;
     char* w = (char*)s->d_ws;
     std::vector<double> sig(nomega);
@@ -866,90 +1126,105 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
         d_etas = (const double*)(w + o_etas);
     }
 
-    // One multishift launch of the selected method: z_rj = e_ref_d[r] + omega_d[j] + i Im z, with
-    // Im z = eta_r_d[r], else eta_s_d[j], else eta.
-    auto run = [&](bool corr, int nr, int ns, const double2* rhs_d, const double* e_ref_d, const double* omega_d,
-                   double omega_seed, const double* sig_d, double tl, double2* x_d, int* mv_d, double* est_d,
-                   int* st_d, int g, const double* eta_s_d, const double* eta_r_d) -> cudaError_t {
-        if (lanczos) {
-            LanczosArgs L;
-            L.nrhs = nr;
-            L.nshift = ns;
-            L.maxk = maxk;
-            L.rhs = rhs_d;
-            L.e_ref = e_ref_d;
-            L.omega = omega_d;
-            L.eta = eta;
-            L.tol = tl;
-            L.x = x_d;
-            char* base = w + o_solver;
-            L.basis = (double2*)base;
-            L.ab = (double*)(base + (size_t)g * (maxk + 1) * vb);
-            L.ysc = (double2*)(base + (size_t)g * ((maxk + 1) * vb + 2 * (size_t)(maxk + 1) * 8));
-            L.counter = (int*)(w + o_cnt);
-            L.out_mv = mv_d;
-            L.out_res = est_d;
-            L.out_status = st_d;
-            L.eta_s = eta_s_d;
-            L.eta_r = eta_r_d;
-            // correction solves only need a fraction of a digit (their target is about
-            // 0.3 tol / |r|); they run in the pass's precision and the FP64 check re-judges
-            return launch_lanczos(plan, L, g, precision, threads, st);
-        }
-        SolveArgs A;
-        A.nrhs = nr;
-        A.nshift = ns;
-        A.ell = ell;
-        A.max_mv = max_mv;
-        A.rhs = rhs_d;
-        A.e_ref = e_ref_d;
-        A.sig = sig_d;
-        A.omega_seed = omega_seed;
-        A.eta = eta;
-        A.tol = tl;
-        A.x = x_d;
-        A.seedw = (double2*)(w + o_solver);
-        A.uw = (double2*)(w + o_solver + (size_t)g * vb * (2 * ell + 3));
-        A.counter = (int*)(w + o_cnt);
-        A.out_mv = mv_d;
-        A.out_res = est_d;
-        A.out_status = st_d;
-        return launch_solve(plan, A, g, st);
+    // One Lanczos launch: z_rj = e_ref_d[r] + omega_d[j] + i Im z, with Im z = eta_r_d[r], else
+    // eta_s_d[j], else eta.
+    auto run_lanczos = [&](const Plan& pl, int prec, int nr, int ns, const double2* rhs_d, const double* e_ref_d,
+                           const double* omega_d, double tl, double ctl, double2* x_d, int* mv_d, double* est_d,
+                           int* st_d, int owners, const double* eta_s_d, const double* eta_r_d) -> cudaError_t {
+        LanczosArgs L;
+        L.nrhs = nr;
+        L.nshift = ns;
+        L.maxk = maxk;
+        L.rhs = rhs_d;
+        L.e_ref = e_ref_d;
+        L.omega = omega_d;
+        L.eta = eta;
+        L.tol = tl;
+        L.cert_tol = ctl;
+        L.x = x_d;
+        char* base = w + o_solver;
+        const size_t vbytes = (size_t)prec_bytes(prec) * s->npw;
+        L.basis = (double2*)base;
+        L.ab = (double*)(base + (size_t)owners * (maxk + 1) * vbytes);
+        L.ysc = (double2*)(base + (size_t)owners * (maxk + 1) * vbytes +
+                           (size_t)owners * pl.csize * 2 * (size_t)(maxk + 1) * 8);
+        L.counter = (int*)(w + o_cnt);
+        L.out_mv = mv_d;
+        L.out_res = est_d;
+        L.out_status = st_d;
+        L.eta_s = eta_s_d;
+        L.eta_r = eta_r_d;
+        return launch_lanczos(pl, L, owners, prec, threads, st);
     };
 
-    // 1. multishift pass
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool timed = report && report->kernel_ms;
+    int launches = 0;
     if (timed) {
         SGW_CUDA(cudaEventCreate(&ev0), "event");
         SGW_CUDA(cudaEventCreate(&ev1), "event");
         SGW_CUDA(cudaEventRecord(ev0, st), "event");
     }
-    SGW_CUDA(run(false, nrhs, nomega, rhs_d, (const double*)(w + o_eref), (const double*)(w + o_om), omega[seed],
-                 (const double*)(w + o_sig), tol, X, (int*)(w + o_mv), (double*)(w + o_est), (int*)(w + o_st), grid,
-                 d_etas, nullptr),
-             "solver kernel");
-    int launches = 1;
+    if (have_x0) {
+        // 1'. resume from the caller's solutions: every pair goes straight to the check
+        SGW_CUDA(cudaMemcpyAsync(X, opts->x0, vb * np, cudaMemcpyDefault, st), "x0 copy");
+        SGW_CUDA(cudaMemsetAsync(w + o_mv, 0, sizeof(int) * np, st), "memset");
+        SGW_CUDA(cudaMemsetAsync(w + o_st, 0, sizeof(int) * np, st), "memset");
+        SGW_CUDA(cudaMemsetAsync(w + o_est, 0, sizeof(double) * np, st), "memset");
+    } else if (lanczos) {
+        // 1. multishift pass
+        SGW_CUDA(run_lanczos(plan, precision, nrhs, nomega, rhs_d, (const double*)(w + o_eref),
+                             (const double*)(w + o_om), tol, use_cert ? cert_tol : 0.0, X, (int*)(w + o_mv),
+                             (double*)(w + o_est), (int*)(w + o_st), own, d_etas, nullptr),
+                 "solver kernel");
+        ++launches;
+    } else {
+        SolveArgs A;
+        A.nrhs = nrhs;
+        A.nshift = nomega;
+        A.ell = ell;
+        A.max_mv = max_mv;
+        A.rhs = rhs_d;
+        A.e_ref = (const double*)(w + o_eref);
+        A.sig = (const double*)(w + o_sig);
+        A.omega_seed = omega[seed];
+        A.eta = eta;
+        A.tol = tol;
+        A.x = X;
+        A.seedw = (double2*)(w + o_solver);
+        A.uw = (double2*)(w + o_solver + (size_t)own * vb * (2 * ell + 3));
+        A.counter = (int*)(w + o_cnt);
+        A.out_mv = (int*)(w + o_mv);
+        A.out_res = (double*)(w + o_est);
+        A.out_status = (int*)(w + o_st);
+        SGW_CUDA(launch_solve(plan, A, own, st), "solver kernel");
+        ++launches;
+    }
     if (timed) SGW_CUDA(cudaEventRecord(ev1, st), "event");
 
-    // 2. true residual of every pair
+    // 2. true residual of every pair (H in FP64 for the FP64 mode, else in float-float; the
+    //    assembly and the norms in FP64)
     double* d_rel = (double*)(w + o_rel);
     double* d_cert = (double*)(w + o_cert);
     const double* d_eref = (const double*)(w + o_eref);
     const double* d_om = (const double*)(w + o_om);
     // b = -P_c rhs once per right-hand side, shared by every residual check of its shifts
-    const double2* d_b = (const double2*)(w + o_bvec);
-    SGW_CUDA(launch_project_rhs(plan, nrhs, rhs_d, (double2*)(w + o_bvec), st), "projection kernel");
-    SGW_CUDA(launch_residual(plan, nrhs, nomega, nullptr, 0, rhs_d, d_eref, d_om, eta, X,
-                             (double2*)(w + o_rscr), d_rel, d_cert, nullptr, grid_r, st, d_etas, d_b),
+    const double2* d_b = project ? (const double2*)(w + o_bvec) : nullptr;
+    if (project) {
+        SGW_CUDA(launch_project_rhs(plan16, nrhs, rhs_d, (double2*)(w + o_bvec), st), "projection kernel");
+        ++launches;
+    }
+    SGW_CUDA(launch_residual(plan16, nrhs, nomega, nullptr, 0, rhs_d, d_eref, d_om, eta, X, (double2*)(w + o_rscr),
+                             d_rel, d_cert, nullptr, own_r, st, d_etas, d_b, res_prec),
              "residual kernel");
-    launches += 2;
+    ++launches;
     std::vector<int> stv(np), mvv(np);
     std::vector<double> estv(np), relv(np), certv(np);
     SGW_CUDA(cudaMemcpyAsync(stv.data(), w + o_st, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
     SGW_CUDA(cudaMemcpyAsync(mvv.data(), w + o_mv, sizeof(int) * np, cudaMemcpyDeviceToHost, st), "report");
     SGW_CUDA(cudaMemcpyAsync(estv.data(), w + o_est, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
     SGW_CUDA(cudaMemcpyAsync(relv.data(), d_rel, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
+    SGW_CUDA(cudaMemcpyAsync(certv.data(), d_cert, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
     SGW_CUDA(cudaStreamSynchronize(st), "solve");
     if (timed) {
         float ms = 0.f;
@@ -958,23 +1233,38 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
     }
+    auto needs = [&](size_t q) {
+        return std::isfinite(relv[q]) && stv[q] != SGW_PAIR_NONFINITE &&
+               (relv[q] > tol || (use_cert && certv[q] > cert_tol));
+    };
 
-    // 3. per-shift correction solves for pairs above tol: A_j d = r_j, x_j += d
+    // 3. per-shift correction solves for pairs above tol or the certificate target:
+    //    A_j d = r_j, x_j += d (Lanczos in the correction precision, or preconditioned BiCGstab)
     std::vector<int> list, mv1(chunk);
-    std::vector<double> eref1(chunk), eta1(chunk);
-    for (int round = 0; round < max_refine; ++round) {
+    std::vector<double> eref1(chunk), eta1(chunk), pe(chunk), po(chunk);
+    int fallbacks = 0;
+    const int rounds = have_x0 ? std::max(max_refine, 1) : max_refine;
+    for (int round = 0; round < rounds; ++round) {
         list.clear();
         for (size_t q = 0; q < np; ++q)
-            if (std::isfinite(relv[q]) && relv[q] > tol && stv[q] != SGW_PAIR_NONFINITE) list.push_back((int)q);
+            if (needs(q)) list.push_back((int)q);
         if (list.empty()) break;
+        // the learned diagonal drives the first preconditioned round (budget 2x the plain one when
+        // given); the pairs it leaves unconverged restart from their current x with the plain one
+        const int pc = precond == SGW_PRECOND_LEARNED && round > 0 ? SGW_PRECOND_PLAIN : precond;
+        if (precond == SGW_PRECOND_LEARNED && round == 1) fallbacks += (int)list.size();
         for (size_t c0 = 0; c0 < list.size(); c0 += chunk) {
             const int nc = (int)std::min<size_t>(chunk, list.size() - c0);
-            double worst = 0.0;
+            double need = 1.0;   // the smallest factor by which a pair's residual must drop
             for (int i = 0; i < nc; ++i) {
                 const int q = list[c0 + i];
                 eref1[i] = e_ref[q / nomega] + omega[q % nomega];
                 eta1[i] = eta_s ? eta_s[q % nomega] : eta;
-                worst = std::max(worst, relv[q]);
+                pe[i] = e_ref[q / nomega];
+                po[i] = omega[q % nomega];
+                double f = tol / relv[q];
+                if (use_cert && certv[q] > 0.0) f = std::min(f, cert_tol / certv[q]);
+                need = std::min(need, f);
             }
             SGW_CUDA(cudaMemcpyAsync(w + o_list, list.data() + c0, sizeof(int) * nc, cudaMemcpyHostToDevice, st),
                      "list copy");
@@ -983,20 +1273,64 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
             SGW_CUDA(cudaMemcpyAsync(w + o_eta1, eta1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st),
                      "list copy");
             const int* d_list = (const int*)(w + o_list);
-            SGW_CUDA(launch_residual(plan, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
+            SGW_CUDA(launch_residual(plan16, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
                                      (double2*)(w + o_rscr), d_rel, d_cert, (double2*)(w + o_rvec),
-                                     std::min(grid_r, nc), st, d_etas, d_b),
+                                     std::min(own_r, nc), st, d_etas, d_b, res_prec),
                      "residual kernel");
-            const double tl = std::min(0.5, std::max(1e-13, 0.3 * tol / worst));
-            SGW_CUDA(run(true, nc, 1, (const double2*)(w + o_rvec), (const double*)(w + o_eref1), (const double*)(w + o_zero),
-                         0.0, (const double*)(w + o_zero), tl, (double2*)(w + o_dbuf), (int*)(w + o_mv1),
-                         (double*)(w + o_est1), (int*)(w + o_st1), std::min(grid1, nc), nullptr,
-                         (const double*)(w + o_eta1)),
-                     "correction solve");
+            const double tl = std::min(0.5, std::max(1e-13, 0.3 * need));
+            if (pc == SGW_PRECOND_NONE) {
+                SGW_CUDA(run_lanczos(plan16, corr_prec, nc, 1, (const double2*)(w + o_rvec),
+                                     (const double*)(w + o_eref1), (const double*)(w + o_zero), tl, 0.0,
+                                     (double2*)(w + o_dbuf), (int*)(w + o_mv1), (double*)(w + o_est1),
+                                     (int*)(w + o_st1), std::min(own1, nc), nullptr, (const double*)(w + o_eta1)),
+                         "correction solve");
+            } else {
+                // the diagonal of each pair from its correction right-hand side (plain: kinetic
+                // scaling by the residual's kinetic energy; learned: the perceptron on top)
+                SGW_CUDA(cudaMemcpyAsync(w + o_pe, pe.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st), "copy");
+                SGW_CUDA(cudaMemcpyAsync(w + o_po, po.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st), "copy");
+                PrecondArgs pa;
+                pa.n = nc;
+                pa.mode = pc;
+                pa.rhs = (const double2*)(w + o_rvec);
+                pa.e_ref = (const double*)(w + o_pe);
+                pa.omega = (const double*)(w + o_po);
+                pa.delta = nullptr;
+                pa.eta = eta;
+                pa.half_ecut = 0.5 * s->ecut;
+                pa.v_mean = s->v_mean;
+                pa.mlp = pc == SGW_PRECOND_LEARNED ? mlp_weights(mlp) : nullptr;
+                pa.d = (double*)(w + o_pre);
+                SGW_CUDA(launch_precond(plan16, pa, st), "preconditioner kernel");
+                SolveArgs A;
+                A.nrhs = nc;
+                A.nshift = 1;
+                A.ell = ell;
+                A.max_mv = (pc == SGW_PRECOND_LEARNED && plain_budget > 0) ? 2 * plain_budget
+                                                                              : std::max(max_mv, 40000);
+                A.rhs = (const double2*)(w + o_rvec);
+                A.e_ref = (const double*)(w + o_eref1);
+                A.sig = (const double*)(w + o_zero);
+                A.omega_seed = 0.0;
+                A.eta = eta;
+                A.tol = tl;
+                A.x = (double2*)(w + o_dbuf);
+                const int gb = std::min(grid_b, nc);
+                A.seedw = (double2*)(w + o_solver);
+                A.uw = (double2*)(w + o_solver + (size_t)gb * vb * (2 * ell + 3));
+                A.pscr = (double2*)(w + o_solver + (size_t)gb * vb * (2 * ell + 4));
+                A.pre = (const double*)(w + o_pre);
+                A.counter = (int*)(w + o_cnt);
+                A.out_mv = (int*)(w + o_mv1);
+                A.out_res = (double*)(w + o_est1);
+                A.out_status = (int*)(w + o_st1);
+                SGW_CUDA(launch_solve(plan16, A, gb, st), "preconditioned correction solve");
+                ++launches;
+            }
             SGW_CUDA(launch_pair_axpy(nc, d_list, s->npw, (const double2*)(w + o_dbuf), X, st), "refinement update");
-            SGW_CUDA(launch_residual(plan, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
-                                     (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(grid_r, nc), st, d_etas,
-                                     d_b),
+            SGW_CUDA(launch_residual(plan16, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
+                                     (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(own_r, nc), st, d_etas,
+                                     d_b, res_prec),
                      "residual kernel");
             launches += 4;
             SGW_CUDA(cudaMemcpyAsync(mv1.data(), w + o_mv1, sizeof(int) * nc, cudaMemcpyDeviceToHost, st), "report");
@@ -1004,13 +1338,13 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
             for (int i = 0; i < nc; ++i) mvv[list[c0 + i]] += mv1[i];
         }
         SGW_CUDA(cudaMemcpyAsync(relv.data(), d_rel, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
+        SGW_CUDA(cudaMemcpyAsync(certv.data(), d_cert, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
         SGW_CUDA(cudaStreamSynchronize(st), "refinement");
     }
-    SGW_CUDA(cudaMemcpyAsync(certv.data(), d_cert, sizeof(double) * np, cudaMemcpyDeviceToHost, st), "report");
-    SGW_CUDA(cudaStreamSynchronize(st), "solve");
     bool all = true;
     for (size_t q = 0; q < np; ++q) {
-        if (relv[q] <= tol) stv[q] = SGW_PAIR_CONVERGED;
+        const bool ok = relv[q] <= tol && (!use_cert || certv[q] <= cert_tol);
+        if (ok) stv[q] = SGW_PAIR_CONVERGED;
         else if (stv[q] == SGW_PAIR_CONVERGED) stv[q] = SGW_PAIR_MAXITER;
         all = all && stv[q] == SGW_PAIR_CONVERGED;
     }
@@ -1021,8 +1355,9 @@ static sgw_status multishift(sgw_system* s, const Plan& plan, int nrhs, const do
         if (report->rel_res) std::memcpy(report->rel_res, relv.data(), sizeof(double) * np);
         if (report->cert) std::memcpy(report->cert, certv.data(), sizeof(double) * np);
         if (report->launches) *report->launches = launches;
+        if (report->fallbacks) *report->fallbacks = fallbacks;
     }
-    if (!all) return fail(SGW_ENOCONV, "some (rhs, omega) pairs did not reach the tolerance");
+    if (!all) return fail(SGW_ENOCONV, "some (rhs, omega) pairs did not reach the tolerance or the certificate");
     return SGW_OK;
 }
 
@@ -1047,7 +1382,7 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     sgw_status r;
     if ((r = stage_in(rhs, vb * nrhs, in, st, "rhs")) != SGW_OK) return r;
     if ((r = stage_out(dpsi, vb * (size_t)nrhs * nomega, out, "dpsi", st)) != SGW_OK) return r;
-    const sgw_status rs = multishift(s, s->plan, nrhs, (const double2*)in.dev, e_ref, nomega, omega, nullptr, eta, tol,
+    const sgw_status rs = multishift(s, true, nrhs, (const double2*)in.dev, e_ref, nomega, omega, nullptr, eta, tol,
                                      opts, (double2*)out.dev, report, st);
     if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
     if ((r = finish_out(out, st, "dpsi copy")) != SGW_OK) return r;
@@ -1075,11 +1410,7 @@ sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, con
     if (ncol == 0) return SGW_OK;
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
-    // the operator is H itself: the plan without occupied states
-    Plan plan = s->plan;
-    plan.nocc = 0;
-    plan.psi = nullptr;
-    plan.psi_dd = nullptr;
+    // the operator is H itself: no occupied states
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in_cols, rb, out;
     sgw_status r;
@@ -1090,7 +1421,7 @@ sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, con
     SGW_CUDA(launch_unit_rhs((const int*)in_cols.dev, ncol, s->npw, (double2*)rb.dev, st), "unit rhs kernel");
     if ((r = stage_out(g, vb * (size_t)ncol * nz, out, "g", st)) != SGW_OK) return r;
     std::vector<double> e0(ncol, 0.0);
-    const sgw_status rs = multishift(s, plan, ncol, (const double2*)rb.dev, e0.data(), nz, zre.data(), zim.data(), 0.0,
+    const sgw_status rs = multishift(s, false, ncol, (const double2*)rb.dev, e0.data(), nz, zre.data(), zim.data(), 0.0,
                                      tol, opts, (double2*)out.dev, report, st);
     if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
     if (report && report->launches) *report->launches += 1;
@@ -1130,7 +1461,7 @@ static sgw_status density_common(sgw_system* s, int n_v, int n_pert, const void*
         om2[nomega + j] = -wre[j];
         eta2[nomega + j] = -wim[j];
     }
-    const sgw_status rs = multishift(s, s->plan, nrhs, (const double2*)in.dev, e_rows.data(), 2 * nomega, om2.data(),
+    const sgw_status rs = multishift(s, true, nrhs, (const double2*)in.dev, e_rows.data(), 2 * nomega, om2.data(),
                                      eta2.data(), 1.0, tol, opts, (double2*)xb.dev, report, st);
     if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
     SGW_CUDA(launch_density(n_v, n_pert, nomega, s->npw, (const double2*)in.dev, (const double2*)xb.dev, weight,
@@ -1374,9 +1705,10 @@ sgw_status sgw_solve_pershift(sgw_system* s, int npairs, const void* rhs, const 
     sgw_status r;
     if ((r = stage_in(rhs, vb * npairs, in, st, "rhs")) != SGW_OK) return r;
     if ((r = stage_out(x, vb * npairs, out, "x", st)) != SGW_OK) return r;
+    if (s->plan.csize > 1) return fail(SGW_EUNSUPPORTED, "per-shift BiCGstab needs a box that fits one CTA");
     int grid = 0, grid_r = 0;
     SGW_CUDA(solve_grid(s->plan, 1, npairs, &grid), "solver occupancy");
-    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid_r, kResThreads), "residual occupancy");
+    SGW_CUDA(residual_owners(s->plan, SGW_PREC_FP64, &grid_r), "residual occupancy");
     grid_r = std::min(grid_r, npairs);
     Carve c;
     const size_t o_seed = c.take(vb * (2 * ell + 3) * grid);
@@ -1500,7 +1832,7 @@ sgw_status sgw_residual(sgw_system* s, int nrhs, const void* rhs, const double* 
     if ((r = stage_in(rhs, vb * nrhs, in_r, st, "rhs")) != SGW_OK) return r;
     if ((r = stage_in(dpsi, vb * np, in_x, st, "dpsi")) != SGW_OK) return r;
     int grid = 0;
-    SGW_CUDA(resident_grid(residual_kernel_ptr(), apply_smem_bytes(s->plan), &grid, kResThreads), "residual occupancy");
+    SGW_CUDA(residual_owners(s->plan, SGW_PREC_FP64, &grid), "residual occupancy");
     grid = (int)std::min<size_t>(grid, np);
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t off_er = al(2 * vb * grid);

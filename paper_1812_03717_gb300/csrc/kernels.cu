@@ -110,13 +110,16 @@ __device__ __forceinline__ double2 cpowr(double2 a, int e) {
 // out = A D in with A = P_c H P_c - z and D = diag(pre) (right preconditioning of a
 // single-shift system): T1 = D in, T2 = P_c T1, out = P_c H T2 - z T1.  Without `pre` the
 // Krylov vectors already lie in range(P_c) and out = P_c H in - z in.
+// (One CTA per vector: the launcher refuses plans split over a cluster.)
 static __device__ void apply_op(const Plan& P, unsigned char* smem, const double2* in, double2* out, double2 zs,
                                 const double* pre, double2* t1, double2* t2) {
+    const ApplySmem L = apply_smem_layout(P, 16);
+    const Part q = make_part(P);
+    Red R = make_red(P, smem, L);
     if (!pre) {
-        apply_h_block<ArF64>(P, smem, in, out, zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+        apply_h_block<ArF64>(P, smem, q, R, in, out, zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
         return;
     }
-    const ApplySmem L = apply_smem_layout(P);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
     const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
@@ -129,7 +132,7 @@ static __device__ void apply_op(const Plan& P, unsigned char* smem, const double
         t2[g] = h;
     }
     __syncthreads();
-    apply_h_block<ArF64>(P, smem, t2, out, cz(), APPLY_PROJ_OUT);
+    apply_h_block<ArF64>(P, smem, q, R, t2, out, cz(), APPLY_PROJ_OUT);
     for (int g = tid; g < npw; g += nt) out[g] = csub(out[g], cmul(zs, t1[g]));
     __syncthreads();
 }
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
     __shared__ double2 s_dot[kRedSlots];
 
     load_twiddles<ArF64>(P, smem);
-    const ApplySmem L = apply_smem_layout(P);
+    const ApplySmem L = apply_smem_layout(P, 16);
     double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
     const int ns = A.nshift, ell = A.ell, npw = P.npw;
@@ -489,257 +492,9 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
     }
 }
 
-// ----------------------------------------------------------------- shifted Lanczos (FOM)
-//
-// Multishift solve by the Hermitian Lanczos process on A = P_c H P_c (Sec. 2.2: systems
-// that differ only in the frequency share one Krylov space).  With b = beta_1 v_1,
-//   A V_k = V_k T_k + beta_{k+1} v_{k+1} e_k^T,   T_k real symmetric tridiagonal (alpha, beta),
-// the Galerkin solution of shift j is x_j = V_k y_j with (T_k - z_j) y_j = beta_1 e_1.  The
-// LDL^T pivots of the complex-symmetric T_k - z_j,
-//   eta_1 = alpha_1 - z_j,  l_i = beta_i / eta_{i-1},  eta_i = alpha_i - z_j - l_i beta_i,
-// never vanish because Im z_j = eta > 0 and T_k has a real spectrum; the forward sweep
-// u_i = -l_i u_{i-1} (u_1 = beta_1) gives the residual norm |beta_{k+1} u_k / eta_k| of every
-// shift from scalars alone, and the residuals of all shifts stay collinear with v_{k+1}.
-// The basis is kept (one slice of global memory per CTA); when every shift has converged
-// (or the basis is full) each y_j is formed by the backward sweep y_i = u_i/eta_i - l_{i+1}
-// y_{i+1} and x_j = V y_j in one pass over the basis.
-template <class Ar, int NT>
-__global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double2 s_dot[kRedSlots];
-    __shared__ int s_r, s_nact, s_kmax, s_fail;
-    load_twiddles<Ar>(P, smem);
-    const ApplySmem L = apply_smem_layout(P);
-    double2* red = reinterpret_cast<double2*>(smem + L.red);
-    double2* coef = reinterpret_cast<double2*>(smem + L.coef);
-    const int ns = A.nshift, npw = P.npw, tid = threadIdx.x, nt = blockDim.x, maxk = A.maxk;
-    // per-shift state after the apply's shared memory
-    int off = L.end;
-    double2* zsh = reinterpret_cast<double2*>(smem + off); off = align16(off + ns * 16);
-    double2* eta = reinterpret_cast<double2*>(smem + off); off = align16(off + ns * 16);
-    double2* zeta = reinterpret_cast<double2*>(smem + off); off = align16(off + ns * 16);
-    double* est = reinterpret_cast<double*>(smem + off); off = align16(off + ns * 8);
-    int* kc = reinterpret_cast<int*>(smem + off); off = align16(off + ns * 4);
-    int* st = reinterpret_cast<int*>(smem + off);
-
-    using C = typename Ar::C;
-    C* V = reinterpret_cast<C*>(A.basis) + (size_t)blockIdx.x * (maxk + 1) * npw;
-    double* ab = A.ab + (size_t)blockIdx.x * 2 * (maxk + 1);     // alpha[0..maxk), beta[0..maxk]
-    double* al = ab;
-    double* be = ab + (maxk + 1);
-    double2* Ysc = A.ysc + (size_t)blockIdx.x * 2 * maxk * ns;   // [maxk][ns] y, [maxk][ns] l
-    double2* Lsc = Ysc + (size_t)maxk * ns;
-    C* Yc = reinterpret_cast<C*>(Ysc);                          // y in the policy's format (same slots)
-
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s_r = atomicAdd(A.counter, 1);
-        __syncthreads();
-        const int r = s_r;
-        if (r >= A.nrhs) break;
-        const double2* rhs = A.rhs + (size_t)r * npw;
-        double2* X = A.x + (size_t)r * ns * npw;
-
-        // b = -P_c rhs (FP64), beta_1 = |b|, V[0] = b / beta_1 in the policy's format
-        block_dots(P.psi, P.nocc, npw, rhs, npw, red, coef);
-        {
-            double2 acc[1] = {cz()};
-            for (int g = tid; g < npw; g += nt) {
-                double2 h = rhs[g];
-                for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
-                acc[0].x += cabs2(h);
-            }
-            block_sum<1>(acc, red, s_dot);
-        }
-        const double b1 = sqrt(s_dot[0].x);
-        const bool zero = !(b1 > 0.0), bad = !isfinite(b1);
-        {
-            const double inv = (zero || bad) ? 0.0 : -1.0 / b1;
-            for (int g = tid; g < npw; g += nt) {
-                double2 h = rhs[g];
-                for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
-                V[g] = Ar::from_d(cscal(h, inv));
-            }
-        }
-        for (int j = tid; j < ns; j += nt) {
-            zsh[j] = make_double2(A.e_ref[r] + A.omega[j], A.eta_r ? A.eta_r[r] : (A.eta_s ? A.eta_s[j] : A.eta));
-            est[j] = 1.0;
-            kc[j] = 0;
-            st[j] = bad ? SGW_PAIR_NONFINITE : (zero ? SGW_PAIR_CONVERGED : -1);
-            if (zero) est[j] = 0.0;
-        }
-        if (tid == 0) {
-            s_nact = (zero || bad) ? 0 : ns;
-            s_fail = 0;
-            be[0] = 0.0;
-        }
-        __syncthreads();
-        int k = 0;
-        while (s_nact > 0 && k < maxk) {
-            C* vk = V + (size_t)k * npw;
-            C* w = V + (size_t)(k + 1) * npw;
-            apply_h_block<Ar>(P, smem, vk, w, cz(), APPLY_PROJ_OUT);
-            const double bk = be[k];
-            const C* vkm = k > 0 ? V + (size_t)(k - 1) * npw : nullptr;
-            {
-                const typename Ar::R bkr = Ar::real(bk);
-                C acc = Ar::zero();
-                for (int g = tid; g < npw; g += nt) {
-                    C h = w[g];
-                    if (vkm) h = Ar::sub(h, Ar::scalr(vkm[g], bkr));
-                    w[g] = h;
-                    acc = Ar::add(acc, Ar::mul(Ar::conj(vk[g]), h));
-                }
-                C a2[1] = {acc};
-                block_sum_c<1>(a2, red, s_dot);
-            }
-            const double a = s_dot[0].x;
-            {
-                const typename Ar::R ar = Ar::real(a);
-                C acc = Ar::zero();
-                for (int g = tid; g < npw; g += nt) {
-                    const C h = Ar::sub(w[g], Ar::scalr(vk[g], ar));
-                    w[g] = h;
-                    acc = Ar::acc_norm(acc, h);
-                }
-                C a2[1] = {acc};
-                block_sum_c<1>(a2, red, s_dot);
-            }
-            const double bn = sqrt(s_dot[0].x);
-            {
-                const typename Ar::R inv = Ar::real(bn > 0.0 ? 1.0 / bn : 0.0);
-                for (int g = tid; g < npw; g += nt) w[g] = Ar::scalr(w[g], inv);
-            }
-            if (tid == 0) {
-                al[k] = a;
-                be[k + 1] = bn;
-                if (!isfinite(a) || !isfinite(bn)) s_fail = SGW_PAIR_NONFINITE;
-            }
-            // per-shift pivots and residual estimates
-            for (int j = tid; j < ns; j += nt) {
-                if (st[j] >= 0) continue;
-                const double2 d = make_double2(a - zsh[j].x, -zsh[j].y);
-                double2 e, u;
-                if (k == 0) {
-                    e = d;
-                    u = make_double2(b1, 0.0);
-                } else {
-                    const double2 l = cdiv(make_double2(bk, 0.0), eta[j]);
-                    e = csub(d, cscal(l, bk));
-                    u = cmul(make_double2(-l.x, -l.y), zeta[j]);
-                }
-                eta[j] = e;
-                zeta[j] = u;
-                const double2 q = cdiv(u, e);
-                const double rr = bn * sqrt(cabs2(q)) / b1;
-                est[j] = rr;
-                kc[j] = k + 1;
-                if (!isfinite(rr)) st[j] = SGW_PAIR_NONFINITE;
-                else if (rr <= A.tol || bn == 0.0) st[j] = SGW_PAIR_CONVERGED;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int n = 0;
-                for (int j = 0; j < ns; ++j) n += st[j] < 0 ? 1 : 0;
-                s_nact = s_fail ? 0 : n;
-            }
-            ++k;
-            __syncthreads();
-            if (bn == 0.0) break;
-        }
-        // budget exhausted / failure
-        for (int j = tid; j < ns; j += nt)
-            if (st[j] < 0) st[j] = s_fail ? s_fail : SGW_PAIR_MAXITER;
-        if (tid == 0) {
-            int m = 0;
-            for (int j = 0; j < ns; ++j) m = max(m, kc[j]);
-            s_kmax = m;
-        }
-        __syncthreads();
-        const int K = s_kmax;
-        // y_j = (T_kj - z_j)^{-1} beta_1 e_1 by forward / backward sweeps (one thread per shift)
-        for (int j = tid; j < ns; j += nt) {
-            const int kj = kc[j];
-            if (kj == 0 || st[j] == SGW_PAIR_NONFINITE) {
-                for (int i = 0; i < K; ++i) Ysc[(size_t)i * ns + j] = cz();
-                continue;
-            }
-            double2 e = make_double2(al[0] - zsh[j].x, -zsh[j].y);
-            double2 u = make_double2(b1, 0.0);
-            Ysc[j] = cdiv(u, e);
-            for (int i = 1; i < kj; ++i) {
-                const double2 l = cdiv(make_double2(be[i], 0.0), e);
-                e = csub(make_double2(al[i] - zsh[j].x, -zsh[j].y), cscal(l, be[i]));
-                u = cmul(make_double2(-l.x, -l.y), u);
-                Lsc[(size_t)i * ns + j] = l;
-                Ysc[(size_t)i * ns + j] = cdiv(u, e);
-            }
-            for (int i = kj - 2; i >= 0; --i)
-                Ysc[(size_t)i * ns + j] = csub(Ysc[(size_t)i * ns + j], cmul(Lsc[(size_t)(i + 1) * ns + j],
-                                                                         Ysc[(size_t)(i + 1) * ns + j]));
-            for (int i = kj; i < K; ++i) Ysc[(size_t)i * ns + j] = cz();
-        }
-        __syncthreads();
-        // y in the policy's format (each slot converted in place by the thread of its shift)
-        for (int j = tid; j < ns; j += nt)
-            for (int i = 0; i < K; ++i) Yc[(size_t)i * ns + j] = Ar::from_d(Ysc[(size_t)i * ns + j]);
-        __syncthreads();
-        // x_j = V y_j, shifts in tiles of TJ (fewer live accumulators for the larger CTAs).  The
-        // tile's y coefficients are staged in the (now idle) FFT buffers of shared memory, KC
-        // Lanczos steps at a time; every thread reads them as broadcasts.
-        constexpr int TJ = NT >= 384 ? 4 : 8;
-        {
-            C* ys = reinterpret_cast<C*>(smem + L.sticks);
-            const int KC = (L.red - L.sticks) / (TJ * (int)sizeof(C));
-            for (int j0 = 0; j0 < ns; j0 += TJ) {
-                const int cnt = min(TJ, ns - j0);
-                int Kt = 0;   // the tile's longest Lanczos run (y is zero beyond each shift's own)
-                for (int t = 0; t < cnt; ++t) Kt = max(Kt, kc[j0 + t]);
-                if (Kt == 0)
-                    for (size_t i = tid; i < (size_t)cnt * npw; i += nt) X[(size_t)j0 * npw + i] = cz();
-                for (int k0 = 0; k0 < Kt; k0 += KC) {
-                    const int kn = min(KC, Kt - k0);
-                    __syncthreads();
-                    for (int i = tid; i < kn * TJ; i += nt) {
-                        const int ii = i / TJ, t = i - ii * TJ;
-                        ys[i] = t < cnt ? Yc[(size_t)(k0 + ii) * ns + j0 + t] : Ar::zero();
-                    }
-                    __syncthreads();
-                    for (int g = tid; g < npw; g += nt) {
-                        C acc[TJ];
-#pragma unroll
-                        for (int t = 0; t < TJ; ++t) acc[t] = Ar::zero();
-                        const C* vg = V + (size_t)k0 * npw + g;
-#pragma unroll 2
-                        for (int i = 0; i < kn; ++i) {
-                            const C v = vg[(size_t)i * npw];
-                            const C* yr = ys + i * TJ;
-#pragma unroll
-                            for (int t = 0; t < TJ; ++t) acc[t] = Ar::add(acc[t], Ar::mul(yr[t], v));
-                        }
-#pragma unroll
-                        for (int t = 0; t < TJ; ++t) {
-                            if (t < cnt) {
-                                double2* xo = X + (size_t)(j0 + t) * npw + g;
-                                const double2 d = Ar::to_d(acc[t]);
-                                *xo = k0 == 0 ? d : cadd(*xo, d);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        for (int j = tid; j < ns; j += nt) {
-            A.out_status[(size_t)r * ns + j] = st[j];
-            A.out_mv[(size_t)r * ns + j] = kc[j];
-            A.out_res[(size_t)r * ns + j] = est[j];
-        }
-        __syncthreads();
-    }
-}
-
-// y_i = H x_i, or (P_c H P_c - z_i) x_i when `project` is set.  One CTA per vector
-// (persistent over the batch); scratch holds P_c x per CTA.
+// y_i = H x_i, or (P_c H P_c - z_i) x_i when `project` is set.  One CTA or cluster per vector
+// (persistent over the batch); scratch holds the input and output in the policy's format
+// per owner.
 template <class Ar>
 __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, const double2* __restrict__ x,
                                                             double2* __restrict__ y, const double2* __restrict__ z,
@@ -747,39 +502,43 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, co
     using C = typename Ar::C;
     extern __shared__ __align__(16) unsigned char smem[];
     load_twiddles<Ar>(P, smem);
-    const ApplySmem L = apply_smem_layout(P);
-    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    const ApplySmem L = apply_smem_layout(P, (int)sizeof(C));
+    Red R = make_red(P, smem, L);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const Part q = make_part(P);
     const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
-    double2* xs = scratch + (size_t)blockIdx.x * 3 * npw;     // P_c x (FP64)
-    C* xa = reinterpret_cast<C*>(xs + npw);                    // input in the policy's format
-    C* ya = reinterpret_cast<C*>(xs + 2 * npw);                // output in the policy's format
-    for (int v = blockIdx.x; v < nvec; v += gridDim.x) {
+    const int cl_id = blockIdx.x / P.csize, ncl = gridDim.x / P.csize;
+    C* xa = reinterpret_cast<C*>(scratch + (size_t)cl_id * 2 * npw);         // input in the policy's format
+    C* ya = reinterpret_cast<C*>(scratch + (size_t)cl_id * 2 * npw + npw);   // output in the policy's format
+    for (int v = cl_id; v < nvec; v += ncl) {
         const double2* xv = x + (size_t)v * npw;
         double2* yv = y + (size_t)v * npw;
         if (project) {
-            block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
-            for (int g = tid; g < npw; g += nt) {
+            part_dots_f64(P, q, R, P.psi, P.nocc, npw, xv, coef);
+            for (int g = q.g0 + tid; g < q.g1; g += nt) {
                 double2 h = xv[g];
                 for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
                 xa[g] = Ar::from_d(h);
             }
         } else {
-            for (int g = tid; g < npw; g += nt) xa[g] = Ar::from_d(xv[g]);
+            for (int g = q.g0 + tid; g < q.g1; g += nt) xa[g] = Ar::from_d(xv[g]);
         }
         __syncthreads();
-        apply_h_block<Ar>(P, smem, xa, ya, cz(), project ? APPLY_PROJ_OUT : 0);
+        apply_h_block<Ar>(P, smem, q, R, xa, ya, cz(), project ? APPLY_PROJ_OUT : 0);
         const double2 zz = project ? z[v] : cz();
-        for (int g = tid; g < npw; g += nt) yv[g] = csub(Ar::to_d(ya[g]), cmul(zz, xv[g]));
+        for (int g = q.g0 + tid; g < q.g1; g += nt) yv[g] = csub(Ar::to_d(ya[g]), cmul(zz, xv[g]));
         __syncthreads();
     }
 }
 
-// For every listed pair q = r * ns + j (all pairs when list is NULL):
-//   res = -P_c rhs_r - (P_c H P_c - z_rj) x_rj  in FP64,
-//   rel[q] = |res| / |P_c rhs_r|,  cert[q] = |res| / (eta |x_rj|),
+// For every listed pair p = r * ns + j (all pairs when list is NULL):
+//   res = -P_c rhs_r - (P_c H P_c - z_rj) x_rj,
+//   rel[p] = |res| / |P_c rhs_r|,  cert[p] = |res| / (|Im z_rj| |x_rj|),
 // and, when store is given, store[i] = -res (the right-hand side of the correction
-// equation in the solver's convention b = -P_c rhs).
+// equation in the solver's convention b = -P_c rhs).  The projections, the assembly of res
+// and the norms are FP64; H (P_c x) is applied in the policy Ar (FP64, or float-float with a
+// relative error near 1e-14).  One CTA or cluster per pair; scratch: 2 n_pw values per owner.
+template <class Ar>
 __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nrhs, int ns, const int* __restrict__ list,
                                                                int nlist, const double2* __restrict__ rhs,
                                                                const double* __restrict__ e_ref,
@@ -789,34 +548,39 @@ __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nr
                                                                double* __restrict__ cert, double2* __restrict__ store,
                                                                const double* __restrict__ eta_s,
                                                                const double2* __restrict__ bvec) {
+    using C = typename Ar::C;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double2 s_dot[kRedSlots];
-    load_twiddles<ArF64>(P, smem);
-    const ApplySmem L = apply_smem_layout(P);
-    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    load_twiddles<Ar>(P, smem);
+    const ApplySmem L = apply_smem_layout(P, (int)sizeof(C));
+    Red R = make_red(P, smem, L);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
+    const Part q = make_part(P);
     const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
-    double2* xs = scratch + (size_t)blockIdx.x * 2 * npw;
-    double2* ys = xs + npw;
+    const int cl_id = blockIdx.x / P.csize, ncl = gridDim.x / P.csize;
+    double2* xs = scratch + (size_t)cl_id * 2 * npw;   // P_c x, stored in the policy's format
+    double2* ys = xs + npw;                             // H P_c x in the policy's format
+    C* xa = reinterpret_cast<C*>(xs);
+    C* ya = reinterpret_cast<C*>(ys);
     const int count = list ? nlist : nrhs * ns;
-    for (int i = blockIdx.x; i < count; i += gridDim.x) {
-        const int q = list ? list[i] : i;
-        const int r = q / ns, j = q % ns;
-        const double2* xv = x + (size_t)q * npw;
+    for (int i = cl_id; i < count; i += ncl) {
+        const int pq = list ? list[i] : i;
+        const int r = pq / ns, j = pq % ns;
+        const double2* xv = x + (size_t)pq * npw;
         const double2* rv = rhs + (size_t)r * npw;
         const double2 z = make_double2(e_ref[r] + omega[j], eta_s ? eta_s[j] : eta);
-        block_dots(P.psi, P.nocc, npw, xv, npw, red, coef);
-        for (int g = tid; g < npw; g += nt) {
+        part_dots_f64(P, q, R, P.psi, P.nocc, npw, xv, coef);
+        for (int g = q.g0 + tid; g < q.g1; g += nt) {
             double2 h = xv[g];
             for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
-            xs[g] = h;
+            xa[g] = Ar::from_d(h);   // same thread, same slot: no FP64 value is read back
         }
         __syncthreads();
-        apply_h_block<ArF64>(P, smem, xs, ys, cz(), APPLY_PROJ_OUT);
+        apply_h_block<Ar>(P, smem, q, R, xa, ya, cz(), APPLY_PROJ_OUT);
         const double2* bv = bvec ? bvec + (size_t)r * npw : nullptr;   // -P_c rhs, when precomputed
-        if (!bv) block_dots(P.psi, P.nocc, npw, rv, npw, red, coef);
+        if (!bv) part_dots_f64(P, q, R, P.psi, P.nocc, npw, rv, coef);
         double2 acc[3] = {cz(), cz(), cz()};
-        for (int g = tid; g < npw; g += nt) {
+        for (int g = q.g0 + tid; g < q.g1; g += nt) {
             double2 b;
             if (bv) {
                 b = bv[g];
@@ -825,22 +589,22 @@ __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nr
                 for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
                 b = make_double2(-h.x, -h.y);
             }
-            const double2 ax = csub(ys[g], cmul(z, xv[g]));
+            const double2 ax = csub(Ar::to_d(ya[g]), cmul(z, xv[g]));
             const double2 res = csub(b, ax);
             if (store) store[(size_t)i * npw + g] = make_double2(-res.x, -res.y);
             acc[0].x += cabs2(res);
             acc[1].x += cabs2(b);
             acc[2].x += cabs2(xv[g]);
         }
-        block_sum<3>(acc, red, s_dot);
-        if (tid == 0) {
+        part_sum<3>(P, R, acc, s_dot);
+        if (q.rank == 0 && tid == 0) {
             const double rn = sqrt(s_dot[0].x), bn = sqrt(s_dot[1].x), xn = sqrt(s_dot[2].x);
             if (!isfinite(rn) || !isfinite(bn) || !isfinite(xn)) {
-                rel[q] = NAN;   // a non-finite input or solution is never reported converged
-                cert[q] = NAN;
+                rel[pq] = NAN;   // a non-finite input or solution is never reported converged
+                cert[pq] = NAN;
             } else {
-                rel[q] = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
-                cert[q] = xn > 0.0 ? rn / (fabs(z.y) * xn) : (rn > 0.0 ? INFINITY : 0.0);
+                rel[pq] = bn > 0.0 ? rn / bn : (rn > 0.0 ? INFINITY : 0.0);
+                cert[pq] = xn > 0.0 ? rn / (fabs(z.y) * xn) : (rn > 0.0 ? INFINITY : 0.0);
             }
         }
         __syncthreads();
@@ -1380,44 +1144,47 @@ cudaError_t launch_precond(const Plan& P, const PrecondArgs& a, cudaStream_t st)
 // ------------------------------------------------------------------------ host launchers
 
 namespace {
+int bicg_extra(int ns) { return shift_layout(0, ns).end; }
+}  // namespace
+
 int optin_smem() {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return v;
 }
-int bicg_extra(int ns) { return shift_layout(0, ns).end; }
-int lanczos_extra(int ns) { return 3 * align16(ns * 16) + align16(ns * 8) + 2 * align16(ns * 4); }
-}  // namespace
 
 // Raises a kernel's dynamic shared-memory limit to everything the device allows next to its
-// static shared memory.  Always the same value for a kernel, so concurrent solves of systems
-// of different sizes (several host threads) never lower it under one another's launch.
+// static shared memory (and allows clusters of 16).  Always the same values for a kernel, so
+// concurrent solves of systems of different sizes (several host threads) never lower them
+// under one another's launch.
 cudaError_t allow_max_smem(const void* kernel) {
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                optin_smem() - (int)fa.sharedSizeBytes);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin_smem() - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 // The plan with as many xy-planes per pass (4, 2 or 1) as fit next to `extra` bytes of
-// kernel-specific shared memory.
-Plan tuned_plan(const Plan& P, int extra) {
+// kernel-specific shared memory, for es-byte complex values.
+Plan tuned_plan(const Plan& P, int extra, int es) {
     Plan Q = P;
     const int cap = optin_smem() - 1024;   // static shared memory of the kernels
     for (int np : {4, 2, 1}) {
         Q.nplanes = np;
-        if (apply_smem_layout(Q).end + extra <= cap) return Q;
+        if (apply_smem_layout(Q, es).end + extra <= cap) return Q;
     }
     Q.nplanes = 1;
     return Q;
 }
 
-int apply_smem_bytes(const Plan& P) { return apply_smem_layout(tuned_plan(P, 0)).end; }
+int apply_smem_bytes(const Plan& P, int es) { return apply_smem_layout(tuned_plan(P, 0, es), es).end; }
 
 int solve_smem_bytes(const Plan& P, int nshift) {
-    return apply_smem_layout(tuned_plan(P, bicg_extra(nshift))).end + bicg_extra(nshift);
+    return apply_smem_layout(tuned_plan(P, bicg_extra(nshift), 16), 16).end + bicg_extra(nshift);
 }
 
 cudaError_t resident_grid(const void* kernel, int smem, int* grid, int threads) {
@@ -1435,7 +1202,53 @@ cudaError_t resident_grid(const void* kernel, int smem, int* grid, int threads) 
     return cudaSuccess;
 }
 
+namespace {
+cudaLaunchConfig_t owned_config(const Plan& P, int owners, int threads, int smem, cudaStream_t st,
+                                cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(owners * P.csize));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    if (P.csize > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)P.csize;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cfg;
+}
+}  // namespace
+
+// Vector owners (CTAs, or clusters of P.csize CTAs) of `kernel` that are resident at once.
+cudaError_t owner_capacity(const void* kernel, const Plan& P, int threads, int smem, int* owners) {
+    if (P.csize == 1) return resident_grid(kernel, smem, owners, threads);
+    cudaError_t e = allow_max_smem(kernel);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = owned_config(P, 1, threads, smem, nullptr, attr);
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    *owners = n;
+    return cudaSuccess;
+}
+
+// Launches `kernel` with `owners` vector owners: owners CTAs, or owners clusters of P.csize.
+cudaError_t launch_owned(const void* kernel, const Plan& P, int owners, int threads, int smem, cudaStream_t st,
+                         void** args) {
+    cudaError_t e = allow_max_smem(kernel);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = owned_config(P, owners, threads, smem, st, attr);
+    return cudaLaunchKernelExC(&cfg, kernel, args);
+}
+
 cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid) {
+    if (P.csize > 1) return cudaErrorNotSupported;
     int g = 0;
     cudaError_t e = resident_grid((const void*)ms_solve_kernel, solve_smem_bytes(P, nshift), &g, kThreads);
     if (e != cudaSuccess) return e;
@@ -1445,7 +1258,8 @@ cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid) {
 }
 
 cudaError_t launch_solve(const Plan& P0, const SolveArgs& a, int grid, cudaStream_t st) {
-    const Plan P = tuned_plan(P0, bicg_extra(a.nshift));
+    if (P0.csize > 1) return cudaErrorNotSupported;   // BiCGstab runs one CTA per vector
+    const Plan P = tuned_plan(P0, bicg_extra(a.nshift), 16);
     const int smem = solve_smem_bytes(P0, a.nshift);
     cudaError_t e = allow_max_smem((const void*)ms_solve_kernel);
     if (e != cudaSuccess) return e;
@@ -1455,31 +1269,49 @@ cudaError_t launch_solve(const Plan& P0, const SolveArgs& a, int grid, cudaStrea
     return cudaGetLastError();
 }
 
+namespace {
+const void* apply_ptr(int precision) {
+    if (precision == SGW_PREC_DF32) return (const void*)apply_kernel<ArDF>;
+    if (precision == SGW_PREC_FP32) return (const void*)apply_kernel<ArF32>;
+    return (const void*)apply_kernel<ArF64>;
+}
+const void* residual_ptr(int precision) {
+    return precision == SGW_PREC_FP64 ? (const void*)residual_kernel<ArF64> : (const void*)residual_kernel<ArDF>;
+}
+int residual_bytes(int precision) { return precision == SGW_PREC_FP64 ? 16 : 16; }
+}  // namespace
+
+cudaError_t apply_owners(const Plan& P, int precision, int* owners) {
+    const int es = prec_bytes(precision);
+    return owner_capacity(apply_ptr(precision), P, kThreads, apply_smem_bytes(P, es), owners);
+}
+
 cudaError_t launch_apply(const Plan& P0, int nvec, const double2* x, double2* y, const double2* z, int project,
-                         double2* scratch, int grid, int precision, cudaStream_t st) {
-    const Plan P = tuned_plan(P0, 0);
-    const int smem = apply_smem_bytes(P0);
-    const void* k = precision == SGW_PREC_DF32 ? (const void*)apply_kernel<ArDF> : (const void*)apply_kernel<ArF64>;
-    cudaError_t e = allow_max_smem(k);
-    if (e != cudaSuccess) return e;
-    if (precision == SGW_PREC_DF32)
-        apply_kernel<ArDF><<<grid, kThreads, smem, st>>>(P, nvec, x, y, z, project, scratch);
-    else
-        apply_kernel<ArF64><<<grid, kThreads, smem, st>>>(P, nvec, x, y, z, project, scratch);
-    return cudaGetLastError();
+                         double2* scratch, int owners, int precision, cudaStream_t st) {
+    const int es = prec_bytes(precision);
+    const Plan P = tuned_plan(P0, 0, es);
+    const int smem = apply_smem_bytes(P0, es);
+    void* args[] = {(void*)&P, (void*)&nvec, (void*)&x, (void*)&y, (void*)&z, (void*)&project, (void*)&scratch};
+    return launch_owned(apply_ptr(precision), P, owners, kThreads, smem, st, args);
+}
+
+cudaError_t residual_owners(const Plan& P, int precision, int* owners) {
+    return owner_capacity(residual_ptr(precision), P, kResThreads, apply_smem_bytes(P, residual_bytes(precision)),
+                          owners);
 }
 
 cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
-                            double* rel, double* cert, double2* store, int grid, cudaStream_t st,
-                            const double* eta_s, const double2* bvec) {
-    const Plan P = tuned_plan(P0, 0);
-    const int smem = apply_smem_bytes(P0);
-    cudaError_t e = allow_max_smem((const void*)residual_kernel);
-    if (e != cudaSuccess) return e;
-    residual_kernel<<<grid, kResThreads, smem, st>>>(P, nrhs, nshift, list, nlist, rhs, e_ref, omega, eta, x, scratch, rel,
-                                                  cert, store, eta_s, bvec);
-    return cudaGetLastError();
+                            double* rel, double* cert, double2* store, int owners, cudaStream_t st,
+                            const double* eta_s, const double2* bvec, int precision) {
+    const int es = residual_bytes(precision);
+    const Plan P = tuned_plan(P0, 0, es);
+    const int smem = apply_smem_bytes(P0, es);
+    void* args[] = {(void*)&P,     (void*)&nrhs,    (void*)&nshift, (void*)&list,  (void*)&nlist,
+                    (void*)&rhs,   (void*)&e_ref,   (void*)&omega,  (void*)&eta,   (void*)&x,
+                    (void*)&scratch, (void*)&rel,   (void*)&cert,   (void*)&store, (void*)&eta_s,
+                    (void*)&bvec};
+    return launch_owned(residual_ptr(precision), P, owners, kResThreads, smem, st, args);
 }
 
 cudaError_t launch_density(int n_v, int n_p, int nw, int npw, const double2* R, const double2* X, double weight,
@@ -1527,55 +1359,44 @@ cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2*
     return cudaGetLastError();
 }
 
-int lanczos_smem_bytes(const Plan& P, int nshift) {
-    return apply_smem_layout(tuned_plan(P, lanczos_extra(nshift))).end + lanczos_extra(nshift);
-}
-
-namespace {
-template <class Ar>
-const void* lanczos_ptr(int nt) {
-    if (nt == 512) return (const void*)lanczos_solve_kernel<Ar, 512>;
-    if (nt == 384) return (const void*)lanczos_solve_kernel<Ar, 384>;
-    return (const void*)lanczos_solve_kernel<Ar, 256>;
-}
-// CTA size: the requested 256 / 384 / 512, else the measured best for the precision (512 for
-// float-float, 384 for FP64 on the config-2 workload)
-int lanczos_threads(int requested, bool df) {
-    if (requested == 256 || requested == 384 || requested == 512) return requested;
-    return df ? 512 : 384;
-}
-}  // namespace
-
-cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int threads, int* grid) {
-    const int nt = lanczos_threads(threads, false), nt2 = lanczos_threads(threads, true);
-    int g = 0, g2 = 0;
-    cudaError_t e = resident_grid(lanczos_ptr<ArF64>(nt), lanczos_smem_bytes(P, nshift), &g, nt);
-    if (e != cudaSuccess) return e;
-    e = resident_grid(lanczos_ptr<ArDF>(nt2), lanczos_smem_bytes(P, nshift), &g2, nt2);
-    if (e != cudaSuccess) return e;
-    g = g < g2 ? g : g2;
-    *grid = g < nrhs ? g : nrhs;
-    if (*grid < 1) *grid = 1;
-    return cudaSuccess;
-}
-
-cudaError_t launch_lanczos(const Plan& P0, const LanczosArgs& a, int grid, int precision, int threads,
-                           cudaStream_t st) {
-    const Plan P = tuned_plan(P0, lanczos_extra(a.nshift));
-    const int smem = lanczos_smem_bytes(P0, a.nshift);
-    const bool df = precision == SGW_PREC_DF32;
-    const int nt = lanczos_threads(threads, df);
-    const void* k = df ? lanczos_ptr<ArDF>(nt) : lanczos_ptr<ArF64>(nt);
-    cudaError_t e = allow_max_smem(k);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    void* args[] = {(void*)&P, (void*)&a};
-    return cudaLaunchKernel(k, dim3(grid), dim3(nt), args, smem, st);
-}
-
 const void* solve_kernel_ptr() { return (const void*)ms_solve_kernel; }
-const void* apply_kernel_ptr() { return (const void*)apply_kernel<ArF64>; }
-const void* residual_kernel_ptr() { return (const void*)residual_kernel; }
+
+int lanczos_smem_f64(const Plan& P, int nshift);
+int lanczos_smem_df(const Plan& P, int nshift);
+int lanczos_smem_f32(const Plan& P, int nshift);
+cudaError_t lanczos_capacity_f64(const Plan& P, int nshift, int threads, int* owners);
+cudaError_t lanczos_capacity_df(const Plan& P, int nshift, int threads, int* owners);
+cudaError_t lanczos_capacity_f32(const Plan& P, int nshift, int threads, int* owners);
+cudaError_t lanczos_launch_f64(const Plan& P, const LanczosArgs& a, int owners, int threads, cudaStream_t st);
+cudaError_t lanczos_launch_df(const Plan& P, const LanczosArgs& a, int owners, int threads, cudaStream_t st);
+cudaError_t lanczos_launch_f32(const Plan& P, const LanczosArgs& a, int owners, int threads, cudaStream_t st);
+
+// CTA size: the requested 256 / 384 / 512, else the measured best for the precision (512 for
+// float-float and FP32, 384 for FP64 on the config-2 workload)
+int lanczos_threads(int requested, int precision) {
+    if (requested == 256 || requested == 384 || requested == 512) return requested;
+    return precision == SGW_PREC_FP64 ? 384 : 512;
+}
+
+int lanczos_smem_bytes(const Plan& P, int nshift, int precision) {
+    if (precision == SGW_PREC_DF32) return lanczos_smem_df(P, nshift);
+    if (precision == SGW_PREC_FP32) return lanczos_smem_f32(P, nshift);
+    return lanczos_smem_f64(P, nshift);
+}
+
+cudaError_t lanczos_capacity(const Plan& P, int nshift, int threads, int precision, int* owners) {
+    const int nt = lanczos_threads(threads, precision);
+    if (precision == SGW_PREC_DF32) return lanczos_capacity_df(P, nshift, nt, owners);
+    if (precision == SGW_PREC_FP32) return lanczos_capacity_f32(P, nshift, nt, owners);
+    return lanczos_capacity_f64(P, nshift, nt, owners);
+}
+
+cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int owners, int precision, int threads,
+                           cudaStream_t st) {
+    const int nt = lanczos_threads(threads, precision);
+    if (precision == SGW_PREC_DF32) return lanczos_launch_df(P, a, owners, nt, st);
+    if (precision == SGW_PREC_FP32) return lanczos_launch_f32(P, a, owners, nt, st);
+    return lanczos_launch_f64(P, a, owners, nt, st);
+}
 
 }  // namespace sgw

@@ -19,7 +19,6 @@
 #include "sgw_internal.cuh"
 
 namespace sgw {
-const void* residual_kernel_ptr();
 sgw_status noalloc_fail(sgw_status s, const char* msg);
 sgw_status noalloc_plan(const sgw_system* sys, const Plan** plan, int* dev);
 }  // namespace sgw
@@ -28,7 +27,7 @@ using namespace sgw;
 
 namespace {
 
-// 4 MiB of scratch: 2 * n_pw complex values per CTA.
+// 4 MiB of scratch: 2 * n_pw complex values per vector owner (a CTA, or a cluster).
 constexpr size_t kScratchElems = SGW_NOALLOC_SCRATCH_BYTES / sizeof(double2);
 static __device__ __align__(256) double2 g_scratch[kScratchElems];
 
@@ -112,13 +111,15 @@ extern "C" sgw_status sgw_residual_noalloc(sgw_system* sys, int nrhs, const void
         }
         scratch = g_scratch_ptr[dev];
     }
-    int grid = 0;
-    e = resident_grid(residual_kernel_ptr(), apply_smem_bytes(*P), &grid, kResThreads);
+    // owners: CTAs, or clusters of CTAs when the box is split over a cluster; each takes
+    // 2 n_pw scratch values
+    int owners = 0;
+    e = residual_owners(*P, SGW_PREC_FP64, &owners);
     if (e != cudaSuccess) return noalloc_fail(SGW_ECUDA, cudaGetErrorString(e));
-    grid = (int)std::min<size_t>({(size_t)grid, kScratchElems / per_cta, np});
+    owners = (int)std::min<size_t>({(size_t)owners, kScratchElems / per_cta, np});
     // The kernel writes every scratch element it reads before reading it: nothing to clear.
     e = launch_residual(*P, nrhs, nomega, nullptr, 0, (const double2*)rhs, e_ref, omega, eta, (const double2*)dpsi,
-                        scratch, rel_res, cert, nullptr, grid, (cudaStream_t)stream);
+                        scratch, rel_res, cert, nullptr, owners, (cudaStream_t)stream);
     if (e != cudaSuccess) return noalloc_fail(SGW_ECUDA, cudaGetErrorString(e));
     return SGW_OK;
 }

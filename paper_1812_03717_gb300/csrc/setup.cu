@@ -197,6 +197,18 @@ cudaError_t launch_to_dd(const double* src, size_t n, float2* dst, cudaStream_t 
     to_dd_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, n, dst);
     return cudaGetLastError();
 }
+// Each FP64 value rounded to FP32 (the single-precision policy's copies of T, beta, psi).
+__global__ void to_f32_kernel(const double* __restrict__ src, size_t n, float* __restrict__ dst) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = __double2float_rn(src[i]);
+}
+
+cudaError_t launch_to_f32(const double* src, size_t n, float* dst, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+    to_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, n, dst);
+    return cudaGetLastError();
+}
 cudaError_t launch_gram(const double2* psi, int nocc, int npw, double2* S, cudaStream_t st) {
     gram_kernel<<<nocc * nocc, kThreads, 0, st>>>(psi, nocc, npw, S);
     return cudaGetLastError();

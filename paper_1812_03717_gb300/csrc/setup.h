@@ -103,24 +103,45 @@ struct LanczosArgs {
     // Im z_rj: eta_r[r] when given, else eta_s[j] when given, else eta (any sign but 0)
     const double* eta_s = nullptr;   // [nshift]
     const double* eta_r = nullptr;   // [nrhs]
+    double cert_tol = 0.0;           // > 0: shifts also stop only once |r| / (|Im z| |x|) <= cert_tol
 };
 
-int lanczos_smem_bytes(const Plan& P, int nshift);
-cudaError_t lanczos_grid(const Plan& P, int nshift, int nrhs, int threads, int* grid);
-cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int grid, int precision, int threads,
+// Bytes per complex value of a precision's arithmetic policy.
+inline int prec_bytes(int precision) { return precision == SGW_PREC_FP32 ? 8 : 16; }
+
+// Launch plumbing shared by the kernels that own one vector per CTA or per cluster.
+int optin_smem();
+cudaError_t allow_max_smem(const void* kernel);
+Plan tuned_plan(const Plan& P, int extra, int es);
+cudaError_t owner_capacity(const void* kernel, const Plan& P, int threads, int smem, int* owners);
+cudaError_t launch_owned(const void* kernel, const Plan& P, int owners, int threads, int smem, cudaStream_t st,
+                         void** args);
+
+// Multishift Lanczos in the policy of `precision`; owners = right-hand sides in flight (CTAs
+// or clusters); threads 0 -> the default CTA size of the policy.
+int lanczos_threads(int requested, int precision);
+int lanczos_smem_bytes(const Plan& P, int nshift, int precision);
+cudaError_t lanczos_capacity(const Plan& P, int nshift, int threads, int precision, int* owners);
+cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int owners, int precision, int threads,
                            cudaStream_t st);
 int solve_smem_bytes(const Plan& P, int nshift);
-int apply_smem_bytes(const Plan& P);
+int apply_smem_bytes(const Plan& P, int es);
 cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid);
 cudaError_t launch_solve(const Plan& P, const SolveArgs& a, int grid, cudaStream_t st);
+cudaError_t apply_owners(const Plan& P, int precision, int* owners);
+// scratch: 2 n_pw complex128 slots per owner
 cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, const double2* z, int project,
-                         double2* scratch, int grid, int precision, cudaStream_t st);
+                         double2* scratch, int owners, int precision, cudaStream_t st);
 // Im z_rj = eta_s[j] when eta_s is given, else eta; the certificate divides by |Im z|;
-// bvec [nrhs][npw] = -P_c rhs when given (else the kernel projects rhs itself).
+// bvec [nrhs][npw] = -P_c rhs when given (else the kernel projects rhs itself).  precision
+// selects the arithmetic of the H application inside (FP64, else float-float); scratch:
+// 2 n_pw complex128 slots per owner.
+cudaError_t residual_owners(const Plan& P, int precision, int* owners);
 cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
-                            double* rel, double* cert, double2* store, int grid, cudaStream_t st,
-                            const double* eta_s = nullptr, const double2* bvec = nullptr);
+                            double* rel, double* cert, double2* store, int owners, cudaStream_t st,
+                            const double* eta_s = nullptr, const double2* bvec = nullptr,
+                            int precision = SGW_PREC_FP64);
 // b[r] = -P_c rhs[r] (FP64) for r < nrhs; a precomputed bvec lets the residual kernel skip it.
 cudaError_t launch_project_rhs(const Plan& P, int nrhs, const double2* rhs, double2* b, cudaStream_t st);
 // dn[po][pi][j] += weight sum_v sum_g conj(R[v n_p + po][g]) (X[v n_p + pi][j][g] + X[v n_p + pi][nw + j][g])
@@ -141,5 +162,6 @@ cudaError_t launch_aaa(int nfun, int m, const double2* z, const double2* f, doub
 cudaError_t launch_unit_rhs(const int* cols, int ncol, int npw, double2* rhs, cudaStream_t st);
 cudaError_t launch_pair_axpy(int nlist, const int* list, int npw, const double2* d, double2* x, cudaStream_t st);
 cudaError_t resident_grid(const void* kernel, int smem, int* grid, int threads = kThreads);
+cudaError_t launch_to_f32(const double* src, size_t n, float* dst, cudaStream_t st);
 
 }  // namespace sgw

@@ -10,18 +10,27 @@
 //   KB projectors           [nproj][npw]             <k+G|beta_p>
 //   occupied states         [nocc][npw]              psi_v of the basis (Eq. 7-8)
 //
-// One CTA owns one whole vector during an H application (Sec. 2.1: kinetic and non-local
-// parts in reciprocal space, V_loc in real space through the FFT).  The whole pruned box
-// of that vector -- only the z-columns ("sticks") through the sphere, plus one xy-plane
-// at a time -- lives in shared memory, so an application reads x once and writes y once.
+// One CTA, or one thread-block cluster of P.csize CTAs, owns one whole vector during an H
+// application (Sec. 2.1: kinetic and non-local parts in reciprocal space, V_loc in real space
+// through the FFT).  The whole pruned box of that vector -- only the z-columns ("sticks")
+// through the sphere, plus a few xy-planes at a time -- lives in shared memory, so an
+// application reads x once and writes y once.  In a cluster, rank r holds the sticks
+// [s0, s1) and owns the plane waves of those sticks, [g0, g1) (a contiguous range: the G of one
+// stick are consecutive in canonical order); it transforms the xy-planes [z0, z1), gathering
+// each plane's stick elements from the other ranks' shared memory (distributed shared memory)
+// and scattering the result back.  Dot products over the vector are summed over the cluster
+// in rank order, so every rank holds bit-identical scalars.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
 #include "sgw.h"
 
 namespace sgw {
+
+namespace cg = cooperative_groups;
 
 constexpr int kThreads = 256;          // threads per CTA of the library kernels
 constexpr int kResThreads = 384;       // threads per CTA of the FP64 true-residual kernel
@@ -30,6 +39,7 @@ constexpr int kMaxStages = 12;         // radix stages per axis (N <= 5^12)
 constexpr int kMaxShifts = 512;        // frequencies per solve
 constexpr int kMaxEll = 4;             // BiCGstab(ell)
 constexpr int kRedSlots = 16;          // complex values reduced per block reduction
+constexpr int kMaxCluster = 16;        // CTAs sharing one vector's box (16 needs the non-portable size)
 
 struct AxisPlan {
     int n;
@@ -64,26 +74,95 @@ struct Plan {
     const float4* psi_dd;    // [nocc][npw]
     const float4* beta_dd;   // [nproj][npw]
     const float2* kin_dd;    // [npw]
+    // FP32 mirrors used by the single-precision policy
+    const float* vloc_f;     // [n3][n1][n2p]
+    const float2* psi_f;     // [nocc][npw]
+    const float2* beta_f;    // [nproj][npw]
+    const float* kin_f;      // [npw]
+    // cluster split of the box (csize == 1: one CTA holds it all)
+    int csize;               // CTAs per vector
+    int nstick_loc;          // most sticks one rank holds (sizes the stick buffer)
+    const int* part;         // [2][kMaxCluster + 1]: plane-wave bounds g_r, then stick bounds s_r
+    const int* stick_loc;    // [nstick] (owner rank << 16) | index of the stick in its owner's buffer
 };
 
 // Shared-memory carve-up of an H application (byte offsets from the dynamic base).
 struct ApplySmem {
-    int tw, sticks, plane, red, coef, end;
+    int tw, sticks, plane, red, coef, coefc, part, end;
 };
 
 inline __host__ __device__ int align16(int b) { return (b + 15) & ~15; }
 
-inline __host__ __device__ ApplySmem apply_smem_layout(const Plan& p) {
+// Complex values per parity buffer of the cluster partial sums (and of the coefficient slots).
+inline __host__ __device__ int coef_slots(const Plan& p) {
+    int nc = p.nocc > p.nproj ? p.nocc : p.nproj;
+    if (nc < kRedSlots) nc = kRedSlots;
+    return (nc + 7) / 8 * 8 + 8;
+}
+
+// es: bytes per complex value of the arithmetic policy (16 FP64 / float-float, 8 FP32).
+inline __host__ __device__ ApplySmem apply_smem_layout(const Plan& p, int es) {
     ApplySmem s;
     int off = 0;
-    s.tw = off;     off = align16(off + (p.n1 + p.n2 + p.n3) * 16);
-    s.sticks = off; off = align16(off + p.nstick * p.n3p * 16);
-    s.plane = off;  off = align16(off + p.nplanes * p.n1 * p.n2p * 16);
+    const int ns = coef_slots(p);
+    s.tw = off;     off = align16(off + (p.n1 + p.n2 + p.n3) * es);
+    s.sticks = off; off = align16(off + p.nstick_loc * p.n3p * es);
+    s.plane = off;  off = align16(off + p.nplanes * p.n1 * p.n2p * es);
     s.red = off;    off = align16(off + (kMaxThreads / 32) * kRedSlots * 16);
-    int nc = p.nocc > p.nproj ? p.nocc : p.nproj;
-    s.coef = off;   off = align16(off + ((nc + 7) / 8 * 8 + 8) * 16);
+    s.coef = off;   off = align16(off + ns * 16);
+    s.coefc = off;  off = align16(off + ns * es);
+    s.part = off;   off = align16(off + (p.csize > 1 ? 2 * ns * 16 : 0));
     s.end = off;
     return s;
+}
+
+// Shared memory of the Lanczos kernel's per-shift state after the H application's carve-up.
+inline __host__ __device__ int lanczos_extra(int ns) {
+    return 3 * align16(ns * 16) + 3 * align16(ns * 8) + 2 * align16(ns * 4);
+}
+
+// The part of a vector one CTA works on: rank `rank` of the cluster owns the plane waves
+// [g0, g1) and holds the sticks [s0, s1) (the whole vector when P.csize == 1).
+struct Part {
+    int rank, g0, g1, s0, s1;
+};
+
+__device__ __forceinline__ Part make_part(const Plan& P) {
+    Part q;
+    if (P.csize > 1) {
+        q.rank = (int)cg::this_cluster().block_rank();
+        q.g0 = P.part[q.rank];
+        q.g1 = P.part[q.rank + 1];
+        q.s0 = P.part[kMaxCluster + 1 + q.rank];
+        q.s1 = P.part[kMaxCluster + 2 + q.rank];
+    } else {
+        q.rank = 0;
+        q.g0 = 0;
+        q.g1 = P.npw;
+        q.s0 = 0;
+        q.s1 = P.nstick;
+    }
+    return q;
+}
+
+// Scratch of the block and cluster reductions.  Cluster partial sums alternate between two
+// buffers (par), so one cluster barrier per reduction suffices: a rank writes buffer par of
+// reduction n + 2 only after the barrier of reduction n + 1, which every rank reaches after
+// reading the buffers of reduction n.
+struct Red {
+    double2* red;     // per-warp slots of block_sum
+    double2* part;    // [2][stride] this CTA's partial sums (clusters only)
+    int stride;
+    int par;
+};
+
+__device__ __forceinline__ Red make_red(const Plan& P, unsigned char* smem, const ApplySmem& L) {
+    Red R;
+    R.red = reinterpret_cast<double2*>(smem + L.red);
+    R.part = reinterpret_cast<double2*>(smem + L.part);
+    R.stride = coef_slots(P);
+    R.par = 0;
+    return R;
 }
 
 // ----------------------------------------------------------------------- complex helpers
@@ -296,6 +375,37 @@ struct ArDF {
     }
 };
 
+// Single precision: complex64 values, FP32 arithmetic and accumulation.
+struct ArF32 {
+    using C = float2;
+    static __device__ __forceinline__ C add(C a, C b) { return make_float2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ C sub(C a, C b) { return make_float2(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ C mul(C a, C b) {
+        return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+    }
+    static __device__ __forceinline__ C conj(C a) { return make_float2(a.x, -a.y); }
+    template <int SIGN>
+    static __device__ __forceinline__ C muli(C a) { return make_float2(-SIGN * a.y, SIGN * a.x); }
+    static __device__ __forceinline__ C scal(C a, double, float ch, float) { return make_float2(a.x * ch, a.y * ch); }
+    static __device__ __forceinline__ C from_d(double2 a) {
+        return make_float2(__double2float_rn(a.x), __double2float_rn(a.y));
+    }
+    static __device__ __forceinline__ double2 to_d(C a) { return make_double2((double)a.x, (double)a.y); }
+    static __device__ __forceinline__ C zero() { return make_float2(0.f, 0.f); }
+    using VT = float;
+    static __device__ __forceinline__ VT vload(const Plan& P, size_t i) { return P.vloc_f[i]; }
+    static __device__ __forceinline__ C vmul(C a, VT v) { return make_float2(a.x * v, a.y * v); }
+    using R = float;
+    static __device__ __forceinline__ R real(double x) { return __double2float_rn(x); }
+    static __device__ __forceinline__ C scalr(C a, R s) { return make_float2(a.x * s, a.y * s); }
+    static __device__ __forceinline__ C psi(const Plan& P, size_t i) { return P.psi_f[i]; }
+    static __device__ __forceinline__ C beta(const Plan& P, size_t i) { return P.beta_f[i]; }
+    static __device__ __forceinline__ C kinx(const Plan& P, int g, C x) { return scalr(x, P.kin_f[g]); }
+    static __device__ __forceinline__ C acc_norm(C acc, C a) {
+        return make_float2(fmaf(a.x, a.x, fmaf(a.y, a.y, acc.x)), acc.y);
+    }
+};
+
 // Real constants of the small DFTs as (double, float hi, float lo).
 #define SGW_CONST(name, val)                                      \
     constexpr double name##_d = val;                              \
@@ -346,20 +456,74 @@ __device__ __forceinline__ void block_sum_c(float4 (&v)[NV], double2* red, doubl
     __syncthreads();
 }
 
-// out[v] = sum_g conj(src_v[g]) x[g] for v < nv, with src the occupied states (which = 0) or
-// the projectors (which = 1) in the policy's format; per-thread sums in the policy's
-// arithmetic, the block reduction by block_sum_c.  out must hold nv rounded up to 8.
+// FP32 complex values: warp sums in FP32, per-warp partials summed in FP64.
+template <int NV>
+__device__ __forceinline__ void block_sum_c(float2 (&v)[NV], double2* red, double2* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[i].x += __shfl_down_sync(0xffffffffu, v[i].x, o);
+            v[i].y += __shfl_down_sync(0xffffffffu, v[i].y, o);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) red[warp * kRedSlots + i] = make_double2((double)v[i].x, (double)v[i].y);
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double2 s = cz();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[w * kRedSlots + threadIdx.x]);
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// out[0..n) = sum over the ranks of the cluster, in rank order, of each rank's loc[0..n)
+// (loc: the same shared-memory offset on every rank).  Every rank gets bit-identical sums.
+__device__ __forceinline__ void cluster_combine(const Plan& P, const double2* loc, int n, double2* out) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 s = cz();
+        for (int r = 0; r < P.csize; ++r) s = cadd(s, cl.map_shared_rank(loc, (unsigned)r)[i]);
+        out[i] = s;
+    }
+    __syncthreads();
+}
+
+// Sums NV complex values per thread over the vector's owners (the CTA, or the cluster) into
+// out[0..NV) (shared memory of this CTA).  All threads of every rank call.
+template <int NV, class T>
+__device__ __forceinline__ void part_sum(const Plan& P, Red& R, T (&v)[NV], double2* out) {
+    if (P.csize == 1) {
+        block_sum_c<NV>(v, R.red, out);
+        return;
+    }
+    double2* loc = R.part + R.par * R.stride;
+    R.par ^= 1;
+    block_sum_c<NV>(v, R.red, loc);
+    cluster_combine(P, loc, NV, out);
+}
+
+// out[v] = sum_g conj(src_v[g]) x[g] for v < nv over the plane waves of the vector's owners,
+// with src the occupied states (WHICH = 0) or the projectors (WHICH = 1) in the policy's
+// format; per-thread sums in the policy's arithmetic, the block reduction by block_sum_c, the
+// cluster sum in FP64.  out must hold nv rounded up to 8.
 template <class Ar, int WHICH>
-__device__ __forceinline__ void block_dots_ar(const Plan& P, int nv, const typename Ar::C* x, double2* red,
-                                              double2* out) {
+__device__ __forceinline__ void part_dots(const Plan& P, const Part& q, Red& R, int nv, const typename Ar::C* x,
+                                          double2* out) {
     using C = typename Ar::C;
     const int n = P.npw;
+    double2* dst = P.csize == 1 ? out : R.part + R.par * R.stride;
     for (int v0 = 0; v0 < nv; v0 += 8) {
         C acc[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc[i] = Ar::zero();
         const int cnt = min(8, nv - v0);
-        for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        for (int g = q.g0 + threadIdx.x; g < q.g1; g += blockDim.x) {
             const C xv = x[g];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -370,7 +534,34 @@ __device__ __forceinline__ void block_dots_ar(const Plan& P, int nv, const typen
                 }
             }
         }
-        block_sum_c<8>(acc, red, out + v0);
+        block_sum_c<8>(acc, R.red, dst + v0);
+    }
+    if (P.csize > 1) {
+        R.par ^= 1;
+        cluster_combine(P, dst, nv, out);
+    }
+}
+
+// FP64 dots out[v] = sum_g conj(V[v ld + g]) x[g] over the owners' plane waves (V: FP64 rows).
+__device__ __forceinline__ void part_dots_f64(const Plan& P, const Part& q, Red& R, const double2* V, int nv, int ld,
+                                              const double2* x, double2* out) {
+    double2* dst = P.csize == 1 ? out : R.part + R.par * R.stride;
+    for (int v0 = 0; v0 < nv; v0 += 8) {
+        double2 acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = cz();
+        const int cnt = min(8, nv - v0);
+        for (int g = q.g0 + threadIdx.x; g < q.g1; g += blockDim.x) {
+            const double2 xv = x[g];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < cnt) acc[i] = cadd(acc[i], cmulc(V[(size_t)(v0 + i) * ld + g], xv));
+        }
+        block_sum<8>(acc, R.red, dst + v0);
+    }
+    if (P.csize > 1) {
+        R.par ^= 1;
+        cluster_combine(P, dst, nv, out);
     }
 }
 
@@ -637,66 +828,79 @@ enum : int {
 // Loads the twiddle tables of the plan into shared memory (call once per kernel).
 template <class Ar>
 __device__ __forceinline__ void load_twiddles(const Plan& P, unsigned char* smem) {
-    const ApplySmem L = apply_smem_layout(P);
+    const ApplySmem L = apply_smem_layout(P, (int)sizeof(typename Ar::C));
     typename Ar::C* tw = reinterpret_cast<typename Ar::C*>(smem + L.tw);
     for (int i = threadIdx.x; i < P.n1 + P.n2 + P.n3; i += blockDim.x) tw[i] = Ar::from_d(P.twid[i]);
     __syncthreads();
 }
 
-// y = H x  (+ options) for one vector, by the whole CTA; x and y are vectors of the
-// policy's type (global, must not alias).  Steps: KB coefficients c_p = <beta_p|x>; scatter
-// x into the sticks; inverse FFT along z on the sticks; per group of z-planes: scatter the
-// planes, inverse FFT along y (only the x-columns that hold sticks) and x, multiply by V(r),
-// forward FFT along x and y, gather back into the sticks; forward FFT along z; gather the
-// (the inverse FFTs leave real space permuted along each axis -- digit-reversed or in the
-// prime-factor order -- where V is stored in the same order; the forward FFTs return to
-// natural order, so the permutation costs nothing);
+// y = H x  (+ options) for one vector, by the CTA or the cluster that owns it (each rank
+// reads and writes only its own plane waves [q.g0, q.g1) of x and y); x and y are vectors of
+// the policy's type (global, must not alias).  Steps: KB coefficients c_p = <beta_p|x>;
+// scatter x into the sticks; inverse FFT along z on the sticks; per group of z-planes (this
+// rank's planes): gather the planes' stick elements (from every rank's shared memory in a
+// cluster), inverse FFT along y (only the x-columns that hold sticks) and x, multiply by V(r),
+// forward FFT along x and y, scatter back into the sticks; forward FFT along z; gather the
 // sphere, scale by 1/N^3 and add T_G x_G + sum_p D_p c_p beta_p(G); optionally project with
-// P_c and subtract z x.  All vector arithmetic in the policy's arithmetic; the block
-// reductions of the projections in FP64.
+// P_c and subtract z x.  (The inverse FFTs leave real space permuted along each axis --
+// digit-reversed or in the prime-factor order -- where V is stored in the same order; the
+// forward FFTs return to natural order, so the permutation costs nothing.)  All vector
+// arithmetic in the policy's arithmetic; the reductions of the projections in FP64.
 // x and y may have been written earlier in the same kernel, so they are read through the
 // coherent path (no __restrict__ / read-only cache).
 template <class Ar>
-__device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, const typename Ar::C* x,
-                                           typename Ar::C* y, double2 zsh, int mode) {
+__device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, const Part& q, Red& R,
+                                           const typename Ar::C* x, typename Ar::C* y, double2 zsh, int mode) {
     using C = typename Ar::C;
-    const ApplySmem L = apply_smem_layout(P);
+    const ApplySmem L = apply_smem_layout(P, (int)sizeof(C));
     const C* tw = reinterpret_cast<const C*>(smem + L.tw);
     C* sticks = reinterpret_cast<C*>(smem + L.sticks);
     C* plane = reinterpret_cast<C*>(smem + L.plane);
-    double2* red = reinterpret_cast<double2*>(smem + L.red);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
-    C* coefc = reinterpret_cast<C*>(smem + L.coef);   // the same slots, in the policy's format
+    C* coefc = reinterpret_cast<C*>(smem + L.coefc);   // the coefficients in the policy's format
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n1 = P.n1, n2 = P.n2, n3 = P.n3, npw = P.npw, nst = P.nstick;
+    const int g0 = q.g0, g1 = q.g1, nsl = q.s1 - q.s0;
     const C* tw1 = tw;
     const C* tw2 = tw + n1;
     const C* tw3 = tw + n1 + n2;
 
     // non-local: D_p <beta_p|x>, kept in the policy's format
     if (P.nproj > 0) {
-        block_dots_ar<Ar, 1>(P, P.nproj, x, red, coef);
+        part_dots<Ar, 1>(P, q, R, P.nproj, x, coef);
         if (tid < P.nproj) coefc[tid] = Ar::from_d(cscal(coef[tid], P.dkb[tid]));
         __syncthreads();
     }
 
-    // sphere -> sticks
+    // sphere -> this rank's sticks
     const int n3p = P.n3p;
-    for (int i = tid; i < nst * n3p; i += nt) sticks[i] = Ar::zero();
+    for (int i = tid; i < nsl * n3p; i += nt) sticks[i] = Ar::zero();
     __syncthreads();
-    for (int g = tid; g < npw; g += nt) sticks[P.g2s[g]] = x[g];
+    for (int g = g0 + tid; g < g1; g += nt) sticks[P.g2s[g]] = x[g];
     __syncthreads();
-    fft_inplace<Ar, +1, true>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
+    fft_inplace<Ar, +1, true>(sticks, nsl, nsl, 0, nullptr, n3p, 1, P.ax[2], tw3);
+    if (P.csize > 1) cg::this_cluster().sync();   // every rank's sticks transformed
 
-    // nplanes xy-planes per pass: one set of barriers serves all of them
+    // this rank's xy-planes, nplanes per pass: one set of barriers serves all of them
     const int n2p = P.n2p, psz = n1 * n2p;
-    for (int iz0 = 0; iz0 < n3; iz0 += P.nplanes) {
-        const int npl = min(P.nplanes, n3 - iz0);
+    const int z0 = q.rank * n3 / P.csize, z1 = (q.rank + 1) * n3 / P.csize;
+    for (int iz0 = z0; iz0 < z1; iz0 += P.nplanes) {
+        const int npl = min(P.nplanes, z1 - iz0);
         for (int i = tid; i < npl * psz; i += nt) plane[i] = Ar::zero();
         __syncthreads();
-        for (int i = tid; i < npl * nst; i += nt) {
-            const int pl = i / nst, s = i - pl * nst;
-            plane[pl * psz + P.stick_xy[s]] = sticks[s * n3p + iz0 + pl];
+        if (P.csize == 1) {
+            for (int i = tid; i < npl * nst; i += nt) {
+                const int pl = i / nst, s = i - pl * nst;
+                plane[pl * psz + P.stick_xy[s]] = sticks[s * n3p + iz0 + pl];
+            }
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            for (int i = tid; i < npl * nst; i += nt) {
+                const int pl = i / nst, s = i - pl * nst;
+                const int loc = P.stick_loc[s];
+                const C* src = cl.map_shared_rank(sticks, (unsigned)(loc >> 16));
+                plane[pl * psz + P.stick_xy[s]] = src[(loc & 0xffff) * n3p + iz0 + pl];
+            }
         }
         __syncthreads();
         fft_inplace<Ar, +1, true>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);  // y, occupied x
@@ -717,18 +921,29 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
         __syncthreads();
         fft_inplace<Ar, -1, false>(plane, npl * n2, n2, psz, nullptr, 1, n2p, P.ax[0], tw1);
         fft_inplace<Ar, -1, false>(plane, npl * P.nxcol, P.nxcol, psz, P.xbase, 0, 1, P.ax[1], tw2);
-        for (int i = tid; i < npl * nst; i += nt) {
-            const int pl = i / nst, s = i - pl * nst;
-            sticks[s * n3p + iz0 + pl] = plane[pl * psz + P.stick_xy[s]];
+        if (P.csize == 1) {
+            for (int i = tid; i < npl * nst; i += nt) {
+                const int pl = i / nst, s = i - pl * nst;
+                sticks[s * n3p + iz0 + pl] = plane[pl * psz + P.stick_xy[s]];
+            }
+        } else {
+            cg::cluster_group cl = cg::this_cluster();
+            for (int i = tid; i < npl * nst; i += nt) {
+                const int pl = i / nst, s = i - pl * nst;
+                const int loc = P.stick_loc[s];
+                C* dst = cl.map_shared_rank(sticks, (unsigned)(loc >> 16));
+                dst[(loc & 0xffff) * n3p + iz0 + pl] = plane[pl * psz + P.stick_xy[s]];
+            }
         }
         __syncthreads();
     }
-    fft_inplace<Ar, -1, false>(sticks, nst, nst, 0, nullptr, n3p, 1, P.ax[2], tw3);
+    if (P.csize > 1) cg::this_cluster().sync();   // every plane scattered back
+    fft_inplace<Ar, -1, false>(sticks, nsl, nsl, 0, nullptr, n3p, 1, P.ax[2], tw3);
 
     // gather + kinetic + non-local
     {
         const typename Ar::R invn = Ar::real(P.inv_nbox);
-        for (int g = tid; g < npw; g += nt) {
+        for (int g = g0 + tid; g < g1; g += nt) {
             C h = Ar::add(Ar::scalr(sticks[P.g2s[g]], invn), Ar::kinx(P, g, x[g]));
             for (int p = 0; p < P.nproj; ++p) h = Ar::add(h, Ar::mul(coefc[p], Ar::beta(P, (size_t)p * npw + g)));
             y[g] = h;
@@ -737,11 +952,11 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
     __syncthreads();
 
     if (mode & APPLY_PROJ_OUT) {
-        block_dots_ar<Ar, 0>(P, P.nocc, y, red, coef);
+        part_dots<Ar, 0>(P, q, R, P.nocc, y, coef);
         for (int v = tid; v < P.nocc; v += nt) coefc[v] = Ar::from_d(coef[v]);
         __syncthreads();
         const C zc = Ar::from_d(zsh);
-        for (int g = tid; g < npw; g += nt) {
+        for (int g = g0 + tid; g < g1; g += nt) {
             C h = y[g];
             for (int v = 0; v < P.nocc; ++v) h = Ar::sub(h, Ar::mul(coefc[v], Ar::psi(P, (size_t)v * npw + g)));
             if (mode & APPLY_SUB_Z) h = Ar::sub(h, Ar::mul(zc, x[g]));
@@ -749,7 +964,7 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
         }
     } else if (mode & APPLY_SUB_Z) {
         const C zc = Ar::from_d(zsh);
-        for (int g = tid; g < npw; g += nt) y[g] = Ar::sub(y[g], Ar::mul(zc, x[g]));
+        for (int g = g0 + tid; g < g1; g += nt) y[g] = Ar::sub(y[g], Ar::mul(zc, x[g]));
     }
     __syncthreads();
 }

@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(_PKG, "libsgw.so")
 SGW_OK, SGW_EINVAL, SGW_ENOMEM, SGW_ECUDA, SGW_ENOCONV, SGW_EALIAS, SGW_ESTATE, SGW_EUNSUPPORTED = range(8)
 PAIR_CONVERGED, PAIR_MAXITER, PAIR_BREAKDOWN, PAIR_NONFINITE = range(4)
 METHOD_LANCZOS, METHOD_BICGSTAB = range(2)
-PREC_FP64, PREC_DF32 = range(2)
-_PREC = {"fp64": PREC_FP64, "df32": PREC_DF32}
+PREC_FP64, PREC_DF32, PREC_FP32 = range(3)
+_PREC = {"fp64": PREC_FP64, "df32": PREC_DF32, "fp32": PREC_FP32}
 STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV", "SGW_EALIAS", "SGW_ESTATE",
                 "SGW_EUNSUPPORTED"]
 
-EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_occupied", "sgw_make_rhs",
+EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_split", "sgw_get_split",
+           "sgw_set_occupied", "sgw_make_rhs",
            "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_density_response_w", "sgw_aaa", "sgw_screened_coulomb", "sgw_residual", "sgw_residual_noalloc",
            "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
            "sgw_mlp_forward", "sgw_mlp_grad", "sgw_mlp_train_step", "sgw_mlp_destroy", "sgw_destroy_system",
@@ -49,14 +50,33 @@ class _KB(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("method", ctypes.c_int), ("precision", ctypes.c_int), ("ell", ctypes.c_int), ("seed_index", ctypes.c_int), ("max_matvec", ctypes.c_int),
-                ("max_refine", ctypes.c_int), ("threads", ctypes.c_int), ("stream", ctypes.c_void_p)]
+    _fields_ = [("method", ctypes.c_int), ("precision", ctypes.c_int), ("ell", ctypes.c_int),
+                ("seed_index", ctypes.c_int), ("max_matvec", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("threads", ctypes.c_int), ("stream", ctypes.c_void_p), ("cert_tol", ctypes.c_double),
+                ("x0", ctypes.c_void_p), ("precond", ctypes.c_int), ("mlp", ctypes.c_void_p),
+                ("plain_budget", ctypes.c_int)]
+
+
+def _opts(method=0, precision=0, ell=4, seed_index=-1, max_matvec=0, max_refine=0, threads=0, stream=None,
+          cert_tol=0.0, x0=None, precond=0, mlp=None, plain_budget=0):
+    return _Opts(method, precision, ell, seed_index, max_matvec, max_refine, threads, stream, cert_tol, x0,
+                 precond, mlp, plain_budget)
+
+
+_REPORT_KEYS = ("matvecs", "est_res", "rel_res", "cert", "status", "launches", "kernel_ms", "fallbacks")
 
 
 class _Report(ctypes.Structure):
-    _fields_ = [("matvecs", ctypes.c_void_p), ("est_res", ctypes.c_void_p), ("rel_res", ctypes.c_void_p),
-                ("cert", ctypes.c_void_p), ("status", ctypes.c_void_p), ("launches", ctypes.c_void_p),
-                ("kernel_ms", ctypes.c_void_p)]
+    _fields_ = [(k, ctypes.c_void_p) for k in _REPORT_KEYS]
+
+
+def _report(nr, nw):
+    """Per-pair report arrays [nr][nw] (nw None: [nr]) and the ctypes struct pointing at them."""
+    shp = (nr,) if nw is None else (nr, nw)
+    rep = {"matvecs": np.zeros(shp, dtype=np.int32), "est_res": np.zeros(shp), "rel_res": np.zeros(shp),
+           "cert": np.zeros(shp), "status": np.zeros(shp, dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
+           "kernel_ms": np.zeros(1), "fallbacks": np.zeros(1, dtype=np.int32)}
+    return rep, _Report(*(rep[k].ctypes.data for k in _REPORT_KEYS))
 
 
 _lib = None
@@ -74,6 +94,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_create_system.argtypes = [ctypes.POINTER(_Cell), dp, vp, vp, vp, ctypes.POINTER(_KB), ctypes.POINTER(vp)]
     lib.sgw_get_gvectors.argtypes = [vp, vp, vp, vp]
     lib.sgw_get_box_map.argtypes = [vp, vp]
+    lib.sgw_set_split.argtypes = [vp, ip]
+    lib.sgw_get_split.argtypes = [vp, vp, vp]
     lib.sgw_set_occupied.argtypes = [vp, ip, vp, vp]
     lib.sgw_make_rhs.argtypes = [vp, vp, ip, vp, ip, vp, vp, vp]
     lib.sgw_apply_h.argtypes = [vp, ip, vp, vp, ip, vp]
@@ -250,6 +272,17 @@ class System:
         _check(load().sgw_get_box_map(self._h, m.ctypes.data))
         return m
 
+    def set_split(self, csize):
+        """Forces the cluster size of the on-chip box (0: automatic); returns split()."""
+        _check(load().sgw_set_split(self._h, int(csize)))
+        return self.split()
+
+    def split(self):
+        """(CTAs per vector for FP64 / float-float, for FP32) of the current box split."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(load().sgw_get_split(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def set_occupied(self, psi_v, eps_v):
         psi = _c128(psi_v)
         eps = np.ascontiguousarray(eps_v, dtype=np.float64)
@@ -285,8 +318,11 @@ class System:
         return out
 
     def solve_shifted(self, rhs, e_ref, omega, eta, tol=1e-10, method="lanczos", precision="fp64", ell=4, seed_index=-1, max_matvec=0,
-                      max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False):
-        """Returns (dpsi [nrhs][nomega][n_pw], report dict, converged flag)."""
+                      max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False, cert_tol=0.0, x0=None,
+                      precond="none", mlp=None, plain_budget=0):
+        """Returns (dpsi [nrhs][nomega][n_pw], report dict, converged flag).  cert_tol: certificate
+        target (0: the library default 1e-8, negative: not checked); x0: initial solutions like
+        dpsi (resume); precond: "none" / "plain" / "learned" for the per-shift corrections."""
         rhs = _c128(rhs)
         nrhs = rhs.shape[0]
         e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
@@ -294,22 +330,22 @@ class System:
         nw = len(omega)
         if out is None:
             out = _like(rhs, (nrhs, nw, self.n_pw))
-        rep = {"matvecs": np.zeros((nrhs, nw), dtype=np.int32), "est_res": np.zeros((nrhs, nw)),
-               "rel_res": np.zeros((nrhs, nw)), "cert": np.zeros((nrhs, nw)),
-               "status": np.zeros((nrhs, nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
-               "kernel_ms": np.zeros(1)}
+        if x0 is not None:
+            x0 = _c128(x0)
+            if tuple(x0.shape) != (nrhs, nw, self.n_pw):
+                raise ValueError("x0 must be [nrhs][nomega][n_pw]")
+        rep, crep = _report(nrhs, nw)
         m = {"lanczos": METHOD_LANCZOS, "bicgstab": METHOD_BICGSTAB}[method]
-        opts = _Opts(m, _PREC[precision], int(ell), int(seed_index), int(max_matvec), int(max_refine), int(threads),
-                     _stream_of(rhs, stream))
-        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
-                                                        "kernel_ms")))
+        opts = _opts(m, _PREC[precision], int(ell), int(seed_index), int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(rhs, stream), float(cert_tol), _ptr(x0) if x0 is not None else None,
+                     _PRECOND[precond], mlp._h if mlp is not None else None, int(plain_budget))
         s = load().sgw_solve_shifted(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data,
                                      float(eta), float(tol), ctypes.byref(opts), _ptr(out), ctypes.byref(crep))
         _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
         return out, rep, s == SGW_OK
 
     def solve_green(self, cols, z, tol=1e-10, precision="fp64", max_matvec=0, max_refine=0, threads=0, out=None,
-                    device=None, stream=None, raise_on_noconv=False):
+                    device=None, stream=None, raise_on_noconv=False, cert_tol=0.0):
         """Columns cols of G(z_j) = (z_j - H)^-1 (sgw_solve_green): returns (g [ncol][nz][n_pw], report
         dict, converged flag).  z: complex shifts with Im z != 0.  The result is a CUDA tensor when
         out is one or device is "cuda", else a numpy array."""
@@ -323,21 +359,16 @@ class System:
                 out = torch.empty((nc, nz, self.n_pw), dtype=torch.complex128, device=device)
             else:
                 out = np.empty((nc, nz, self.n_pw), dtype=np.complex128)
-        rep = {"matvecs": np.zeros((nc, nz), dtype=np.int32), "est_res": np.zeros((nc, nz)),
-               "rel_res": np.zeros((nc, nz)), "cert": np.zeros((nc, nz)),
-               "status": np.zeros((nc, nz), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
-               "kernel_ms": np.zeros(1)}
-        opts = _Opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
-                     _stream_of(out, stream))
-        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
-                                                        "kernel_ms")))
+        rep, crep = _report(nc, nz)
+        opts = _opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(out, stream), float(cert_tol))
         s = load().sgw_solve_green(self._h, nc, cols.ctypes.data, nz, zz.ctypes.data, float(tol), ctypes.byref(opts),
                                    _ptr(out), ctypes.byref(crep))
         _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
         return out, rep, s == SGW_OK
 
     def density_response(self, rhs, eps_v, omega, eta, weight=1.0, tol=1e-10, precision="fp64", max_matvec=0,
-                         max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False):
+                         max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False, cert_tol=0.0):
         """One k-point's contribution to Eq. 5 (sgw_density_response): rhs [n_v * n_pert][n_pw] from
         make_rhs, eps_v [n_v].  Accumulates into out [n_pert][n_pert][nomega] (zeros when None; a
         CUDA tensor stays on the device) and returns (out, report [n_v * n_pert][2 nomega], converged)."""
@@ -355,14 +386,9 @@ class System:
             else:
                 out = np.zeros((n_p, n_p, nw), dtype=np.complex128)
         nr = rhs.shape[0]
-        rep = {"matvecs": np.zeros((nr, 2 * nw), dtype=np.int32), "est_res": np.zeros((nr, 2 * nw)),
-               "rel_res": np.zeros((nr, 2 * nw)), "cert": np.zeros((nr, 2 * nw)),
-               "status": np.zeros((nr, 2 * nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
-               "kernel_ms": np.zeros(1)}
-        opts = _Opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
-                     _stream_of(rhs, stream))
-        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
-                                                        "kernel_ms")))
+        rep, crep = _report(nr, 2 * nw)
+        opts = _opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(rhs, stream), float(cert_tol))
         s = load().sgw_density_response(self._h, n_v, n_p, _ptr(rhs), eps_v.ctypes.data, nw, omega.ctypes.data,
                                         float(eta), float(weight), float(tol), ctypes.byref(opts), _ptr(out),
                                         ctypes.byref(crep))
@@ -370,7 +396,7 @@ class System:
         return out, rep, s == SGW_OK
 
     def density_response_w(self, rhs, eps_v, w, weight=1.0, tol=1e-10, precision="fp64", max_matvec=0,
-                           max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False):
+                           max_refine=0, threads=0, out=None, stream=None, raise_on_noconv=False, cert_tol=0.0):
         """sgw_density_response_w: as density_response at complex frequencies w (w = 1j * omega on
         the imaginary axis); returns (dn [n_pert][n_pert][nw], report, converged)."""
         rhs = _c128(rhs)
@@ -388,14 +414,9 @@ class System:
             else:
                 out = np.zeros((n_p, n_p, nw), dtype=np.complex128)
         nr = rhs.shape[0]
-        rep = {"matvecs": np.zeros((nr, 2 * nw), dtype=np.int32), "est_res": np.zeros((nr, 2 * nw)),
-               "rel_res": np.zeros((nr, 2 * nw)), "cert": np.zeros((nr, 2 * nw)),
-               "status": np.zeros((nr, 2 * nw), dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
-               "kernel_ms": np.zeros(1)}
-        opts = _Opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
-                     _stream_of(rhs, stream))
-        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
-                                                        "kernel_ms")))
+        rep, crep = _report(nr, 2 * nw)
+        opts = _opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
+                     _stream_of(rhs, stream), float(cert_tol))
         s = load().sgw_density_response_w(self._h, n_v, n_p, _ptr(rhs), eps_v.ctypes.data, nw, ww.ctypes.data,
                                           float(weight), float(tol), ctypes.byref(opts), _ptr(out), ctypes.byref(crep))
         _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
@@ -452,12 +473,8 @@ class System:
         dl = None if delta is None else np.ascontiguousarray(np.broadcast_to(delta, (n,)), dtype=np.float64)
         if out is None:
             out = _like(rhs, (n, self.n_pw))
-        rep = {"matvecs": np.zeros(n, dtype=np.int32), "est_res": np.zeros(n), "rel_res": np.zeros(n),
-               "cert": np.zeros(n), "status": np.zeros(n, dtype=np.int32), "launches": np.zeros(1, dtype=np.int32),
-               "kernel_ms": np.zeros(1)}
-        opts = _Opts(METHOD_BICGSTAB, PREC_FP64, int(ell), -1, int(max_matvec), -1, 0, _stream_of(rhs, stream))
-        crep = _Report(*(rep[k].ctypes.data for k in ("matvecs", "est_res", "rel_res", "cert", "status", "launches",
-                                                        "kernel_ms")))
+        rep, crep = _report(n, None)
+        opts = _opts(METHOD_BICGSTAB, PREC_FP64, int(ell), -1, int(max_matvec), -1, 0, _stream_of(rhs, stream))
         st = load().sgw_solve_pershift(self._h, n, _ptr(rhs), e_ref.ctypes.data, omega.ctypes.data, float(eta),
                                        float(tol), _PRECOND[precond], dl.ctypes.data if dl is not None else None,
                                        mlp._h if mlp is not None else None, ctypes.byref(opts), _ptr(out),
