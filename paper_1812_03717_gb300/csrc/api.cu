@@ -1057,15 +1057,21 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
     }
     SGW_CUDA(lanczos_capacity(plan16, 1, threads, corr_prec, &own1), "solver occupancy");
     own1 = std::min(own1, chunk);
-    if (precond != SGW_PRECOND_NONE) SGW_CUDA(solve_grid(plan16, 1, chunk, &grid_b), "solver occupancy");
+    // corrections: single-shift Lanczos, or BiCGstab(ell) when the method is BiCGstab or a
+    // preconditioner is asked for
+    const bool bicg_corr = !lanczos || precond != SGW_PRECOND_NONE;
+    if (bicg_corr) SGW_CUDA(solve_grid(plan16, 1, chunk, &grid_b), "solver occupancy");
     SGW_CUDA(residual_owners(plan16, res_prec, &own_r), "residual occupancy");
     own_r = (int)std::min<size_t>(own_r, np);
     // Krylov workspace of one launch (reused by the correction solves); the basis per owner
     int maxk = max_mv;
     const size_t eb = (size_t)prec_bytes(precision) * s->npw;   // basis vector of the pass
+    // basis [owners][mk + 1][n_pw], then alpha / beta [ctas][2][mk + 1], then the y and l
+    // coefficients [ctas][2][mk][ns]; each part starts on a 256-byte boundary
+    auto al256 = [](size_t b) { return (b + 255) / 256 * 256; };
     auto lanczos_bytes = [&](int owners, int ctas, int ns, int mk, size_t vbytes) -> size_t {
-        return (size_t)owners * (size_t)(mk + 1) * vbytes +
-               (size_t)ctas * (2 * (size_t)(mk + 1) * 8 + 2 * (size_t)mk * ns * 16) + 4096;
+        return al256((size_t)owners * (size_t)(mk + 1) * vbytes) + al256((size_t)ctas * 2 * (size_t)(mk + 1) * 8) +
+               (size_t)ctas * 2 * (size_t)mk * ns * 16 + 4096;
     };
     if (lanczos) {
         size_t free_b = 0, total_b = 0;
@@ -1084,7 +1090,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
                        lanczos_bytes(own1, own1 * plan16.csize, 1, maxk, vb));
     else
         wsb = (size_t)own * (vb * (2 * ell + 3) + vb * (size_t)nomega) + 4096;
-    if (precond != SGW_PRECOND_NONE)
+    if (bicg_corr)
         wsb = std::max(wsb, (size_t)grid_b * vb * (2 * ell + 6) + 4096);   // BiCGstab seeds, directions, scratch
     Carve c;
     const size_t o_solver = c.take(wsb);
@@ -1144,10 +1150,10 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         L.x = x_d;
         char* base = w + o_solver;
         const size_t vbytes = (size_t)prec_bytes(prec) * s->npw;
+        const size_t o_ab = al256((size_t)owners * (maxk + 1) * vbytes);
         L.basis = (double2*)base;
-        L.ab = (double*)(base + (size_t)owners * (maxk + 1) * vbytes);
-        L.ysc = (double2*)(base + (size_t)owners * (maxk + 1) * vbytes +
-                           (size_t)owners * pl.csize * 2 * (size_t)(maxk + 1) * 8);
+        L.ab = (double*)(base + o_ab);
+        L.ysc = (double2*)(base + o_ab + al256((size_t)owners * pl.csize * 2 * (size_t)(maxk + 1) * 8));
         L.counter = (int*)(w + o_cnt);
         L.out_mv = mv_d;
         L.out_res = est_d;
@@ -1215,7 +1221,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         ++launches;
     }
     SGW_CUDA(launch_residual(plan16, nrhs, nomega, nullptr, 0, rhs_d, d_eref, d_om, eta, X, (double2*)(w + o_rscr),
-                             d_rel, d_cert, nullptr, own_r, st, d_etas, d_b, res_prec),
+                             d_rel, d_cert, nullptr, own_r, st, d_etas, d_b, res_prec, 1),
              "residual kernel");
     ++launches;
     std::vector<int> stv(np), mvv(np);
@@ -1275,10 +1281,10 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
             const int* d_list = (const int*)(w + o_list);
             SGW_CUDA(launch_residual(plan16, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
                                      (double2*)(w + o_rscr), d_rel, d_cert, (double2*)(w + o_rvec),
-                                     std::min(own_r, nc), st, d_etas, d_b, res_prec),
+                                     std::min(own_r, nc), st, d_etas, d_b, res_prec, 1),
                      "residual kernel");
             const double tl = std::min(0.5, std::max(1e-13, 0.3 * need));
-            if (pc == SGW_PRECOND_NONE) {
+            if (!bicg_corr) {
                 SGW_CUDA(run_lanczos(plan16, corr_prec, nc, 1, (const double2*)(w + o_rvec),
                                      (const double*)(w + o_eref1), (const double*)(w + o_zero), tl, 0.0,
                                      (double2*)(w + o_dbuf), (int*)(w + o_mv1), (double*)(w + o_est1),
@@ -1287,6 +1293,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
             } else {
                 // the diagonal of each pair from its correction right-hand side (plain: kinetic
                 // scaling by the residual's kinetic energy; learned: the perceptron on top)
+                if (pc != SGW_PRECOND_NONE) {
                 SGW_CUDA(cudaMemcpyAsync(w + o_pe, pe.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st), "copy");
                 SGW_CUDA(cudaMemcpyAsync(w + o_po, po.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st), "copy");
                 PrecondArgs pa;
@@ -1302,6 +1309,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
                 pa.mlp = pc == SGW_PRECOND_LEARNED ? mlp_weights(mlp) : nullptr;
                 pa.d = (double*)(w + o_pre);
                 SGW_CUDA(launch_precond(plan16, pa, st), "preconditioner kernel");
+                }
                 SolveArgs A;
                 A.nrhs = nc;
                 A.nshift = 1;
@@ -1319,7 +1327,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
                 A.seedw = (double2*)(w + o_solver);
                 A.uw = (double2*)(w + o_solver + (size_t)gb * vb * (2 * ell + 3));
                 A.pscr = (double2*)(w + o_solver + (size_t)gb * vb * (2 * ell + 4));
-                A.pre = (const double*)(w + o_pre);
+                A.pre = pc != SGW_PRECOND_NONE ? (const double*)(w + o_pre) : nullptr;
                 A.counter = (int*)(w + o_cnt);
                 A.out_mv = (int*)(w + o_mv1);
                 A.out_res = (double*)(w + o_est1);
@@ -1330,7 +1338,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
             SGW_CUDA(launch_pair_axpy(nc, d_list, s->npw, (const double2*)(w + o_dbuf), X, st), "refinement update");
             SGW_CUDA(launch_residual(plan16, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
                                      (double2*)(w + o_rscr), d_rel, d_cert, nullptr, std::min(own_r, nc), st, d_etas,
-                                     d_b, res_prec),
+                                     d_b, res_prec, 1),
                      "residual kernel");
             launches += 4;
             SGW_CUDA(cudaMemcpyAsync(mv1.data(), w + o_mv1, sizeof(int) * nc, cudaMemcpyDeviceToHost, st), "report");

@@ -535,19 +535,23 @@ __global__ void __launch_bounds__(kThreads, 1) apply_kernel(Plan P, int nvec, co
 //   res = -P_c rhs_r - (P_c H P_c - z_rj) x_rj,
 //   rel[p] = |res| / |P_c rhs_r|,  cert[p] = |res| / (|Im z_rj| |x_rj|),
 // and, when store is given, store[i] = -res (the right-hand side of the correction
-// equation in the solver's convention b = -P_c rhs).  The projections, the assembly of res
-// and the norms are FP64; H (P_c x) is applied in the policy Ar (FP64, or float-float with a
-// relative error near 1e-14).  One CTA or cluster per pair; scratch: 2 n_pw values per owner.
+// equation in the solver's convention b = -P_c rhs).  With `clean` set, x_rj is first
+// replaced by P_c x_rj (the solution lies in range(P_c), and the correction solves act there
+// only: an occupied component -- rounding of a single-precision pass, or a caller's initial
+// guess -- is removed exactly instead of being left in the residual).  The projections, the
+// assembly of res and the norms are FP64; H (P_c x) is applied in the policy Ar (FP64, or
+// float-float with a relative error near 1e-14).  One CTA or cluster per pair; scratch: 2 n_pw
+// values per owner.
 template <class Ar>
 __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nrhs, int ns, const int* __restrict__ list,
                                                                int nlist, const double2* __restrict__ rhs,
                                                                const double* __restrict__ e_ref,
                                                                const double* __restrict__ omega, double eta,
-                                                               const double2* __restrict__ x,
+                                                               double2* __restrict__ x,
                                                                double2* __restrict__ scratch, double* __restrict__ rel,
                                                                double* __restrict__ cert, double2* __restrict__ store,
                                                                const double* __restrict__ eta_s,
-                                                               const double2* __restrict__ bvec) {
+                                                               const double2* __restrict__ bvec, int clean) {
     using C = typename Ar::C;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double2 s_dot[kRedSlots];
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nr
     for (int i = cl_id; i < count; i += ncl) {
         const int pq = list ? list[i] : i;
         const int r = pq / ns, j = pq % ns;
-        const double2* xv = x + (size_t)pq * npw;
+        double2* xv = x + (size_t)pq * npw;
         const double2* rv = rhs + (size_t)r * npw;
         const double2 z = make_double2(e_ref[r] + omega[j], eta_s ? eta_s[j] : eta);
         part_dots_f64(P, q, R, P.psi, P.nocc, npw, xv, coef);
@@ -574,6 +578,7 @@ __global__ void __launch_bounds__(kResThreads, 1) residual_kernel(Plan P, int nr
             double2 h = xv[g];
             for (int o = 0; o < P.nocc; ++o) h = csub(h, cmul(coef[o], P.psi[(size_t)o * npw + g]));
             xa[g] = Ar::from_d(h);   // same thread, same slot: no FP64 value is read back
+            if (clean) xv[g] = h;    // read again below by this thread only
         }
         __syncthreads();
         apply_h_block<Ar>(P, smem, q, R, xa, ya, cz(), APPLY_PROJ_OUT);
@@ -1303,14 +1308,15 @@ cudaError_t residual_owners(const Plan& P, int precision, int* owners) {
 cudaError_t launch_residual(const Plan& P0, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int owners, cudaStream_t st,
-                            const double* eta_s, const double2* bvec, int precision) {
+                            const double* eta_s, const double2* bvec, int precision, int clean) {
     const int es = residual_bytes(precision);
     const Plan P = tuned_plan(P0, 0, es);
     const int smem = apply_smem_bytes(P0, es);
+    double2* xm = const_cast<double2*>(x);   // written only with clean set
     void* args[] = {(void*)&P,     (void*)&nrhs,    (void*)&nshift, (void*)&list,  (void*)&nlist,
-                    (void*)&rhs,   (void*)&e_ref,   (void*)&omega,  (void*)&eta,   (void*)&x,
+                    (void*)&rhs,   (void*)&e_ref,   (void*)&omega,  (void*)&eta,   (void*)&xm,
                     (void*)&scratch, (void*)&rel,   (void*)&cert,   (void*)&store, (void*)&eta_s,
-                    (void*)&bvec};
+                    (void*)&bvec,  (void*)&clean};
     return launch_owned(residual_ptr(precision), P, owners, kResThreads, smem, st, args);
 }
 

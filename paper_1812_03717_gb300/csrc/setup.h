@@ -134,14 +134,15 @@ cudaError_t launch_apply(const Plan& P, int nvec, const double2* x, double2* y, 
                          double2* scratch, int owners, int precision, cudaStream_t st);
 // Im z_rj = eta_s[j] when eta_s is given, else eta; the certificate divides by |Im z|;
 // bvec [nrhs][npw] = -P_c rhs when given (else the kernel projects rhs itself).  precision
-// selects the arithmetic of the H application inside (FP64, else float-float); scratch:
-// 2 n_pw complex128 slots per owner.
+// selects the arithmetic of the H application inside (FP64, else float-float); clean:
+// replace each checked x by P_c x first (x is then written); scratch: 2 n_pw complex128 slots
+// per owner.
 cudaError_t residual_owners(const Plan& P, int precision, int* owners);
 cudaError_t launch_residual(const Plan& P, int nrhs, int nshift, const int* list, int nlist, const double2* rhs,
                             const double* e_ref, const double* omega, double eta, const double2* x, double2* scratch,
                             double* rel, double* cert, double2* store, int owners, cudaStream_t st,
                             const double* eta_s = nullptr, const double2* bvec = nullptr,
-                            int precision = SGW_PREC_FP64);
+                            int precision = SGW_PREC_FP64, int clean = 0);
 // b[r] = -P_c rhs[r] (FP64) for r < nrhs; a precomputed bvec lets the residual kernel skip it.
 cudaError_t launch_project_rhs(const Plan& P, int nrhs, const double2* rhs, double2* b, cudaStream_t st);
 // dn[po][pi][j] += weight sum_v sum_g conj(R[v n_p + po][g]) (X[v n_p + pi][j][g] + X[v n_p + pi][nw + j][g])
