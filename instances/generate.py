@@ -161,24 +161,64 @@ def kb_coeffs(a, tau, k_frac, mil, width):
     return np.array(out)
 
 
-def ground_state(inst: Instance, k_frac, n_bands: int):
-    """Lowest n_bands eigenpairs of the synthetic Hamiltonian at k (stand-in for the DFT input)."""
+def closed_form_h(inst: Instance, k_frac):
+    """Dense H in the k sphere from the closed-form V(G - G') (kept for |G - G'|^2 <= 4 E_cut),
+    T_G and the KB projectors: the generator's own route to the ground state.  V is tabulated
+    once on the grid of Miller differences and gathered row block by row block."""
     mil, n2 = sphere(inst.a, k_frac, inst.ecut_ry)
     b = recip(inst.a)
-    d = mil[:, None, :] - mil[None, :, :]
-    flat = d.reshape(-1, 3)
-    uniq, inv = np.unique(flat, axis=0, return_inverse=True)
-    vg = vloc_coeffs(inst.a, inst.tau, uniq)
-    g2 = np.einsum("ij,ij->i", uniq @ b, uniq @ b)
-    vg[g2 > 4.0 * inst.ecut_ry * (1 + 1e-12)] = 0.0
-    h = vg[inv.ravel()].reshape(len(mil), len(mil))
-    h[np.diag_indices(len(mil))] += 0.5 * n2
-    beta = kb_coeffs(inst.a, inst.tau, k_frac, mil, inst.kb_width)
-    for p in range(len(inst.kb_atom)):
-        bp = beta[inst.kb_atom[p]]
-        h += inst.kb_d[p] * np.outer(bp, bp.conj())
+    n = len(mil)
+    lo = (mil.min(axis=0) - mil.max(axis=0)).astype(np.int64)      # smallest difference per axis
+    ext = (2 * (mil.max(axis=0) - mil.min(axis=0)) + 1).astype(np.int64)
+    grid = np.stack(np.meshgrid(*[np.arange(lo[i], lo[i] + ext[i]) for i in range(3)], indexing="ij"),
+                    axis=-1).reshape(-1, 3)
+    g2 = np.einsum("ij,ij->i", grid @ b, grid @ b)
+    keep = g2 <= 4.0 * inst.ecut_ry * (1 + 1e-12)
+    vtab = np.zeros(len(grid), dtype=np.complex128)
+    vtab[keep] = vloc_coeffs(inst.a, inst.tau, grid[keep])
+    m = mil.astype(np.int64) - lo[None, :]
+    h = np.empty((n, n), dtype=np.complex128)
+    for r0 in range(0, n, 1024):
+        r1 = min(n, r0 + 1024)
+        d = m[r0:r1, None, :] - mil.astype(np.int64)[None, :, :]
+        h[r0:r1] = vtab[(d[..., 0] * ext[1] + d[..., 1]) * ext[2] + d[..., 2]]
+    h[np.diag_indices(n)] += 0.5 * n2
+    beta = kb_coeffs(inst.a, inst.tau, k_frac, mil, inst.kb_width)[inst.kb_atom]
+    h += (beta.T * inst.kb_d[None, :]) @ beta.conj()
     h = 0.5 * (h + h.conj().T)
-    w, v = scipy.linalg.eigh(h, subset_by_index=[0, n_bands])
+    return mil, h
+
+
+def _lowest_eigenpairs(h, count):
+    """The `count` lowest eigenpairs of the Hermitian h.  Large matrices go to the GPU's dense
+    eigensolver (cuSOLVER through torch) when one is present, else LAPACK's subset driver; each
+    eigenvector's phase is fixed (its largest component real and positive)."""
+    w = v = None
+    if h.shape[0] > 6000:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                t = torch.from_numpy(h).cuda()
+                wt, vt = torch.linalg.eigh(t)
+                w = wt[:count].cpu().numpy()
+                v = vt[:, :count].cpu().numpy()
+                del t, wt, vt
+                torch.cuda.empty_cache()
+        except ImportError:
+            pass
+    if w is None:
+        w, v = scipy.linalg.eigh(h, subset_by_index=[0, count - 1])
+    big = np.argmax(np.abs(v), axis=0)
+    ph = v[big, np.arange(v.shape[1])]
+    v = v * (np.abs(ph) / ph)[None, :]
+    return w, v
+
+
+def ground_state(inst: Instance, k_frac, n_bands: int):
+    """Lowest n_bands eigenpairs of the synthetic Hamiltonian at k (stand-in for the DFT input)."""
+    mil, h = closed_form_h(inst, k_frac)
+    w, v = _lowest_eigenpairs(h, n_bands + 1)
+    del h
     return mil, np.ascontiguousarray(v[:, :n_bands].T), w[:n_bands], float(w[n_bands] - w[n_bands - 1])
 
 
@@ -218,7 +258,11 @@ def cubic8_cell(alat):
     return np.eye(3) * alat, DIAMOND_FRAC * alat
 
 
-def make_instance(name, seed, a, tau, ecut_ry, dims, n_occ, kq_pairs, gp, omega, eta):
+def make_instance(name, seed, a, tau, ecut_ry, dims, n_occ, kq_pairs, gp, omega, eta, cache=False):
+    if cache:
+        inst = _cache_load(name, seed)
+        if inst is not None:
+            return inst
     n_at = len(tau)
     inst = Instance(name=name, seed=seed, a=np.asarray(a, float), tau=np.asarray(tau, float),
                     ecut_ry=float(ecut_ry), fft_dims=tuple(int(x) for x in dims),
@@ -229,10 +273,67 @@ def make_instance(name, seed, a, tau, ecut_ry, dims, n_occ, kq_pairs, gp, omega,
                     omega=np.asarray(omega, float), eta=float(eta))
     for k, kq in kq_pairs:
         mk, pk, ek, gk = ground_state(inst, k, n_occ)
-        mq, pq, eq, gq = ground_state(inst, kq, n_occ)
+        if np.array_equal(np.asarray(k, float), np.asarray(kq, float)):
+            mq, pq, eq, gq = mk, pk, ek, gk          # q = 0: one basis
+        else:
+            mq, pq, eq, gq = ground_state(inst, kq, n_occ)
         inst.kpoints.append(KPointData(k_frac=np.asarray(k, float), kq_frac=np.asarray(kq, float),
                                        miller_k=mk, miller_kq=mq, psi_k=pk, eps_k=ek,
                                        psi_kq=pq, eps_kq=eq, gap_k=gk, gap_kq=gq))
+    if cache:
+        _cache_store(inst)
+    return inst
+
+
+# ---------------------------------------------------------------- on-disk instance cache
+#
+# The large instances take minutes to diagonalise; their arrays are kept in
+# $SGW_INSTANCE_CACHE (default: <tmp>/sgw_instances) under the instance name and seed, so that
+# the processes of one session (tests, benchmark) generate each only once.
+
+_CACHE_VERSION = 1
+
+
+def _cache_path(name, seed):
+    import os
+    import tempfile
+    d = os.environ.get("SGW_INSTANCE_CACHE") or os.path.join(tempfile.gettempdir(), "sgw_instances")
+    return os.path.join(d, f"{name}-seed{seed}-v{_CACHE_VERSION}.npz")
+
+
+def _cache_store(inst):
+    import os
+    path = _cache_path(inst.name, inst.seed)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    arrays = {"a": inst.a, "tau": inst.tau, "ecut_ry": inst.ecut_ry, "fft_dims": np.asarray(inst.fft_dims),
+              "vloc_r": inst.vloc_r, "kb_atom": inst.kb_atom, "kb_width": inst.kb_width, "kb_d": inst.kb_d,
+              "n_occ": inst.n_occ, "gp_miller": inst.gp_miller, "omega": inst.omega, "eta": inst.eta,
+              "nk": len(inst.kpoints)}
+    for i, kp in enumerate(inst.kpoints):
+        for f in ("k_frac", "kq_frac", "miller_k", "miller_kq", "psi_k", "eps_k", "psi_kq", "eps_kq", "gap_k",
+                  "gap_kq"):
+            arrays[f"k{i}_{f}"] = getattr(kp, f)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, **arrays)
+    os.replace(tmp, path)
+
+
+def _cache_load(name, seed):
+    import os
+    path = _cache_path(name, seed)
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+    inst = Instance(name=name, seed=seed, a=z["a"], tau=z["tau"], ecut_ry=float(z["ecut_ry"]),
+                    fft_dims=tuple(int(x) for x in z["fft_dims"]), vloc_r=z["vloc_r"], kb_atom=z["kb_atom"],
+                    kb_width=z["kb_width"], kb_d=z["kb_d"], n_occ=int(z["n_occ"]), gp_miller=z["gp_miller"],
+                    omega=z["omega"], eta=float(z["eta"]))
+    for i in range(int(z["nk"])):
+        g = lambda f: z[f"k{i}_{f}"]
+        inst.kpoints.append(KPointData(k_frac=g("k_frac"), kq_frac=g("kq_frac"), miller_k=g("miller_k"),
+                                       miller_kq=g("miller_kq"), psi_k=g("psi_k"), eps_k=g("eps_k"),
+                                       psi_kq=g("psi_kq"), eps_kq=g("eps_kq"), gap_k=float(g("gap_k")),
+                                       gap_kq=float(g("gap_kq"))))
     return inst
 
 
@@ -298,3 +399,29 @@ def fcc_perturbed(seed: int, ecut_ry: float = 10.0, dims=(16, 16, 16), n_occ: in
     omega = np.linspace(0.0, 50.0, n_omega) / HA_EV
     return make_instance("fcc2-disordered-%d" % seed, seed, a, tau, ecut_ry, dims, n_occ,
                          [(k, k + q)], shortest_g(a, n_pert, True), omega, 0.1 / HA_EV)
+
+
+def supercell64_cell(alat=10.26):
+    """2 x 2 x 2 supercell of the 8-atom cubic diamond cell: cube of side 2 alat, 64 sites."""
+    sites = np.array([(np.array([i, j, k]) + f) / 2.0 for i in (0, 1) for j in (0, 1) for k in (0, 1)
+                      for f in DIAMOND_FRAC])
+    return np.eye(3) * (2 * alat), sites * (2 * alat)
+
+
+def config3(seed: int = 0, ecut_ry: float = 25.0, dims=(72, 72, 72), n_occ: int = 128, n_pert: int = 64,
+            n_omega: int = 128, cache: bool = True):
+    """64-atom 2 x 2 x 2 supercell of the cubic cell (a = 20.52 bohr), ecut 25 Ry (18 277 plane
+    waves), 72^3 box, k = Gamma, q = 0, 128 occupied bands, the 64 shortest non-zero G,
+    omega = linspace(0, 60 eV, 128), eta = 0.1 eV.
+    Draws: rng = default_rng(seed); displacements rng.normal(0, 0.05, (64, 3)) bohr added to the
+    diamond sites (site order: supercell offset (i, j, k) outermost, then the 8-atom cell's sites).
+    With q = 0 the right-hand side of G_p = 0 would be zero after P_c (the bands are
+    eigenvectors), hence the non-zero G."""
+    alat = 10.26
+    a, tau = supercell64_cell(alat)
+    rng = np.random.default_rng(seed)
+    tau = tau + rng.normal(0.0, 0.05, size=tau.shape)
+    omega = np.linspace(0.0, 60.0, n_omega) / HA_EV
+    k = np.zeros(3)
+    return make_instance("supercell64-ecut%g" % ecut_ry, seed, a, tau, ecut_ry, dims, n_occ, [(k, k)],
+                         shortest_g(a, n_pert, False), omega, 0.1 / HA_EV, cache=cache)

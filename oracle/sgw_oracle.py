@@ -130,8 +130,8 @@ def dense_h(a, tau, ecut_ry, k_frac, dims, vloc_r, kb_atom, kb_width, kb_d):
         h[i, :] = vh[d[:, 0], d[:, 1], d[:, 2]]
     h[np.diag_indices(n)] += kin
     beta = kb_beta(a, tau, k_frac, miller, kb_atom, kb_width)
-    for p in range(len(kb_d)):
-        h += kb_d[p] * np.outer(beta[p], beta[p].conj())
+    # sum_p D_p beta_p(G) conj(beta_p(G')) as one matrix product over p
+    h += (beta.T * np.asarray(kb_d, np.float64)[None, :]) @ beta.conj()
     return h, miller, kin
 
 
@@ -185,11 +185,21 @@ def make_rhs(miller_kq, miller_k, psi_k, gp_miller):
 
 # ------------------------------------------------------------------ Eq. 6-7 the solve
 
+def projected_h(h, psi_v):
+    """P_c H P_c with P_c = 1 - Q, Q = sum_v |psi_v><psi_v| (Eq. 7), expanded as
+    H - Q H - H Q + Q H Q and each Q product taken through the n_occ states (the same matrix as
+    forming P_c densely, at a cost linear in n_occ)."""
+    psi = np.asarray(psi_v, np.complex128)
+    a = psi.conj() @ h                 # <psi_v| H      [n_occ][n]
+    b = h @ psi.T                      # H |psi_v>      [n][n_occ]
+    c = a @ psi.T                      # <psi_v|H|psi_w>
+    return h - psi.T @ a - b @ psi.conj() + psi.T @ (c @ psi.conj())
+
+
 def shifted_operator(h, psi_v, z):
     """P_c H P_c - z on the full basis (on range(P_v) it acts as -z; z has Im z = eta > 0)."""
     n = h.shape[0]
-    pc = np.eye(n, dtype=np.complex128) - np.asarray(psi_v).T @ np.asarray(psi_v).conj()
-    return pc @ h @ pc - z * np.eye(n)
+    return projected_h(h, psi_v) - z * np.eye(n)
 
 
 def solve_shifted(h, psi_v, rhs, e_ref, omega, eta):
@@ -198,8 +208,7 @@ def solve_shifted(h, psi_v, rhs, e_ref, omega, eta):
     rhs = np.atleast_2d(np.asarray(rhs, np.complex128))
     b = -project_c(psi_v, rhs)
     n = h.shape[0]
-    pc = np.eye(n, dtype=np.complex128) - np.asarray(psi_v).T @ np.asarray(psi_v).conj()
-    pcp = pc @ h @ pc
+    pcp = projected_h(h, psi_v)
     e_ref = np.asarray(e_ref, np.float64)
     out = np.zeros((len(rhs), len(omega), n), dtype=np.complex128)
     for e in np.unique(e_ref):
