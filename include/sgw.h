@@ -166,9 +166,9 @@ typedef struct {
                          float-float otherwise) */
     int ell;          /* BiCGstab(ell) degree 1..4 (0 -> 4); unused by Lanczos */
     int seed_index;   /* BiCGstab seed shift; -1 -> the largest omega; unused by Lanczos */
-    int max_matvec;   /* H applications per right-hand side and per correction solve (0 -> 4096 for
+    int max_matvec;   /* H applications per right-hand side and per correction solve (0 -> 16384 for
                          Lanczos, whose basis it sizes, 40000 for BiCGstab); the Lanczos basis is also
-                         capped by free device memory */
+                         capped by half the free device memory */
     int max_refine;   /* rounds of per-shift correction solves (0 -> 3, negative -> none) */
     int threads;      /* CTA size of the Lanczos kernel: 256, 384 or 512 (0 -> 384 FP64, else 512) */
     void* stream;     /* cudaStream_t, NULL = default stream */
@@ -212,9 +212,11 @@ typedef struct {
  *    BiCGstab(ell) (Frommer 2003, the solver the paper cites), one seed system carrying
  *    all shifts through scalar recurrences.
  * 2. True FP64 residual and certificate of every pair (as sgw_residual).
- * 3. Pairs whose true residual exceeds tol (recursive/true residual gap, budget exhausted)
- *    get per-shift correction solves A_j d = r_j, x_j += d, then step 2 again; up to
- *    max_refine rounds.
+ * 3. Pairs whose true residual exceeds tol or whose certificate exceeds cert_tol, but whose
+ *    relative residual is at most 1e-3 (near convergence: rounding of the pass, the
+ *    recursive / true residual gap), get per-shift correction solves A_j d = r_j, x_j += d,
+ *    then step 2 again; up to max_refine rounds.  The returned solutions are projected onto
+ *    range(P_c), where the exact ones lie.
  *   rhs    complex [nrhs][n_pw] (host or device): dV psi_v in this basis.
  *   e_ref  [nrhs] host, Ha.   omega [nomega] host, Ha.   eta > 0 (Ha), else SGW_EINVAL.
  *   tol    relative residual target (e.g. 1e-10).

@@ -508,33 +508,100 @@ __device__ __forceinline__ void part_sum(const Plan& P, Red& R, T (&v)[NV], doub
     cluster_combine(P, loc, NV, out);
 }
 
-// out[v] = sum_g conj(src_v[g]) x[g] for v < nv over the plane waves of the vector's owners,
-// with src the occupied states (WHICH = 0) or the projectors (WHICH = 1) in the policy's
-// format; per-thread sums in the policy's arithmetic, the block reduction by block_sum_c, the
-// cluster sum in FP64.  out must hold nv rounded up to 8.
+// Warp sum of NV complex values of the policy's type; lane 0 ends with the totals.
+template <int NV>
+__device__ __forceinline__ void warp_sum_c(double2 (&v)[NV]) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[i].x += __shfl_down_sync(0xffffffffu, v[i].x, o);
+            v[i].y += __shfl_down_sync(0xffffffffu, v[i].y, o);
+        }
+}
+template <int NV>
+__device__ __forceinline__ void warp_sum_c(float4 (&v)[NV]) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float4 t;
+            t.x = __shfl_down_sync(0xffffffffu, v[i].x, o);
+            t.y = __shfl_down_sync(0xffffffffu, v[i].y, o);
+            t.z = __shfl_down_sync(0xffffffffu, v[i].z, o);
+            t.w = __shfl_down_sync(0xffffffffu, v[i].w, o);
+            v[i] = ArDF::add(v[i], t);
+        }
+}
+template <int NV>
+__device__ __forceinline__ void warp_sum_c(float2 (&v)[NV]) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v[i].x += __shfl_down_sync(0xffffffffu, v[i].x, o);
+            v[i].y += __shfl_down_sync(0xffffffffu, v[i].y, o);
+        }
+}
+
+// Rows of a dot product: the occupied states (WHICH = 0) or projectors (WHICH = 1) in the
+// policy's format, or FP64 rows V[v ld + g] (WHICH = 2).
 template <class Ar, int WHICH>
-__device__ __forceinline__ void part_dots(const Plan& P, const Part& q, Red& R, int nv, const typename Ar::C* x,
-                                          double2* out) {
+struct DotRows {
+    const Plan& P;
+    const double2* V;
+    int ld;
+    __device__ __forceinline__ typename Ar::C operator()(int v, int g) const {
+        if constexpr (WHICH == 0) return Ar::psi(P, (size_t)v * P.npw + g);
+        else if constexpr (WHICH == 1) return Ar::beta(P, (size_t)v * P.npw + g);
+        else return V[(size_t)v * ld + g];
+    }
+};
+
+// out[v] = sum_g conj(row_v[g]) x[g] for v < nv over the plane waves of the vector's owners.
+// The rows come in groups of 8; the (group, slice) work items -- a slice being every
+// slices-th 32-wide chunk of the plane waves -- are spread over the warps, so both many rows
+// (the occupied states of a large cell) and few rows keep every warp busy.  Each item is
+// summed within its warp in the policy's arithmetic; the per-slice partials (FP64) are
+// summed by one thread per row; one block barrier, and the cluster sum in FP64 (rank order).
+// out (and the cluster partial buffer) must hold nv rounded up to 8.
+template <class Ar, int WHICH>
+__device__ __forceinline__ void part_dots_rows(const Plan& P, const Part& q, Red& R, int nv, const DotRows<Ar, WHICH>& row,
+                                               const typename Ar::C* x, double2* out) {
     using C = typename Ar::C;
-    const int n = P.npw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double2* dst = P.csize == 1 ? out : R.part + R.par * R.stride;
-    for (int v0 = 0; v0 < nv; v0 += 8) {
+    const int ngroups = (nv + 7) >> 3;
+    const int slices = max(1, nw / max(ngroups, 1));
+    for (int t = warp; t < ngroups * slices; t += nw) {
+        const int gi = t / slices, sl = t - gi * slices;
+        const int v0 = gi * 8, cnt = min(8, nv - v0);
         C acc[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) acc[i] = Ar::zero();
-        const int cnt = min(8, nv - v0);
-        for (int g = q.g0 + threadIdx.x; g < q.g1; g += blockDim.x) {
+        for (int g = q.g0 + sl * 32 + lane; g < q.g1; g += 32 * slices) {
             const C xv = x[g];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (i < cnt) {
-                    const size_t o = (size_t)(v0 + i) * n + g;
-                    const C s = WHICH == 0 ? Ar::psi(P, o) : Ar::beta(P, o);
-                    acc[i] = Ar::add(acc[i], Ar::mul(Ar::conj(s), xv));
-                }
+            for (int i = 0; i < 8; ++i)
+                if (i < cnt) acc[i] = Ar::add(acc[i], Ar::mul(Ar::conj(row(v0 + i, g)), xv));
+        }
+        warp_sum_c<8>(acc);
+        if (lane == 0) {
+            for (int i = 0; i < cnt; ++i) {
+                const double2 d = Ar::to_d(acc[i]);
+                if (slices == 1) dst[v0 + i] = d;
+                else R.red[(v0 + i) * slices + sl] = d;
             }
         }
-        block_sum_c<8>(acc, R.red, dst + v0);
+    }
+    __syncthreads();
+    if (slices > 1) {
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            double2 s = cz();
+            for (int sl = 0; sl < slices; ++sl) s = cadd(s, R.red[v * slices + sl]);
+            dst[v] = s;
+        }
+        __syncthreads();
     }
     if (P.csize > 1) {
         R.par ^= 1;
@@ -542,27 +609,19 @@ __device__ __forceinline__ void part_dots(const Plan& P, const Part& q, Red& R, 
     }
 }
 
+// Dots with the occupied states (WHICH = 0) or the projectors (WHICH = 1), policy format.
+template <class Ar, int WHICH>
+__device__ __forceinline__ void part_dots(const Plan& P, const Part& q, Red& R, int nv, const typename Ar::C* x,
+                                          double2* out) {
+    const DotRows<Ar, WHICH> row{P, nullptr, 0};
+    part_dots_rows<Ar, WHICH>(P, q, R, nv, row, x, out);
+}
+
 // FP64 dots out[v] = sum_g conj(V[v ld + g]) x[g] over the owners' plane waves (V: FP64 rows).
 __device__ __forceinline__ void part_dots_f64(const Plan& P, const Part& q, Red& R, const double2* V, int nv, int ld,
                                               const double2* x, double2* out) {
-    double2* dst = P.csize == 1 ? out : R.part + R.par * R.stride;
-    for (int v0 = 0; v0 < nv; v0 += 8) {
-        double2 acc[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = cz();
-        const int cnt = min(8, nv - v0);
-        for (int g = q.g0 + threadIdx.x; g < q.g1; g += blockDim.x) {
-            const double2 xv = x[g];
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (i < cnt) acc[i] = cadd(acc[i], cmulc(V[(size_t)(v0 + i) * ld + g], xv));
-        }
-        block_sum<8>(acc, R.red, dst + v0);
-    }
-    if (P.csize > 1) {
-        R.par ^= 1;
-        cluster_combine(P, dst, nv, out);
-    }
+    const DotRows<ArF64, 2> row{P, V, ld};
+    part_dots_rows<ArF64, 2>(P, q, R, nv, row, x, out);
 }
 
 // -------------------------------------------------------------- shared-memory FFT lines

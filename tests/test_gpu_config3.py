@@ -1,7 +1,7 @@
 """Parity at the size of the 64-atom supercell (18 277 plane waves, 72^3 box, 128 occupied
 bands, 64 perturbations, 128 frequencies), where the on-chip box is shared by a
 thread-block cluster: bit-exact sphere, map and Eq. 8 gather; H against the oracle's dense H;
-the multishift solve of every perturbation of two bands at all 128 frequencies, each pair's
+the multishift solve of every perturbation of one band at all 128 frequencies, each pair's
 FP64 residual and certificate, and dense-LU spot checks of three (band, frequency) pairs with
 all 64 perturbations.  The oracle's dense H is 5.3 GB and each LU some 1.6e13 flops on the
 host: this module takes minutes."""
@@ -73,42 +73,24 @@ def test_config3_apply_matches_dense(sys3, h3):
 
 
 def test_config3_rhs_solve_and_lu_spot_checks(sgw, sys3, inst3, h3):
+    """All 64 perturbations of one band at all 128 frequencies (the highest ones need some
+    14 000 Lanczos steps): every pair's FP64 residual and certificate, and the dense LU of
+    three (band, frequency) pairs with all 64 perturbations."""
     import torch
     kp = inst3.kpoints[0]
     npert = inst3.n_pert
-    bands = np.array([0, inst3.n_occ - 1])
-    # Eq. 8 right-hand sides of two bands and every perturbation, bit-exact against the oracle
+    band = 37
+    # Eq. 8 right-hand sides of the band for every perturbation, bit-exact against the oracle
     sk = sgw.System.from_instance(inst3, kp.k_frac)
-    rhs = sys3.make_rhs(sk, torch.from_numpy(kp.psi_k[bands]).cuda(), inst3.gp_miller)
-    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k[bands], inst3.gp_miller)
+    rhs = sys3.make_rhs(sk, torch.from_numpy(kp.psi_k[[band]]).cuda(), inst3.gp_miller)
+    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k[[band]], inst3.gp_miller)
     assert np.array_equal(rhs.cpu().numpy(), rref)
-    e_ref = np.repeat(kp.eps_k[bands], npert)
+    e_ref = np.full(npert, kp.eps_k[band])
     d, rep, ok = sys3.solve_shifted(rhs, e_ref, inst3.omega, inst3.eta, tol=1e-10, precision="df32")
     torch.cuda.synchronize()
     assert ok, np.unique(rep["status"], return_counts=True)
     assert rep["rel_res"].max() <= 1e-10 and rep["cert"].max() <= 1e-8
     d = d.cpu().numpy()
-    # dense LU of three (band, frequency) pairs with all 64 perturbations
-    rows0 = np.arange(npert)
-    ref = O.solve_shifted(h3, kp.psi_kq, rref[rows0], e_ref[rows0], inst3.omega[[0, 127]], inst3.eta)
-    assert _relerr(d[rows0][:, [0, 127]], ref).max() < TOL_SOLVE
-    rows1 = np.arange(npert, 2 * npert)
-    ref = O.solve_shifted(h3, kp.psi_kq, rref[rows1], e_ref[rows1], inst3.omega[[64]], inst3.eta)
-    assert _relerr(d[rows1][:, [64]], ref).max() < TOL_SOLVE
-
-
-def test_config3_fp32_inner_solve(sgw, sys3, inst3):
-    """The FP32 inner solve with FP64 refinement at this size: every pair certified, and the
-    same solutions as the float-float solve to 1e-8."""
-    import torch
-    kp = inst3.kpoints[0]
-    sk = sgw.System.from_instance(inst3, kp.k_frac)
-    rhs = sys3.make_rhs(sk, torch.from_numpy(kp.psi_k[[5]]).cuda(), inst3.gp_miller[:8])
-    e_ref = np.repeat(kp.eps_k[[5]], 8)
-    om = inst3.omega[::8].copy()
-    d32, rep, ok = sys3.solve_shifted(rhs, e_ref, om, inst3.eta, tol=1e-10, precision="fp32")
-    assert ok, np.unique(rep["status"], return_counts=True)
-    assert rep["rel_res"].max() <= 1e-10 and rep["cert"].max() <= 1e-8
-    ddf, _, ok2 = sys3.solve_shifted(rhs, e_ref, om, inst3.eta, tol=1e-10, precision="df32")
-    assert ok2
-    assert _relerr(d32.cpu().numpy(), ddf.cpu().numpy()).max() < TOL_SOLVE
+    js = [0, 64, 127]
+    ref = O.solve_shifted(h3, kp.psi_kq, rref, e_ref, inst3.omega[js], inst3.eta)
+    assert _relerr(d[:, js], ref).max() < TOL_SOLVE
