@@ -202,6 +202,11 @@ typedef struct {
                            learned round (SGW_PRECOND_LEARNED) */
 } sgw_report;
 
+/* Right-hand sides the multishift kernel works on at once (one per CTA, or per cluster when
+ * the box is split) for nomega shifts in `precision` with `threads` per CTA (0: default):
+ * batches of a multiple of it keep every owner busy.  Not in the paper: a sizing query. */
+sgw_status sgw_solve_capacity(const sgw_system* sys, int nomega, int precision, int threads, int* owners);
+
 /* Multishift solve (the hot path).  For every r < nrhs and j < nomega solves
  *   (P_c H P_c - z_rj) dpsi[r][j] = -P_c rhs[r],   z_rj = e_ref[r] + omega[j] + i eta.
  * 1. Multishift pass (Sec. 2.2: shifted systems share one Krylov space).  Default: the

@@ -807,6 +807,21 @@ sgw_status sgw_get_split(const sgw_system* s, int* csize, int* csize_fp32) {
     return SGW_OK;
 }
 
+sgw_status sgw_solve_capacity(const sgw_system* s, int nomega, int precision, int threads, int* owners) {
+    g_err.clear();
+    if (!s || !owners) return fail(SGW_EINVAL, "NULL argument");
+    if (nomega < 1 || nomega > kMaxShifts) return fail(SGW_EINVAL, "nomega must be in [1, 512]");
+    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32 && precision != SGW_PREC_FP32)
+        return fail(SGW_EINVAL, "unknown precision");
+    const Plan& plan = precision == SGW_PREC_FP32 ? s->plan8 : s->plan;
+    if (plan.csize == 0) return fail(SGW_EUNSUPPORTED, "the FFT box does not fit on chip in FP32");
+    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    int n = 0;
+    SGW_CUDA(lanczos_capacity(plan, nomega, threads, precision, &n), "solver occupancy");
+    *owners = n;
+    return SGW_OK;
+}
+
 sgw_status sgw_set_occupied(sgw_system* s, int n_occ, const void* psi_v, const double* eps_v) {
     g_err.clear();
     if (!s) return fail(SGW_EINVAL, "NULL system");

@@ -24,6 +24,7 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
                 "SGW_EUNSUPPORTED"]
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_split", "sgw_get_split",
+           "sgw_solve_capacity",
            "sgw_set_occupied", "sgw_make_rhs",
            "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_density_response_w", "sgw_aaa", "sgw_screened_coulomb", "sgw_residual", "sgw_residual_noalloc",
            "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
@@ -96,6 +97,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_get_box_map.argtypes = [vp, vp]
     lib.sgw_set_split.argtypes = [vp, ip]
     lib.sgw_get_split.argtypes = [vp, vp, vp]
+    lib.sgw_solve_capacity.argtypes = [vp, ip, ip, ip, vp]
     lib.sgw_set_occupied.argtypes = [vp, ip, vp, vp]
     lib.sgw_make_rhs.argtypes = [vp, vp, ip, vp, ip, vp, vp, vp]
     lib.sgw_apply_h.argtypes = [vp, ip, vp, vp, ip, vp]
@@ -282,6 +284,12 @@ class System:
         a, b = ctypes.c_int(), ctypes.c_int()
         _check(load().sgw_get_split(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def lanczos_owners(self, nomega, precision="df32", threads=0):
+        """Right-hand sides the multishift kernel holds at once (sgw_solve_capacity)."""
+        n = ctypes.c_int()
+        _check(load().sgw_solve_capacity(self._h, int(nomega), _PREC[precision], int(threads), ctypes.byref(n)))
+        return n.value
 
     def set_occupied(self, psi_v, eps_v):
         psi = _c128(psi_v)
