@@ -45,9 +45,10 @@ WORKLOAD2 = ("8-atom cubic Si-like cell a=10.26 bohr, ecut 20 Ry (N_pw~1640), 36
              "16 bands x 32 G_p = 2048 rhs x 64 omega in [0,60] eV, eta 0.1 eV")
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070     # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (1.26 TFLOP/s)
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070   # 80.5 TFLOP/s
-# DRAM bytes (read + write) per launch of the dominant kernel from an ncu capture (None: not
-# captured since the kernel last changed)
-TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) per right-hand side and Lanczos step of the dominant kernel, from
+# the ncu capture in profiles/ (16 right-hand sides x 100 steps of the supercell); a launch's
+# traffic is this times its steps.  None: not captured since the kernel last changed.
+TRAFFIC_PER_RHS_STEP = {"df32": 19.43e9 / 1600}
 
 
 def dist_env():
@@ -394,7 +395,12 @@ def run_ours(args):
                             "projector dots and updates) x steps + x = V y"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["time"] = "CUDA events around the multishift kernel launch on the solve's stream"
-        roof["traffic"] = TRAFFIC_PER_LAUNCH.get(precision)
+        tps = TRAFFIC_PER_RHS_STEP.get(precision)
+        steps_launch = float(np.mean([r["matvecs"].max(axis=1).sum() for r in recs]))
+        roof["traffic"] = tps * steps_launch if tps else None
+        if tps:
+            roof["traffic_unit"] = ("DRAM bytes per launch: %.1f MB per right-hand side and step (ncu, 16 rhs x 100 "
+                                    "steps) x the launch's %d steps" % (tps / 1e6, steps_launch))
         mv_all = np.concatenate([r["matvecs"].max(axis=1) for r in recs])
         quality = {"pairs": npairs, "certified": certified,
                    "max_true_rel_res": float(max(r["rel_res"].max() for r in recs)),
@@ -432,6 +438,11 @@ def run_ours(args):
                "what": "sgw_solve_shifted on pinned host buffers: rhs host->device, solve, dpsi and the per-pair "
                        "report device->host, all inside the timed region"}
         del rh, dh
+
+    # the supercell's Krylov workspace (tens of GB) is released before the other workloads
+    job["sys"].close()
+    del job["rhs"], out
+    torch.cuda.empty_cache()
 
     # secondary measurements on the 8-atom cubic cell
     secondary = None

@@ -236,6 +236,32 @@ sgw_status sgw_solve_shifted(sgw_system* sys, int nrhs, const void* rhs, const d
                              int nomega, const double* omega, double eta, double tol,
                              const sgw_solve_opts* opts, void* dpsi, sgw_report* report);
 
+/* Batched multishift solves of several systems of uneven sizes (the paper has no counterpart:
+ * this packs the right-hand sides, frequencies and k-points of different bases into few kernel
+ * launches).  Every item is solved exactly as sgw_solve_shifted would (same eta, tol and opts;
+ * each item has its own frequencies), but the multishift passes of all items whose on-chip box
+ * uses the same cluster size run in ONE persistent launch: its work queue hands out (item,
+ * right-hand side) pairs, the items with the most plane waves first, each owner re-reading the
+ * item's plan and twiddles when it changes item; the Krylov workspace is sized for the largest
+ * item.  Then each item's FP64 check and corrections run as in sgw_solve_shifted.
+ *   items   [nitems] host array; item.sys distinct, all on one device, with occupied states;
+ *           rhs / dpsi host or device as in sgw_solve_shifted; report optional (launches counts
+ *           the shared launch in the first item of each group; kernel_ms is the shared launch's).
+ *   opts    as sgw_solve_shifted; method Lanczos only, no x0 (else SGW_EUNSUPPORTED).
+ * Returns SGW_ENOCONV if any pair of any item misses tol or the certificate. */
+typedef struct {
+    sgw_system* sys;
+    int nrhs;
+    const void* rhs;        /* complex [nrhs][n_pw(sys)] (host or device) */
+    const double* e_ref;    /* [nrhs] host, Ha */
+    int nomega;
+    const double* omega;    /* [nomega] host, Ha */
+    void* dpsi;             /* complex [nrhs][nomega][n_pw(sys)] (host or device), overwritten */
+    sgw_report* report;     /* optional */
+} sgw_batch_item;
+sgw_status sgw_solve_batched(int nitems, const sgw_batch_item* items, double eta, double tol,
+                             const sgw_solve_opts* opts);
+
 /* Green's-function columns (Sec. 2.2, Eq. 2 with the operator of Eq. 3).  For every c < ncol
  * and j < nz solves
  *   (H - z_j) g[c][j] = -e_{G'},   G' = cols[c],

@@ -425,3 +425,59 @@ def config3(seed: int = 0, ecut_ry: float = 25.0, dims=(72, 72, 72), n_occ: int 
     k = np.zeros(3)
     return make_instance("supercell64-ecut%g" % ecut_ry, seed, a, tau, ecut_ry, dims, n_occ, [(k, k)],
                          shortest_g(a, n_pert, False), omega, 0.1 / HA_EV, cache=cache)
+
+
+def smooth235(n: int) -> int:
+    """Smallest integer >= n whose only prime factors are 2, 3 and 5."""
+    m = max(1, n)
+    while True:
+        r = m
+        for p in (2, 3, 5):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return m
+        m += 1
+
+
+def config4_spec(seed: int):
+    """The drawn parameters of instance `seed` of the batched uneven workload (reading of
+    SURVEY 8c item 15): n atoms uniform in [2, 64], cubic cell L = 10.26 (n/8)^(1/3) bohr, the
+    smallest c x c x c conventional supercell holding n diamond sites, a seeded choice of n of its
+    sites (fractional coordinates kept), N(0, 0.05 bohr) noise, N_occ = 2n, E_cut uniform in
+    [10, 25] Ry, n_omega uniform in [16, 256], N_pert uniform in [1, 16]; k = Gamma, q = 0 and the
+    N_pert shortest non-zero G; the FFT box is the smallest 2-3-5 size >= 2 m_rho + 1.
+    Draws: rng = default_rng(seed); n = rng.integers(2, 65); ecut = rng.uniform(10, 25);
+    n_omega = rng.integers(16, 257); n_pert = rng.integers(1, 17); sites = rng.permutation(8 c^3);
+    noise = rng.normal(0, 0.05, (n, 3))."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 65))
+    ecut = float(rng.uniform(10.0, 25.0))
+    n_omega = int(rng.integers(16, 257))
+    n_pert = int(rng.integers(1, 17))
+    c = 1
+    while 8 * c ** 3 < n:
+        c += 1
+    perm = rng.permutation(8 * c ** 3)
+    noise = rng.normal(0.0, 0.05, size=(n, 3))
+    L = 10.26 * (n / 8.0) ** (1.0 / 3.0)
+    sites = np.array([(np.array([i, j, k]) + f) / c for i in range(c) for j in range(c) for k in range(c)
+                      for f in DIAMOND_FRAC])
+    tau = sites[perm[:n]] * L + noise
+    a = np.eye(3) * L
+    mil, _ = sphere(a, (0.0, 0.0, 0.0), 4.0 * ecut, check_margin=False)
+    dims = tuple(smooth235(2 * int(np.abs(mil[:, i]).max()) + 1) for i in range(3))
+    npw = len(sphere(a, (0.0, 0.0, 0.0), ecut, check_margin=False)[0])
+    return {"seed": seed, "n_atoms": n, "ecut_ry": ecut, "n_omega": n_omega, "n_pert": n_pert, "a": a, "tau": tau,
+            "dims": dims, "n_pw": npw, "n_occ": 2 * n}
+
+
+def config4(seed: int, cache: bool = True):
+    """Instance `seed` (0..47) of the batched uneven workload (config4_spec), with its ground
+    state; omega = linspace(0, 60 eV, n_omega), eta = 0.1 eV."""
+    sp = config4_spec(seed)
+    omega = np.linspace(0.0, 60.0, sp["n_omega"]) / HA_EV
+    k = np.zeros(3)
+    return make_instance("uneven%d-n%d-ecut%.3f" % (seed, sp["n_atoms"], sp["ecut_ry"]), seed, sp["a"], sp["tau"],
+                         sp["ecut_ry"], sp["dims"], sp["n_occ"], [(k, k)],
+                         shortest_g(sp["a"], sp["n_pert"], False), omega, 0.1 / HA_EV, cache=cache)

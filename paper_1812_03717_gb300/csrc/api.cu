@@ -999,9 +999,20 @@ struct Carve {
 // operator (P_c H P_c with the system's occupied states, else H itself).  A pair is
 // converged when rel_res <= tol and its certificate <= cert_tol.  Returns SGW_ENOCONV, with X
 // and the report written, when a pair misses either.
+// The multishift pass of a packed multi-system launch (sgw_solve_batched): device per-pair
+// Krylov steps, recursive estimates and statistics, and the launch's kernel time.
+struct PassDone {
+    const int* mv;
+    const double* est;
+    const int* st;
+    double kernel_ms;
+    int launches;
+};
+
 static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double2* rhs_d, const double* e_ref,
                              int nomega, const double* omega, const double* eta_s, double eta, double tol,
-                             const sgw_solve_opts* opts, double2* X, sgw_report* report, cudaStream_t st) {
+                             const sgw_solve_opts* opts, double2* X, sgw_report* report, cudaStream_t st,
+                             const PassDone* done = nullptr) {
     const int method = opts ? opts->method : SGW_METHOD_LANCZOS;
     const int precision = opts ? opts->precision : SGW_PREC_FP64;
     const int threads = opts ? opts->threads : 0;
@@ -1032,7 +1043,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
     }
     if (seed >= nomega) return fail(SGW_EINVAL, "seed_index out of range");
     const bool lanczos = method == SGW_METHOD_LANCZOS;
-    const bool have_x0 = opts && opts->x0;
+    const bool have_x0 = opts && opts->x0 && !done;
     // plans: the pass in its precision; the FP64 check and the corrections in the 16-byte split
     // (corrections of an FP32 pass run in float-float: FP64 iterative refinement)
     Plan plan = precision == SGW_PREC_FP32 ? s->plan8 : s->plan;
@@ -1055,7 +1066,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
     const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : (lanczos ? 16384 : 40000);
     const int max_refine = !opts || opts->max_refine == 0 ? 3 : std::max(0, opts->max_refine);
     const int plain_budget = opts && opts->plain_budget > 0 ? opts->plain_budget : 0;
-    if (lanczos && !have_x0 && lanczos_smem_bytes(plan, nomega, precision) > max_optin_smem())
+    if (lanczos && !have_x0 && !done && lanczos_smem_bytes(plan, nomega, precision) > max_optin_smem())
         return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
     if (!lanczos && solve_smem_bytes(plan, nomega) > max_optin_smem())
         return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
@@ -1102,7 +1113,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
     }
     size_t wsb;
     if (lanczos)
-        wsb = std::max(have_x0 ? 0 : lanczos_bytes(own, own * plan.csize, nomega, maxk, eb),
+        wsb = std::max(have_x0 || done ? 0 : lanczos_bytes(own, own * plan.csize, nomega, maxk, eb),
                        lanczos_bytes(own1, own1 * plan16.csize, 1, maxk, vb));
     else
         wsb = (size_t)own * (vb * (2 * ell + 3) + vb * (size_t)nomega) + 4096;
@@ -1187,7 +1198,13 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         SGW_CUDA(cudaEventCreate(&ev1), "event");
         SGW_CUDA(cudaEventRecord(ev0, st), "event");
     }
-    if (have_x0) {
+    if (done) {
+        // 1''. the pass ran in a packed multi-system launch: take over its per-pair results
+        SGW_CUDA(cudaMemcpyAsync(w + o_mv, done->mv, sizeof(int) * np, cudaMemcpyDeviceToDevice, st), "pass copy");
+        SGW_CUDA(cudaMemcpyAsync(w + o_est, done->est, sizeof(double) * np, cudaMemcpyDeviceToDevice, st), "pass copy");
+        SGW_CUDA(cudaMemcpyAsync(w + o_st, done->st, sizeof(int) * np, cudaMemcpyDeviceToDevice, st), "pass copy");
+        launches += done->launches;
+    } else if (have_x0) {
         // 1'. resume from the caller's solutions: every pair goes straight to the check
         SGW_CUDA(cudaMemcpyAsync(X, opts->x0, vb * np, cudaMemcpyDefault, st), "x0 copy");
         SGW_CUDA(cudaMemsetAsync(w + o_mv, 0, sizeof(int) * np, st), "memset");
@@ -1251,7 +1268,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
     if (timed) {
         float ms = 0.f;
         SGW_CUDA(cudaEventElapsedTime(&ms, ev0, ev1), "event");
-        *report->kernel_ms = ms;
+        *report->kernel_ms = done ? done->kernel_ms : ms;
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
     }
@@ -1417,6 +1434,186 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     if ((r = finish_out(out, st, "dpsi copy")) != SGW_OK) return r;
     SGW_CUDA(cudaStreamSynchronize(st), "solve");
     return rs;
+}
+
+sgw_status sgw_solve_batched(int nitems, const sgw_batch_item* items, double eta, double tol,
+                             const sgw_solve_opts* opts) {
+    g_err.clear();
+    if (nitems < 0 || (nitems > 0 && !items)) return fail(SGW_EINVAL, "bad item list");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(SGW_EINVAL, "eta must be positive");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(SGW_EINVAL, "tol must be positive");
+    if (opts && opts->method != SGW_METHOD_LANCZOS) return fail(SGW_EUNSUPPORTED, "batched solves use the Lanczos method");
+    if (opts && opts->x0) return fail(SGW_EUNSUPPORTED, "batched solves take no x0");
+    const int precision = opts ? opts->precision : SGW_PREC_FP64;
+    if (precision != SGW_PREC_FP64 && precision != SGW_PREC_DF32 && precision != SGW_PREC_FP32)
+        return fail(SGW_EINVAL, "unknown precision");
+    const int threads = opts ? opts->threads : 0;
+    const double cert_tol = !opts || opts->cert_tol == 0.0 ? 1e-8 : opts->cert_tol;
+    if (nitems == 0) return SGW_OK;
+    const int dev = items[0].sys ? items[0].sys->dev : 0;
+    for (int i = 0; i < nitems; ++i) {
+        const sgw_batch_item& it = items[i];
+        if (!it.sys || !it.rhs || !it.e_ref || !it.omega || !it.dpsi) return fail(SGW_EINVAL, "NULL field in an item");
+        if (it.sys->dev != dev) return fail(SGW_EINVAL, "items on different devices");
+        if (it.nrhs < 0 || it.nomega < 1 || it.nomega > kMaxShifts) return fail(SGW_EINVAL, "item sizes out of range");
+        if (!finite_all(it.e_ref, it.nrhs) || !finite_all(it.omega, it.nomega))
+            return fail(SGW_EINVAL, "non-finite e_ref or omega");
+        if (it.sys->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
+        for (int j = 0; j < i; ++j)
+            if (items[j].sys == it.sys) return fail(SGW_EINVAL, "a system appears in two items (merge their rhs)");
+        const Plan& pl = precision == SGW_PREC_FP32 ? it.sys->plan8 : it.sys->plan;
+        if (pl.csize == 0) return fail(SGW_EUNSUPPORTED, "an item's box does not fit on chip in FP32");
+        if (lanczos_smem_bytes(pl, it.nomega, precision) > max_optin_smem())
+            return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
+    }
+    cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
+    SGW_CUDA(cudaSetDevice(dev), "cudaSetDevice");
+    const int es = prec_bytes(precision);
+    const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : 16384;
+    // every item's buffers on the device
+    std::vector<Staged> in(nitems), out(nitems);
+    sgw_status r;
+    for (int i = 0; i < nitems; ++i) {
+        const size_t vb = sizeof(double2) * (size_t)items[i].sys->npw;
+        if ((r = stage_in(items[i].rhs, vb * items[i].nrhs, in[i], st, "rhs")) != SGW_OK) return r;
+        if ((r = stage_out(items[i].dpsi, vb * (size_t)items[i].nrhs * items[i].nomega, out[i], "dpsi", st)) !=
+            SGW_OK)
+            return r;
+    }
+    // per-item device arrays: e_ref, omega and the pass's per-pair outputs
+    std::vector<size_t> o_er(nitems), o_om(nitems), o_mv(nitems), o_es(nitems), o_stt(nitems);
+    Carve c;
+    for (int i = 0; i < nitems; ++i) {
+        const size_t np = (size_t)items[i].nrhs * items[i].nomega;
+        o_er[i] = c.take(sizeof(double) * items[i].nrhs);
+        o_om[i] = c.take(sizeof(double) * items[i].nomega);
+        o_mv[i] = c.take(sizeof(int) * np);
+        o_es[i] = c.take(sizeof(double) * np);
+        o_stt[i] = c.take(sizeof(int) * np);
+    }
+    Staged small;
+    SGW_CUDA(cudaMallocAsync(&small.dev, c.off, st), "batch allocation");
+    small.owned = true;
+    small.st = st;
+    char* ws = (char*)small.dev;
+    for (int i = 0; i < nitems; ++i) {
+        SGW_CUDA(cudaMemcpyAsync(ws + o_er[i], items[i].e_ref, sizeof(double) * items[i].nrhs, cudaMemcpyHostToDevice,
+                                 st),
+                 "e_ref copy");
+        SGW_CUDA(cudaMemcpyAsync(ws + o_om[i], items[i].omega, sizeof(double) * items[i].nomega,
+                                 cudaMemcpyHostToDevice, st),
+                 "omega copy");
+    }
+    // items with the same cluster size share one persistent launch; the largest systems first
+    std::map<int, std::vector<int>> groups;
+    for (int i = 0; i < nitems; ++i) {
+        const Plan& pl = precision == SGW_PREC_FP32 ? items[i].sys->plan8 : items[i].sys->plan;
+        if (items[i].nrhs > 0) groups[pl.csize].push_back(i);
+    }
+    std::vector<double> group_ms(nitems, 0.0);
+    std::vector<int> group_launch(nitems, 0);
+    auto al256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    for (auto& kv : groups) {
+        std::vector<int> idx = kv.second;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return items[a].sys->npw > items[b].sys->npw; });
+        int smem = 0, max_npw = 0, max_ns = 0, total = 0;
+        for (int i : idx) {
+            const Plan& pl = precision == SGW_PREC_FP32 ? items[i].sys->plan8 : items[i].sys->plan;
+            smem = std::max(smem, lanczos_smem_bytes(pl, items[i].nomega, precision));
+            max_npw = std::max(max_npw, items[i].sys->npw);
+            max_ns = std::max(max_ns, items[i].nomega);
+            total += items[i].nrhs;
+        }
+        const Plan& p0 = precision == SGW_PREC_FP32 ? items[idx[0]].sys->plan8 : items[idx[0]].sys->plan;
+        int owners = 0;
+        SGW_CUDA(lanczos_batch_capacity(p0, threads, precision, smem, &owners), "solver occupancy");
+        owners = std::max(1, std::min(owners, total));
+        // every owner's basis sized for the largest system, capped by free memory
+        size_t free_b = 0, total_b = 0;
+        SGW_CUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+        const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+        const int ctas = owners * p0.csize;
+        const size_t per_k = (size_t)owners * es * max_npw + (size_t)ctas * (16 + 32 * (size_t)max_ns);
+        const size_t cap = budget / std::max<size_t>(per_k, 1);
+        if (cap < 8) return fail(SGW_ENOMEM, "not enough device memory for the Lanczos bases");
+        const int maxk = (int)std::min<size_t>((size_t)max_mv, cap - 2);
+        const size_t vstride = (size_t)(maxk + 1) * max_npw;
+        const size_t ystride = 2 * (size_t)maxk * max_ns;
+        const size_t o_ab = al256((size_t)owners * vstride * es);
+        const size_t o_ysc = o_ab + al256((size_t)ctas * 2 * (maxk + 1) * 8);
+        const size_t o_items = o_ysc + al256((size_t)ctas * ystride * 16);
+        const size_t o_start = o_items + al256(sizeof(BatchItem) * idx.size());
+        const size_t o_cnt = o_start + al256(sizeof(int) * (idx.size() + 1));
+        sgw_system* s0 = items[idx[0]].sys;
+        if ((r = ensure_ws(s0, o_cnt + 256)) != SGW_OK) return r;
+        char* w = (char*)s0->d_ws;
+        std::vector<BatchItem> hb(idx.size());
+        std::vector<int> start(idx.size() + 1, 0);
+        for (size_t t = 0; t < idx.size(); ++t) {
+            const int i = idx[t];
+            const Plan& pl = precision == SGW_PREC_FP32 ? items[i].sys->plan8 : items[i].sys->plan;
+            hb[t].plan = tuned_plan(pl, lanczos_extra(items[i].nomega), es);
+            LanczosArgs& A = hb[t].args;
+            A = LanczosArgs();
+            A.nrhs = items[i].nrhs;
+            A.nshift = items[i].nomega;
+            A.maxk = maxk;
+            A.rhs = (const double2*)in[i].dev;
+            A.e_ref = (const double*)(ws + o_er[i]);
+            A.omega = (const double*)(ws + o_om[i]);
+            A.eta = eta;
+            A.tol = tol;
+            A.cert_tol = cert_tol > 0.0 ? cert_tol : 0.0;
+            A.x = (double2*)out[i].dev;
+            A.basis = (double2*)w;
+            A.ab = (double*)(w + o_ab);
+            A.ysc = (double2*)(w + o_ysc);
+            A.counter = (int*)(w + o_cnt);
+            A.out_mv = (int*)(ws + o_mv[i]);
+            A.out_res = (double*)(ws + o_es[i]);
+            A.out_status = (int*)(ws + o_stt[i]);
+            A.vstride = vstride;
+            A.ystride = ystride;
+            start[t + 1] = start[t] + items[i].nrhs;
+        }
+        SGW_CUDA(cudaMemcpyAsync(w + o_items, hb.data(), sizeof(BatchItem) * hb.size(), cudaMemcpyHostToDevice, st),
+                 "items copy");
+        SGW_CUDA(cudaMemcpyAsync(w + o_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, st),
+                 "start copy");
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        SGW_CUDA(cudaEventCreate(&e0), "event");
+        SGW_CUDA(cudaEventCreate(&e1), "event");
+        SGW_CUDA(cudaEventRecord(e0, st), "event");
+        SGW_CUDA(launch_lanczos_batch(hb[0].plan, (const BatchItem*)(w + o_items), (const int*)(w + o_start),
+                                      (int)idx.size(), (int*)(w + o_cnt), owners, precision, threads, smem, st),
+                 "batched solver kernel");
+        SGW_CUDA(cudaEventRecord(e1, st), "event");
+        SGW_CUDA(cudaEventSynchronize(e1), "batched solver kernel");   // the workspace is reused next
+        float ms = 0.f;
+        SGW_CUDA(cudaEventElapsedTime(&ms, e0, e1), "event");
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (size_t t = 0; t < idx.size(); ++t) {
+            group_ms[idx[t]] = ms;
+            group_launch[idx[t]] = t == 0 ? 1 : 0;
+        }
+    }
+    // the FP64 check and the corrections of every item, as in sgw_solve_shifted
+    sgw_status worst = SGW_OK;
+    for (int i = 0; i < nitems; ++i) {
+        if (items[i].nrhs == 0) continue;
+        const PassDone done{(const int*)(ws + o_mv[i]), (const double*)(ws + o_es[i]), (const int*)(ws + o_stt[i]),
+                            group_ms[i], group_launch[i]};
+        const sgw_status rs = multishift(items[i].sys, true, items[i].nrhs, (const double2*)in[i].dev, items[i].e_ref,
+                                         items[i].nomega, items[i].omega, nullptr, eta, tol, opts,
+                                         (double2*)out[i].dev, items[i].report, st, &done);
+        if (rs != SGW_OK && rs != SGW_ENOCONV) return rs;
+        if (rs == SGW_ENOCONV) worst = rs;
+        if ((r = finish_out(out[i], st, "dpsi copy")) != SGW_OK) return r;
+    }
+    SGW_CUDA(cudaStreamSynchronize(st), "batched solve");
+    if (worst != SGW_OK) return fail(worst, "some (rhs, omega) pairs did not reach the tolerance or the certificate");
+    return SGW_OK;
 }
 
 sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, const double* z, double tol,

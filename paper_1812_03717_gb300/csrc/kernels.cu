@@ -1377,6 +1377,33 @@ cudaError_t lanczos_launch_f64(const Plan& P, const LanczosArgs& a, int owners, 
 cudaError_t lanczos_launch_df(const Plan& P, const LanczosArgs& a, int owners, int threads, cudaStream_t st);
 cudaError_t lanczos_launch_f32(const Plan& P, const LanczosArgs& a, int owners, int threads, cudaStream_t st);
 
+cudaError_t lanczos_batch_capacity_f64(const Plan& P, int threads, int smem, int* owners);
+cudaError_t lanczos_batch_capacity_df(const Plan& P, int threads, int smem, int* owners);
+cudaError_t lanczos_batch_capacity_f32(const Plan& P, int threads, int smem, int* owners);
+cudaError_t lanczos_batch_launch_f64(const Plan& P, const BatchItem* items, const int* start, int nitems, int* counter,
+                                     int owners, int threads, int smem, cudaStream_t st);
+cudaError_t lanczos_batch_launch_df(const Plan& P, const BatchItem* items, const int* start, int nitems, int* counter,
+                                    int owners, int threads, int smem, cudaStream_t st);
+cudaError_t lanczos_batch_launch_f32(const Plan& P, const BatchItem* items, const int* start, int nitems, int* counter,
+                                     int owners, int threads, int smem, cudaStream_t st);
+
+cudaError_t lanczos_batch_capacity(const Plan& P, int threads, int precision, int smem, int* owners) {
+    const int nt = lanczos_threads(threads, precision);
+    if (precision == SGW_PREC_DF32) return lanczos_batch_capacity_df(P, nt, smem, owners);
+    if (precision == SGW_PREC_FP32) return lanczos_batch_capacity_f32(P, nt, smem, owners);
+    return lanczos_batch_capacity_f64(P, nt, smem, owners);
+}
+
+cudaError_t launch_lanczos_batch(const Plan& P, const BatchItem* items, const int* start, int nitems, int* counter,
+                                 int owners, int precision, int threads, int smem, cudaStream_t st) {
+    const int nt = lanczos_threads(threads, precision);
+    if (precision == SGW_PREC_DF32)
+        return lanczos_batch_launch_df(P, items, start, nitems, counter, owners, nt, smem, st);
+    if (precision == SGW_PREC_FP32)
+        return lanczos_batch_launch_f32(P, items, start, nitems, counter, owners, nt, smem, st);
+    return lanczos_batch_launch_f64(P, items, start, nitems, counter, owners, nt, smem, st);
+}
+
 // CTA size: the requested 256 / 384 / 512, else the measured best for the precision (512 for
 // float-float and FP32, 384 for FP64 on the config-2 workload)
 int lanczos_threads(int requested, int precision) {

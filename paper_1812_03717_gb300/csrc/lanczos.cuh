@@ -36,13 +36,13 @@
 
 namespace sgw {
 
+// Right-hand side r of the system (P, A): the whole multishift solve by the CTA or cluster
+// that owns it.  All threads of every rank call.
 template <class Ar, int NT>
-__global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {
+__device__ __noinline__ void lanczos_rhs(const Plan& P, const LanczosArgs& A, unsigned char* smem, int r) {
     using C = typename Ar::C;
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double2 s_dot[kRedSlots];
-    __shared__ int s_r, s_nact, s_kmax, s_fail, s_more;
-    load_twiddles<Ar>(P, smem);
+    __shared__ int s_nact, s_kmax, s_fail, s_more;
     const ApplySmem L = apply_smem_layout(P, (int)sizeof(C));
     Red R = make_red(P, smem, L);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
@@ -61,28 +61,16 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
     int* kc = reinterpret_cast<int*>(smem + off); off = align16(off + ns * 4);
     int* st = reinterpret_cast<int*>(smem + off);
 
-    C* V = reinterpret_cast<C*>(A.basis) + (size_t)cl_id * (maxk + 1) * npw;
+    // per-owner basis, per-CTA recurrence scalars and coefficients (strides fixed per launch, so
+    // that systems of several sizes can share one workspace)
+    C* V = reinterpret_cast<C*>(A.basis) + (size_t)cl_id * A.vstride;
     double* al = A.ab + (size_t)blockIdx.x * 2 * (maxk + 1);     // alpha[0..maxk), beta[0..maxk]
     double* be = al + (maxk + 1);
-    double2* Ysc = A.ysc + (size_t)blockIdx.x * 2 * maxk * ns;   // [maxk][ns] y, [maxk][ns] l
+    double2* Ysc = A.ysc + (size_t)blockIdx.x * A.ystride;       // [maxk][ns] y, [maxk][ns] l
     double2* Lsc = Ysc + (size_t)maxk * ns;
     C* Yc = reinterpret_cast<C*>(Lsc);                          // y in the policy's format, after the sweeps
 
-    for (;;) {
-        int r;
-        if (P.csize == 1) {
-            __syncthreads();
-            if (tid == 0) s_r = atomicAdd(A.counter, 1);
-            __syncthreads();
-            r = s_r;
-        } else {
-            cg::cluster_group cl = cg::this_cluster();
-            if (q.rank == 0 && tid == 0) s_r = atomicAdd(A.counter, 1);
-            cl.sync();
-            r = *cl.map_shared_rank(&s_r, 0u);
-            cl.sync();   // rank 0 overwrites s_r, or exits, only after every rank has read it
-        }
-        if (r >= A.nrhs) break;
+    {
         const double2* rhs = A.rhs + (size_t)r * npw;
         double2* X = A.x + (size_t)r * ns * npw;
 
@@ -323,6 +311,64 @@ __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArg
     }
 }
 
+// The next work item of the launch for this owner: rank 0 of a cluster takes it from the
+// queue and every rank reads it (rank 0 overwrites it, or exits, only after all have read).
+__device__ __forceinline__ int next_item(const Plan& P, int* counter) {
+    __shared__ int s_r;
+    if (P.csize == 1) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
+        __syncthreads();
+        return s_r;
+    }
+    cg::cluster_group cl = cg::this_cluster();
+    if (cl.block_rank() == 0 && threadIdx.x == 0) s_r = atomicAdd(counter, 1);
+    cl.sync();
+    const int r = *cl.map_shared_rank(&s_r, 0u);
+    cl.sync();
+    return r;
+}
+
+// One system: a work queue hands its right-hand sides to the owners.
+template <class Ar, int NT>
+__global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    load_twiddles<Ar>(P, smem);
+    for (;;) {
+        const int r = next_item(P, A.counter);
+        if (r >= A.nrhs) break;
+        lanczos_rhs<Ar, NT>(P, A, smem, r);
+    }
+}
+
+// Several systems (uneven sizes, one cluster size) in one persistent launch: the queue hands
+// out (system, right-hand side) items in the order of the items array (the host puts the
+// costliest systems first); start[i] is the first queue index of system i.
+template <class Ar, int NT>
+__global__ void __launch_bounds__(NT, 1) lanczos_batch_kernel(const BatchItem* __restrict__ items, const int* __restrict__ start,
+                                                             int nitems, int* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int total = start[nitems];
+    int cur = -1;
+    for (;;) {
+        const int t = next_item(items[0].plan, counter);
+        if (t >= total) break;
+        int lo = 0, hi = nitems - 1;   // the system holding queue index t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const Plan& P = items[lo].plan;
+        if (lo != cur) {
+            __syncthreads();   // the previous system's twiddles are no longer read
+            load_twiddles<Ar>(P, smem);
+            cur = lo;
+        }
+        lanczos_rhs<Ar, NT>(P, items[lo].args, smem, t - start[lo]);
+    }
+}
+
 template <class Ar>
 const void* lanczos_ptr_t(int nt) {
     if (nt == 512) return (const void*)lanczos_solve_kernel<Ar, 512>;
@@ -342,14 +388,39 @@ cudaError_t lanczos_capacity_t(const Plan& P, int nshift, int threads, int* owne
 }
 
 template <class Ar>
-cudaError_t lanczos_launch_t(const Plan& P0, const LanczosArgs& a, int owners, int threads, cudaStream_t st) {
+cudaError_t lanczos_launch_t(const Plan& P0, const LanczosArgs& a0, int owners, int threads, cudaStream_t st) {
     const int es = (int)sizeof(typename Ar::C);
-    const Plan P = tuned_plan(P0, lanczos_extra(a.nshift), es);
-    const int smem = lanczos_smem_t<Ar>(P0, a.nshift);
+    const Plan P = tuned_plan(P0, lanczos_extra(a0.nshift), es);
+    const int smem = lanczos_smem_t<Ar>(P0, a0.nshift);
+    LanczosArgs a = a0;
+    if (a.vstride == 0) a.vstride = (size_t)(a.maxk + 1) * P.npw;
+    if (a.ystride == 0) a.ystride = 2 * (size_t)a.maxk * a.nshift;
     cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&P, (void*)&a};
     return launch_owned(lanczos_ptr_t<Ar>(threads), P, owners, threads, smem, st, args);
+}
+
+template <class Ar>
+const void* lanczos_batch_ptr_t(int nt) {
+    if (nt == 512) return (const void*)lanczos_batch_kernel<Ar, 512>;
+    if (nt == 384) return (const void*)lanczos_batch_kernel<Ar, 384>;
+    return (const void*)lanczos_batch_kernel<Ar, 256>;
+}
+
+// items: device array (plans already tuned for smem bytes of dynamic shared memory).
+template <class Ar>
+cudaError_t lanczos_batch_launch_t(const Plan& P0, const BatchItem* items, const int* start, int nitems, int* counter,
+                                   int owners, int threads, int smem, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&items, (void*)&start, (void*)&nitems, (void*)&counter};
+    return launch_owned(lanczos_batch_ptr_t<Ar>(threads), P0, owners, threads, smem, st, args);
+}
+
+template <class Ar>
+cudaError_t lanczos_batch_capacity_t(const Plan& P, int threads, int smem, int* owners) {
+    return owner_capacity(lanczos_batch_ptr_t<Ar>(threads), P, threads, smem, owners);
 }
 
 }  // namespace sgw

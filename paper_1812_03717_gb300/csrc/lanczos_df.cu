@@ -14,4 +14,13 @@ cudaError_t lanczos_launch_df(const Plan& P, const LanczosArgs& a, int owners, i
     return lanczos_launch_t<ArDF>(P, a, owners, threads, st);
 }
 
+cudaError_t lanczos_batch_capacity_df(const Plan& P, int threads, int smem, int* owners) {
+    return lanczos_batch_capacity_t<ArDF>(P, threads, smem, owners);
+}
+
+cudaError_t lanczos_batch_launch_df(const Plan& P, const BatchItem* items, const int* start, int nitems, int* counter,
+                                    int owners, int threads, int smem, cudaStream_t st) {
+    return lanczos_batch_launch_t<ArDF>(P, items, start, nitems, counter, owners, threads, smem, st);
+}
+
 }  // namespace sgw

@@ -104,6 +104,14 @@ struct LanczosArgs {
     const double* eta_s = nullptr;   // [nshift]
     const double* eta_r = nullptr;   // [nrhs]
     double cert_tol = 0.0;           // > 0: shifts also stop only once |r| / (|Im z| |x|) <= cert_tol
+    size_t vstride = 0;              // basis elements per owner (0: (maxk + 1) npw)
+    size_t ystride = 0;              // y / l coefficients per CTA (0: 2 maxk nshift)
+};
+
+// One system of a packed multi-system launch.
+struct BatchItem {
+    Plan plan;
+    LanczosArgs args;
 };
 
 // Bytes per complex value of a precision's arithmetic policy.
@@ -124,6 +132,10 @@ int lanczos_smem_bytes(const Plan& P, int nshift, int precision);
 cudaError_t lanczos_capacity(const Plan& P, int nshift, int threads, int precision, int* owners);
 cudaError_t launch_lanczos(const Plan& P, const LanczosArgs& a, int owners, int precision, int threads,
                            cudaStream_t st);
+// Packed launch of several systems sharing the cluster size of P (items, start on the device).
+cudaError_t lanczos_batch_capacity(const Plan& P, int threads, int precision, int smem, int* owners);
+cudaError_t launch_lanczos_batch(const Plan& P, const BatchItem* items, const int* start, int nitems, int* counter,
+                                 int owners, int precision, int threads, int smem, cudaStream_t st);
 int solve_smem_bytes(const Plan& P, int nshift);
 int apply_smem_bytes(const Plan& P, int es);
 cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid);

@@ -24,7 +24,7 @@ STATUS_NAMES = ["SGW_OK", "SGW_EINVAL", "SGW_ENOMEM", "SGW_ECUDA", "SGW_ENOCONV"
                 "SGW_EUNSUPPORTED"]
 
 EXPORTS = ["sgw_create_system", "sgw_get_gvectors", "sgw_get_box_map", "sgw_set_split", "sgw_get_split",
-           "sgw_solve_capacity",
+           "sgw_solve_capacity", "sgw_solve_batched",
            "sgw_set_occupied", "sgw_make_rhs",
            "sgw_apply_h", "sgw_apply_shifted", "sgw_solve_shifted", "sgw_solve_green", "sgw_density_response", "sgw_density_response_w", "sgw_aaa", "sgw_screened_coulomb", "sgw_residual", "sgw_residual_noalloc",
            "sgw_solve_pershift", "sgw_precond_diag", "sgw_training_rows", "sgw_mlp_create", "sgw_mlp_get_params",
@@ -80,6 +80,41 @@ def _report(nr, nw):
     return rep, _Report(*(rep[k].ctypes.data for k in _REPORT_KEYS))
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("sys", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("rhs", ctypes.c_void_p), ("e_ref", ctypes.c_void_p),
+                ("nomega", ctypes.c_int), ("omega", ctypes.c_void_p), ("dpsi", ctypes.c_void_p),
+                ("report", ctypes.c_void_p)]
+
+
+def solve_batched(items, eta, tol=1e-10, precision="fp64", threads=0, max_matvec=0, max_refine=0, cert_tol=0.0,
+                  stream=None, raise_on_noconv=False):
+    """sgw_solve_batched: items is a list of dicts {sys, rhs, e_ref, omega[, out]} (systems of
+    uneven sizes); returns (list of dpsi, list of report dicts, converged flag)."""
+    keep, citems, outs, reps = [], [], [], []
+    for it in items:
+        rhs = _c128(it["rhs"])
+        e_ref = np.ascontiguousarray(it["e_ref"], dtype=np.float64)
+        om = np.ascontiguousarray(it["omega"], dtype=np.float64)
+        nr, nw = rhs.shape[0], len(om)
+        out = it.get("out")
+        if out is None:
+            out = _like(rhs, (nr, nw, it["sys"].n_pw))
+        rep, crep = _report(nr, nw)
+        keep += [rhs, e_ref, om, out, crep]
+        citems.append(_BatchItem(it["sys"]._h.value, nr, _ptr(rhs), e_ref.ctypes.data, nw, om.ctypes.data, _ptr(out),
+                                 ctypes.addressof(crep)))
+        outs.append(out)
+        reps.append(rep)
+    arr = (_BatchItem * len(citems))(*citems)
+    st = stream if stream is not None else (_stream_of(outs[0], None) if outs else None)
+    opts = _opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads), st,
+                 float(cert_tol))
+    s = load().sgw_solve_batched(len(citems), ctypes.cast(arr, ctypes.c_void_p), float(eta), float(tol),
+                                 ctypes.byref(opts))
+    _check(s, allow=() if raise_on_noconv else (SGW_ENOCONV,))
+    return outs, reps, s == SGW_OK
+
+
 _lib = None
 
 
@@ -98,6 +133,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sgw_set_split.argtypes = [vp, ip]
     lib.sgw_get_split.argtypes = [vp, vp, vp]
     lib.sgw_solve_capacity.argtypes = [vp, ip, ip, ip, vp]
+    lib.sgw_solve_batched.argtypes = [ip, vp, dp, dp, ctypes.POINTER(_Opts)]
     lib.sgw_set_occupied.argtypes = [vp, ip, vp, vp]
     lib.sgw_make_rhs.argtypes = [vp, vp, ip, vp, ip, vp, vp, vp]
     lib.sgw_apply_h.argtypes = [vp, ip, vp, vp, ip, vp]
