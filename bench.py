@@ -537,6 +537,85 @@ def run_secondary(args, P, dev, stream, ws, rank):
         out["learned_preconditioner"] = measure_learned(P, inst, jobs, k0, dev)
     for j in jobs:
         j["sys"].close()
+    jobs.clear()
+    torch.cuda.empty_cache()
+    if not args.no_extras:
+        out["batched_uneven"] = measure_batched(P, dev, variants[0])
+    for j in jobs:
+        j["sys"].close()
+    return out
+
+
+BATCH_SEEDS = (27, 23, 42, 30, 34, 35, 14, 11, 47, 38, 25, 37, 43, 46, 31)
+
+
+def measure_batched(P, dev, precision, rhs_cap=32):
+    """The batched uneven workload's 15 instances with at most 3000 plane waves (2 to 43 atoms,
+    boxes 15^3 to 36^3, 16 to 234 frequencies), up to `rhs_cap` right-hand sides each, solved
+    (1) packed: sgw_solve_batched, one persistent launch for all (CTA size from the autotuner);
+    (2) sequential: one sgw_solve_shifted per instance; (3) concurrent: one stream and host thread
+    per instance.  Certified solves/s of each, after one untimed packed run."""
+    import torch
+    import instances as I
+    from paper_1812_03717_gb300 import autotune as T
+    from paper_1812_03717_gb300.batch import solve_concurrent
+    t0 = time.perf_counter()
+    jobs = []
+    for seed in BATCH_SEEDS:
+        inst = I.config4(seed)
+        kp = inst.kpoints[0]
+        s = P.System.from_instance(inst, kp.kq_frac)
+        sk = P.System.from_instance(inst, kp.k_frac)
+        s.set_occupied(torch.from_numpy(kp.psi_kq).to(dev), kp.eps_kq)
+        rhs = s.make_rhs(sk, torch.from_numpy(kp.psi_k).to(dev), inst.gp_miller)[:rhs_cap].contiguous()
+        sk.close()
+        out = torch.empty((rhs.shape[0], len(inst.omega), s.n_pw), dtype=torch.complex128, device=dev)
+        jobs.append({"inst": inst, "sys": s, "rhs": rhs, "e_ref": inst.e_ref(0)[:rhs.shape[0]], "omega": inst.omega,
+                     "out": out})
+    gen_s = time.perf_counter() - t0
+    big = max(jobs, key=lambda j: j["sys"].n_pw)
+    tune = T.tune(big["sys"], big["rhs"], big["e_ref"], big["omega"], big["inst"].eta, big["inst"].fft_dims,
+                  big["inst"].n_occ, len(big["inst"].kb_atom), precision=precision, probe_steps=40)
+    nt = tune["threads"] or 0
+    eta = jobs[0]["inst"].eta
+    items = [{"sys": j["sys"], "rhs": j["rhs"], "e_ref": j["e_ref"], "omega": j["omega"], "out": j["out"]} for j in jobs]
+    pairs = sum(j["rhs"].shape[0] * len(j["omega"]) for j in jobs)
+
+    def certified(reps):
+        return sum(int(((r["status"] == 0) & (r["cert"] <= 1e-8)).sum()) for r in reps)
+
+    P.solve_batched(items, eta, tol=1e-10, precision=precision, threads=nt)
+    torch.cuda.synchronize()
+    res = {}
+    t = time.perf_counter()
+    _, reps, _ = P.solve_batched(items, eta, tol=1e-10, precision=precision, threads=nt)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    res["packed"] = {"value": certified(reps) / dt, "s": dt, "launches": int(sum(int(r["launches"][0]) for r in reps)),
+                     "kernel_ms": float(reps[0]["kernel_ms"][0])}
+    t = time.perf_counter()
+    reps = []
+    for j in jobs:
+        _, rep, _ = j["sys"].solve_shifted(j["rhs"], j["e_ref"], j["omega"], eta, tol=1e-10, precision=precision,
+                                           out=j["out"])
+        reps.append(rep)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    res["sequential"] = {"value": certified(reps) / dt, "s": dt}
+    t = time.perf_counter()
+    cres = solve_concurrent([{"sys": j["sys"], "rhs": j["rhs"], "e_ref": j["e_ref"], "out": j["out"]} for j in jobs],
+                            None, eta, tol=1e-10, precision=precision, omegas=[j["omega"] for j in jobs])
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    res["concurrent_streams"] = {"value": certified([r for r, _ in cres]) / dt, "s": dt}
+    out = {"metric": "batched uneven Sternheimer (rhs x omega) solves/s at 1e-8, certified",
+           "instances": [{"seed": j["inst"].seed, "n_pw": j["sys"].n_pw, "box": list(j["inst"].fft_dims),
+                          "rhs": int(j["rhs"].shape[0]), "omega": len(j["omega"])} for j in jobs],
+           "pairs": pairs, "precision": precision, "generate_s": round(gen_s, 1),
+           "autotune": {"threads": tune["threads"], "csize": tune["csize"], "timed": tune.get("timed", [])},
+           "packed": res["packed"], "sequential": res["sequential"], "concurrent_streams": res["concurrent_streams"],
+           "packed_vs_sequential": res["packed"]["value"] / res["sequential"]["value"],
+           "packed_vs_concurrent": res["packed"]["value"] / res["concurrent_streams"]["value"]}
     return out
 
 

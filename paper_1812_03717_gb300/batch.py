@@ -10,9 +10,11 @@ from __future__ import annotations
 import threading
 
 
-def solve_concurrent(jobs, omega, eta, tol=1e-10, **kwargs):
+def solve_concurrent(jobs, omega, eta, tol=1e-10, omegas=None, **kwargs):
     """jobs: list of dicts with keys sys, rhs, e_ref, out (CUDA tensors, or pinned host tensors
-    that the library stages on each job's stream).  Returns [(report, converged)] in job order."""
+    that the library stages on each job's stream); every job solves at `omega`, or job i at
+    omegas[i].  Returns [(report, converged)] in job order.  (sgw_solve_batched packs several
+    systems into one persistent launch instead.)"""
     import torch
     results = [None] * len(jobs)
     errors = []
@@ -26,7 +28,8 @@ def solve_concurrent(jobs, omega, eta, tol=1e-10, **kwargs):
         try:
             with torch.cuda.stream(streams[i]):
                 j = jobs[i]
-                _, rep, ok = j["sys"].solve_shifted(j["rhs"], j["e_ref"], omega, eta, tol=tol, out=j["out"],
+                om = omegas[i] if omegas is not None else omega
+                _, rep, ok = j["sys"].solve_shifted(j["rhs"], j["e_ref"], om, eta, tol=tol, out=j["out"],
                                                     stream=streams[i].cuda_stream, **kwargs)
                 results[i] = (rep, ok)
         except Exception as e:  # re-raised in the caller's thread
