@@ -1100,27 +1100,47 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         return al256((size_t)owners * (size_t)(mk + 1) * vbytes) + al256((size_t)ctas * 2 * (size_t)(mk + 1) * 8) +
                (size_t)ctas * 2 * (size_t)mk * ns * 16 + 4096;
     };
-    if (lanczos) {
-        size_t free_b = 0, total_b = 0;
-        SGW_CUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-        const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
-        const size_t per_k = std::max<size_t>((size_t)own * (eb + 16 * plan.csize) + (size_t)own * plan.csize * 32 *
-                                                  (size_t)nomega,
-                                              (size_t)own1 * (vb + 16 * plan16.csize + 32 * plan16.csize));
+    // The Krylov workspaces are allocated for the duration of the call only (stream-ordered), so
+    // systems solved one after another or side by side do not keep each other's bases.  The pass
+    // basis is capped by half the free device memory; a correction solve (one shift, a fraction
+    // of a digit or a few digits to gain) gets at most 4096 steps and one owner per pair.
+    size_t free_b = 0, total_b = 0;
+    SGW_CUDA(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+    const size_t budget = std::min<size_t>(free_b / 2, (size_t)96 << 30);
+    const bool pass = !have_x0 && !done;
+    if (lanczos && pass) {
+        const size_t per_k = (size_t)own * (eb + 16 * plan.csize) + (size_t)own * plan.csize * 32 * (size_t)nomega;
         const size_t cap = budget / std::max<size_t>(per_k, 1);
         if (cap < 8) return fail(SGW_ENOMEM, "not enough device memory for a Lanczos basis");
         maxk = (int)std::min<size_t>((size_t)max_mv, cap - 2);
     }
-    size_t wsb;
-    if (lanczos)
-        wsb = std::max(have_x0 || done ? 0 : lanczos_bytes(own, own * plan.csize, nomega, maxk, eb),
-                       lanczos_bytes(own1, own1 * plan16.csize, 1, maxk, vb));
-    else
-        wsb = (size_t)own * (vb * (2 * ell + 3) + vb * (size_t)nomega) + 4096;
-    if (bicg_corr)
-        wsb = std::max(wsb, (size_t)grid_b * vb * (2 * ell + 6) + 4096);   // BiCGstab seeds, directions, scratch
+    int maxk_c = std::min(max_mv, 4096);
+    {
+        const size_t per_k = (size_t)own1 * (vb + 16 * plan16.csize + 32 * plan16.csize);
+        const size_t cap = budget / std::max<size_t>(per_k, 1);
+        if (cap < 8) return fail(SGW_ENOMEM, "not enough device memory for a correction basis");
+        maxk_c = (int)std::min<size_t>((size_t)maxk_c, cap - 2);
+    }
+    size_t pass_bytes = 0;
+    if (pass) {
+        pass_bytes = lanczos ? lanczos_bytes(own, own * plan.csize, nomega, maxk, eb)
+                             : (size_t)own * (vb * (2 * ell + 3) + vb * (size_t)nomega) + 4096;
+    }
+    auto corr_bytes = [&](int nc) -> size_t {
+        if (!bicg_corr) {
+            const int o = std::min(own1, nc);
+            return lanczos_bytes(o, o * plan16.csize, 1, maxk_c, vb);
+        }
+        return (size_t)std::min(grid_b, nc) * vb * (2 * ell + 6) + 4096;   // BiCGstab seeds, directions, scratch
+    };
+    Staged passbuf;
+    if (pass_bytes) {
+        SGW_CUDA(cudaMallocAsync(&passbuf.dev, pass_bytes, st), "Krylov workspace");
+        passbuf.owned = true;
+        passbuf.st = st;
+    }
+    char* pw = (char*)passbuf.dev;
     Carve c;
-    const size_t o_solver = c.take(wsb);
     const size_t o_eref = c.take(sizeof(double) * nrhs);
     const size_t o_om = c.take(sizeof(double) * nomega);
     const size_t o_sig = c.take(sizeof(double) * nomega);
@@ -1161,13 +1181,14 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
 
     // One Lanczos launch: z_rj = e_ref_d[r] + omega_d[j] + i Im z, with Im z = eta_r_d[r], else
     // eta_s_d[j], else eta.
-    auto run_lanczos = [&](const Plan& pl, int prec, int nr, int ns, const double2* rhs_d, const double* e_ref_d,
-                           const double* omega_d, double tl, double ctl, double2* x_d, int* mv_d, double* est_d,
-                           int* st_d, int owners, const double* eta_s_d, const double* eta_r_d) -> cudaError_t {
+    auto run_lanczos = [&](char* base, int mk, const Plan& pl, int prec, int nr, int ns, const double2* rhs_d,
+                           const double* e_ref_d, const double* omega_d, double tl, double ctl, double2* x_d, int* mv_d,
+                           double* est_d, int* st_d, int owners, const double* eta_s_d,
+                           const double* eta_r_d) -> cudaError_t {
         LanczosArgs L;
         L.nrhs = nr;
         L.nshift = ns;
-        L.maxk = maxk;
+        L.maxk = mk;
         L.rhs = rhs_d;
         L.e_ref = e_ref_d;
         L.omega = omega_d;
@@ -1175,12 +1196,11 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         L.tol = tl;
         L.cert_tol = ctl;
         L.x = x_d;
-        char* base = w + o_solver;
         const size_t vbytes = (size_t)prec_bytes(prec) * s->npw;
-        const size_t o_ab = al256((size_t)owners * (maxk + 1) * vbytes);
+        const size_t o_ab = al256((size_t)owners * (mk + 1) * vbytes);
         L.basis = (double2*)base;
         L.ab = (double*)(base + o_ab);
-        L.ysc = (double2*)(base + o_ab + al256((size_t)owners * pl.csize * 2 * (size_t)(maxk + 1) * 8));
+        L.ysc = (double2*)(base + o_ab + al256((size_t)owners * pl.csize * 2 * (size_t)(mk + 1) * 8));
         L.counter = (int*)(w + o_cnt);
         L.out_mv = mv_d;
         L.out_res = est_d;
@@ -1212,7 +1232,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         SGW_CUDA(cudaMemsetAsync(w + o_est, 0, sizeof(double) * np, st), "memset");
     } else if (lanczos) {
         // 1. multishift pass
-        SGW_CUDA(run_lanczos(plan, precision, nrhs, nomega, rhs_d, (const double*)(w + o_eref),
+        SGW_CUDA(run_lanczos(pw, maxk, plan, precision, nrhs, nomega, rhs_d, (const double*)(w + o_eref),
                              (const double*)(w + o_om), tol, use_cert ? cert_tol : 0.0, X, (int*)(w + o_mv),
                              (double*)(w + o_est), (int*)(w + o_st), own, d_etas, nullptr),
                  "solver kernel");
@@ -1230,8 +1250,8 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         A.eta = eta;
         A.tol = tol;
         A.x = X;
-        A.seedw = (double2*)(w + o_solver);
-        A.uw = (double2*)(w + o_solver + (size_t)own * vb * (2 * ell + 3));
+        A.seedw = (double2*)pw;
+        A.uw = (double2*)(pw + (size_t)own * vb * (2 * ell + 3));
         A.counter = (int*)(w + o_cnt);
         A.out_mv = (int*)(w + o_mv);
         A.out_res = (double*)(w + o_est);
@@ -1282,6 +1302,11 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
                (relv[q] > tol || (use_cert && certv[q] > cert_tol)) && (have_x0 || relv[q] <= 1e-3);
     };
 
+    if (passbuf.dev) {   // the pass's basis is released before the corrections
+        SGW_CUDA(cudaFreeAsync(passbuf.dev, st), "Krylov workspace");
+        passbuf.dev = nullptr;
+    }
+
     // 3. per-shift correction solves for pairs above tol or the certificate target:
     //    A_j d = r_j, x_j += d (Lanczos in the correction precision, or preconditioned BiCGstab)
     std::vector<int> list, mv1(chunk);
@@ -1317,13 +1342,18 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
             SGW_CUDA(cudaMemcpyAsync(w + o_eta1, eta1.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st),
                      "list copy");
             const int* d_list = (const int*)(w + o_list);
+            Staged corrbuf;   // this chunk's Krylov workspace
+            SGW_CUDA(cudaMallocAsync(&corrbuf.dev, corr_bytes(nc), st), "correction workspace");
+            corrbuf.owned = true;
+            corrbuf.st = st;
+            char* cw = (char*)corrbuf.dev;
             SGW_CUDA(launch_residual(plan16, nrhs, nomega, d_list, nc, rhs_d, d_eref, d_om, eta, X,
                                      (double2*)(w + o_rscr), d_rel, d_cert, (double2*)(w + o_rvec),
                                      std::min(own_r, nc), st, d_etas, d_b, res_prec, 1),
                      "residual kernel");
             const double tl = std::min(0.5, std::max(1e-13, 0.3 * need));
             if (!bicg_corr) {
-                SGW_CUDA(run_lanczos(plan16, corr_prec, nc, 1, (const double2*)(w + o_rvec),
+                SGW_CUDA(run_lanczos(cw, maxk_c, plan16, corr_prec, nc, 1, (const double2*)(w + o_rvec),
                                      (const double*)(w + o_eref1), (const double*)(w + o_zero), tl, 0.0,
                                      (double2*)(w + o_dbuf), (int*)(w + o_mv1), (double*)(w + o_est1),
                                      (int*)(w + o_st1), std::min(own1, nc), nullptr, (const double*)(w + o_eta1)),
@@ -1362,9 +1392,9 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
                 A.tol = tl;
                 A.x = (double2*)(w + o_dbuf);
                 const int gb = std::min(grid_b, nc);
-                A.seedw = (double2*)(w + o_solver);
-                A.uw = (double2*)(w + o_solver + (size_t)gb * vb * (2 * ell + 3));
-                A.pscr = (double2*)(w + o_solver + (size_t)gb * vb * (2 * ell + 4));
+                A.seedw = (double2*)cw;
+                A.uw = (double2*)(cw + (size_t)gb * vb * (2 * ell + 3));
+                A.pscr = (double2*)(cw + (size_t)gb * vb * (2 * ell + 4));
                 A.pre = pc != SGW_PRECOND_NONE ? (const double*)(w + o_pre) : nullptr;
                 A.counter = (int*)(w + o_cnt);
                 A.out_mv = (int*)(w + o_mv1);
@@ -1544,9 +1574,11 @@ sgw_status sgw_solve_batched(int nitems, const sgw_batch_item* items, double eta
         const size_t o_items = o_ysc + al256((size_t)ctas * ystride * 16);
         const size_t o_start = o_items + al256(sizeof(BatchItem) * idx.size());
         const size_t o_cnt = o_start + al256(sizeof(int) * (idx.size() + 1));
-        sgw_system* s0 = items[idx[0]].sys;
-        if ((r = ensure_ws(s0, o_cnt + 256)) != SGW_OK) return r;
-        char* w = (char*)s0->d_ws;
+        Staged gbuf;   // the group's Krylov workspace, for this launch only
+        SGW_CUDA(cudaMallocAsync(&gbuf.dev, o_cnt + 256, st), "batch workspace");
+        gbuf.owned = true;
+        gbuf.st = st;
+        char* w = (char*)gbuf.dev;
         std::vector<BatchItem> hb(idx.size());
         std::vector<int> start(idx.size() + 1, 0);
         for (size_t t = 0; t < idx.size(); ++t) {
