@@ -272,8 +272,14 @@ __device__ __noinline__ void lanczos_rhs(const Plan& P, const LanczosArgs& A, un
                 const bool active = jg < wj;
                 const int stride = 8 * wj;   // staged y of one step
                 const int KC = (L.red - L.sticks) / (stride * (int)sizeof(C));
-                int Kt = 0;   // the tile's longest Lanczos run (y is zero beyond each shift's own)
-                for (int t = 0; t < cnt; ++t) Kt = max(Kt, st[j0 + t] == SGW_PAIR_NONFINITE ? 0 : kc[j0 + t]);
+                // the tile's longest Lanczos run, and this warp's (y is zero beyond each shift's own
+                // stopping step: a warp whose shifts stopped early skips the rest of the chunks)
+                int Kt = 0, Kw = 0;
+                for (int t = 0; t < cnt; ++t) {
+                    const int kt = st[j0 + t] == SGW_PAIR_NONFINITE ? 0 : kc[j0 + t];
+                    Kt = max(Kt, kt);
+                    if (active && t >= 8 * jg && t < 8 * jg + 8) Kw = max(Kw, kt);
+                }
                 for (int gb = g0; gb < g1; gb += 32 * wg) {
                     const int g = gb + 32 * gs + lane;
                     const bool in = active && g < g1;
@@ -283,16 +289,16 @@ __device__ __noinline__ void lanczos_rhs(const Plan& P, const LanczosArgs& A, un
                     for (int k0 = 0; k0 < Kt; k0 += KC) {
                         const int kn = min(KC, Kt - k0);
                         __syncthreads();
-                        for (int i = tid; i < kn * stride; i += nt) {
-                            const int ii = i / stride, t = i - ii * stride;
-                            ys[i] = t < cnt ? Yc[(size_t)(k0 + ii) * ns + j0 + t] : Ar::zero();
-                        }
+                        for (int ii = warp; ii < kn; ii += nw)
+                            for (int t = lane; t < stride; t += 32)
+                                ys[ii * stride + t] = t < cnt ? Yc[(size_t)(k0 + ii) * ns + j0 + t] : Ar::zero();
                         __syncthreads();
-                        if (in) {
+                        const int kk = min(kn, Kw - k0);
+                        if (in && kk > 0) {
                             const C* vg = V + (size_t)k0 * npw + g;
                             const C* yb = ys + 8 * jg;
 #pragma unroll 2
-                            for (int i = 0; i < kn; ++i) {
+                            for (int i = 0; i < kk; ++i) {
                                 const C v = vg[(size_t)i * npw];
                                 const C* yr = yb + i * stride;
 #pragma unroll
