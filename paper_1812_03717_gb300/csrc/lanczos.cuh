@@ -36,76 +36,6 @@
 
 namespace sgw {
 
-// x_j = V y_j for the shifts of one right-hand side over the plane waves [g0, g1) (the caller's
-// rank), from the basis V [k][npw] and the coefficients Yc [k][ns] in the policy's format.  A
-// function of its own: its accumulators do not add to the register pressure of the Krylov
-// loop.  All threads of the CTA call.
-template <class Ar>
-__device__ __noinline__ void lanczos_xvy(const ApplySmem& L, unsigned char* smem, const typename Ar::C* V,
-                                         const typename Ar::C* Yc, const int* kc, const int* st, int ns, int npw,
-                                         int g0, int g1, double2* X) {
-    using C = typename Ar::C;
-    // x_j = V y_j over this rank's plane waves.  A tile takes up to 8 nw shifts (nw warps):
-    // the shifts fall into groups of 8, wj groups per tile, and the warps into wj x wg with
-    // wg = nw / wj, so warp (jg, gs) accumulates shifts [8 jg, 8 jg + 8) of the plane waves
-    // gb + 32 gs + lane, a block of 32 wg plane waves per pass.  Every basis element is loaded
-    // once per tile -- once in all for up to 8 nw shifts (128 at 512 threads); the warps of a
-    // block share it through L1 -- and each solution element is written once.  The tile's y
-    // coefficients are staged in the idle FFT buffers, KC steps at a time, and read as
-    // broadcasts.
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    C* ys = reinterpret_cast<C*>(smem + L.sticks);
-    for (int j0 = 0; j0 < ns; j0 += 8 * nw) {
-        const int cnt = min(8 * nw, ns - j0);
-        const int wj = (cnt + 7) >> 3, wg = nw / wj;
-        const int jg = warp / wg, gs = warp - jg * wg;
-        const bool active = jg < wj;
-        const int stride = 8 * wj;   // staged y of one step
-        const int KC = (L.red - L.sticks) / (stride * (int)sizeof(C));
-        // the tile's longest Lanczos run, and this warp's (y is zero beyond each shift's own
-        // stopping step: a warp whose shifts stopped early skips the rest of the chunks)
-        int Kt = 0, Kw = 0;
-        for (int t = 0; t < cnt; ++t) {
-            const int kt = st[j0 + t] == SGW_PAIR_NONFINITE ? 0 : kc[j0 + t];
-            Kt = max(Kt, kt);
-            if (active && t >= 8 * jg && t < 8 * jg + 8) Kw = max(Kw, kt);
-        }
-        for (int gb = g0; gb < g1; gb += 32 * wg) {
-            const int g = gb + 32 * gs + lane;
-            const bool in = active && g < g1;
-            C acc[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) acc[t] = Ar::zero();
-            for (int k0 = 0; k0 < Kt; k0 += KC) {
-                const int kn = min(KC, Kt - k0);
-                __syncthreads();
-                for (int ii = warp; ii < kn; ii += nw)
-                    for (int t = lane; t < stride; t += 32)
-                        ys[ii * stride + t] = t < cnt ? Yc[(size_t)(k0 + ii) * ns + j0 + t] : Ar::zero();
-                __syncthreads();
-                const int kk = min(kn, Kw - k0);
-                if (in && kk > 0) {
-                    const C* vg = V + (size_t)k0 * npw + g;
-                    const C* yb = ys + 8 * jg;
-#pragma unroll 2
-                    for (int i = 0; i < kk; ++i) {
-                        const C v = vg[(size_t)i * npw];
-                        const C* yr = yb + i * stride;
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) acc[t] = Ar::add(acc[t], Ar::mul(yr[t], v));
-                    }
-                }
-            }
-            if (in) {
-#pragma unroll
-                for (int t = 0; t < 8; ++t)
-                    if (8 * jg + t < cnt) X[(size_t)(j0 + 8 * jg + t) * npw + g] = Ar::to_d(acc[t]);
-            }
-        }
-    }
-}
-
 // Right-hand side r of the system (P, A): the whole multishift solve by the CTA or cluster
 // that owns it.  All threads of every rank call.
 template <class Ar, int NT>
@@ -324,7 +254,52 @@ __device__ __noinline__ void lanczos_rhs(const Plan& P, const LanczosArgs& A, un
             for (int i = 0; i < K; ++i) Yc[(size_t)i * ns + j] = i < kj ? Ar::from_d(Ysc[(size_t)i * ns + j]) : Ar::zero();
         }
         __syncthreads();
-        lanczos_xvy<Ar>(L, smem, V, Yc, kc, st, ns, npw, g0, g1, X);
+        // x_j = V y_j over this rank's plane waves, shifts in tiles of TJ.  The tile's y
+        // coefficients are staged in the (now idle) FFT buffers of shared memory, KC Lanczos
+        // steps at a time; every thread reads them as broadcasts.
+        constexpr int TJ = NT >= 384 ? 4 : 8;
+        {
+            C* ys = reinterpret_cast<C*>(smem + L.sticks);
+            const int KC = (L.red - L.sticks) / (TJ * (int)sizeof(C));
+            for (int j0 = 0; j0 < ns; j0 += TJ) {
+                const int cnt = min(TJ, ns - j0);
+                int Kt = 0;   // the tile's longest Lanczos run (y is zero beyond each shift's own)
+                for (int t = 0; t < cnt; ++t) Kt = max(Kt, st[j0 + t] == SGW_PAIR_NONFINITE ? 0 : kc[j0 + t]);
+                if (Kt == 0)
+                    for (int t = 0; t < cnt; ++t)
+                        for (int g = g0 + tid; g < g1; g += nt) X[(size_t)(j0 + t) * npw + g] = cz();
+                for (int k0 = 0; k0 < Kt; k0 += KC) {
+                    const int kn = min(KC, Kt - k0);
+                    __syncthreads();
+                    for (int i = tid; i < kn * TJ; i += nt) {
+                        const int ii = i / TJ, t = i - ii * TJ;
+                        ys[i] = t < cnt ? Yc[(size_t)(k0 + ii) * ns + j0 + t] : Ar::zero();
+                    }
+                    __syncthreads();
+                    for (int g = g0 + tid; g < g1; g += nt) {
+                        C acc[TJ];
+#pragma unroll
+                        for (int t = 0; t < TJ; ++t) acc[t] = Ar::zero();
+                        const C* vg = V + (size_t)k0 * npw + g;
+#pragma unroll 2
+                        for (int i = 0; i < kn; ++i) {
+                            const C v = vg[(size_t)i * npw];
+                            const C* yr = ys + i * TJ;
+#pragma unroll
+                            for (int t = 0; t < TJ; ++t) acc[t] = Ar::add(acc[t], Ar::mul(yr[t], v));
+                        }
+#pragma unroll
+                        for (int t = 0; t < TJ; ++t) {
+                            if (t < cnt) {
+                                double2* xo = X + (size_t)(j0 + t) * npw + g;
+                                const double2 d = Ar::to_d(acc[t]);
+                                *xo = k0 == 0 ? d : cadd(*xo, d);
+                            }
+                        }
+                    }
+                }
+            }
+        }
         if (q.rank == 0) {
             for (int j = tid; j < ns; j += nt) {
                 A.out_status[(size_t)r * ns + j] = st[j];
