@@ -277,6 +277,13 @@ struct ArF64 {
     static __device__ __forceinline__ C kinx(const Plan& P, int g, C x) { return cscal(x, P.kin[g]); }
     // |a|^2 accumulated into the real part of acc
     static __device__ __forceinline__ C acc_norm(C acc, C a) { return make_double2(acc.x + cabs2(a), acc.y); }
+    // long sums (dots and projections): the accumulator is a value of the policy's type
+    using A = C;
+    static __device__ __forceinline__ A acc_of(C a) { return a; }
+    static __device__ __forceinline__ void acc_cmac(A& a, C r, C x) { a = add(a, mul(conj(r), x)); }   // a += conj(r) x
+    static __device__ __forceinline__ void acc_mac(A& a, C c, C p) { a = add(a, mul(c, p)); }          // a += c p
+    static __device__ __forceinline__ void acc_msub(A& a, C c, C p) { a = sub(a, mul(c, p)); }         // a -= c p
+    static __device__ __forceinline__ C acc_val(A a) { return a; }
 };
 
 struct dd {
@@ -373,6 +380,47 @@ struct ArDF {
         const dd m = dd_add(dd_mul(re(a), re(a)), dd_mul(im(a), im(a)));
         return mk(dd_add(re(acc), m), im(acc));
     }
+    // Long sums (the projector and occupied-state dots and projections) accumulate lazily:
+    // per part an unevaluated pair (s, e) -- the leading products enter s by TwoSum, and e
+    // gathers their exact rounding errors (FMA), the TwoSum errors and the hi * lo cross
+    // terms -- renormalised once at the end (48 FP32 operations per complex term instead of
+    // 60 for a float-float multiply and add; the same terms are kept, and the error of the
+    // sum stays at the float-float level: e's own rounding is 2^-24 of terms that are
+    // themselves 2^-24 of the products).
+    using A = float4;   // (s_re, e_re, s_im, e_im); a float-float value (hi, lo) is such a pair
+    // (s, e) += a b + c d for the (hi, lo) words (a, al), (b, bl), (c, cl), (d, dl)
+    static __device__ __forceinline__ void lazy2(float& s, float& e, float a, float al, float b, float bl, float c,
+                                                 float cl, float d, float dl) {
+        const float p = __fmul_rn(a, b), q = __fmul_rn(c, d);   // not fused into the sums below
+        const float ep = fmaf(a, b, -p), eq = fmaf(c, d, -q);
+        const float s1 = s + p, b1 = s1 - s;
+        const float t1 = (s - (s1 - b1)) + (p - b1);
+        const float s2 = s1 + q, b2 = s2 - s1;
+        const float t2 = (s1 - (s2 - b2)) + (q - b2);
+        float f = e + ((ep + eq) + (t1 + t2));
+        f = fmaf(a, bl, f);
+        f = fmaf(al, b, f);
+        f = fmaf(c, dl, f);
+        f = fmaf(cl, d, f);
+        s = s2;
+        e = f;
+    }
+    static __device__ __forceinline__ A acc_of(C a) { return a; }
+    static __device__ __forceinline__ void acc_cmac(A& a, C r, C x) {   // a += conj(r) x
+        lazy2(a.x, a.y, r.x, r.y, x.x, x.y, r.z, r.w, x.z, x.w);       // rr xr + ri xi
+        lazy2(a.z, a.w, r.x, r.y, x.z, x.w, -r.z, -r.w, x.x, x.y);     // rr xi - ri xr
+    }
+    static __device__ __forceinline__ void acc_mac(A& a, C c, C p) {    // a += c p
+        lazy2(a.x, a.y, c.x, c.y, p.x, p.y, -c.z, -c.w, p.z, p.w);     // cr pr - ci pi
+        lazy2(a.z, a.w, c.x, c.y, p.z, p.w, c.z, c.w, p.x, p.y);       // cr pi + ci pr
+    }
+    static __device__ __forceinline__ void acc_msub(A& a, C c, C p) {   // a -= c p
+        acc_mac(a, make_float4(-c.x, -c.y, -c.z, -c.w), p);
+    }
+    static __device__ __forceinline__ C acc_val(A a) {   // TwoSum of each pair
+        const float hr = a.x + a.y, br = hr - a.x, hi = a.z + a.w, bi = hi - a.z;
+        return make_float4(hr, (a.x - (hr - br)) + (a.y - br), hi, (a.z - (hi - bi)) + (a.w - bi));
+    }
 };
 
 // Single precision: complex64 values, FP32 arithmetic and accumulation.
@@ -404,6 +452,13 @@ struct ArF32 {
     static __device__ __forceinline__ C acc_norm(C acc, C a) {
         return make_float2(fmaf(a.x, a.x, fmaf(a.y, a.y, acc.x)), acc.y);
     }
+    // long sums (dots and projections): the accumulator is a value of the policy's type
+    using A = C;
+    static __device__ __forceinline__ A acc_of(C a) { return a; }
+    static __device__ __forceinline__ void acc_cmac(A& a, C r, C x) { a = add(a, mul(conj(r), x)); }   // a += conj(r) x
+    static __device__ __forceinline__ void acc_mac(A& a, C c, C p) { a = add(a, mul(c, p)); }          // a += c p
+    static __device__ __forceinline__ void acc_msub(A& a, C c, C p) { a = sub(a, mul(c, p)); }         // a -= c p
+    static __device__ __forceinline__ C acc_val(A a) { return a; }
 };
 
 // Real constants of the small DFTs as (double, float hi, float lo).
@@ -559,33 +614,70 @@ struct DotRows {
 };
 
 // out[v] = sum_g conj(row_v[g]) x[g] for v < nv over the plane waves of the vector's owners.
-// The rows come in groups of 8; the (group, slice) work items -- a slice being every
+// The rows come in groups of kDotRows; the (group, slice) work items -- a slice being every
 // slices-th 32-wide chunk of the plane waves -- are spread over the warps, so both many rows
 // (the occupied states of a large cell) and few rows keep every warp busy.  Each item is
 // summed within its warp in the policy's arithmetic; the per-slice partials (FP64) are
 // summed by one thread per row; one block barrier, and the cluster sum in FP64 (rank order).
 // out (and the cluster partial buffer) must hold nv rounded up to 8.
+constexpr int kDotRows = 4;          // rows per warp work item
+constexpr bool kDotPrefetch = true;   // loads of the next pass before the arithmetic
+constexpr int kDotChunks = 1;        // 32-wide plane-wave chunks per pass
+
 template <class Ar, int WHICH>
 __device__ __forceinline__ void part_dots_rows(const Plan& P, const Part& q, Red& R, int nv, const DotRows<Ar, WHICH>& row,
                                                const typename Ar::C* x, double2* out) {
     using C = typename Ar::C;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double2* dst = P.csize == 1 ? out : R.part + R.par * R.stride;
-    const int ngroups = (nv + 7) >> 3;
+    constexpr int RW = kDotRows;
+    const int ngroups = (nv + RW - 1) / RW;
     const int slices = max(1, nw / max(ngroups, 1));
     for (int t = warp; t < ngroups * slices; t += nw) {
         const int gi = t / slices, sl = t - gi * slices;
-        const int v0 = gi * 8, cnt = min(8, nv - v0);
-        C acc[8];
+        const int v0 = gi * RW, cnt = min(RW, nv - v0);
+        const int gs = 32 * slices;
+        typename Ar::A a[RW];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = Ar::zero();
-        for (int g = q.g0 + sl * 32 + lane; g < q.g1; g += 32 * slices) {
-            const C xv = x[g];
+        for (int i = 0; i < RW; ++i) a[i] = Ar::acc_of(Ar::zero());
+        int g = q.g0 + sl * 32 + lane;
+        // U chunks of 32 plane waves per pass: their loads first, then their arithmetic;
+        // with kDotPrefetch the next pass's loads are issued before this pass's arithmetic.
+        // Rows past the end of a chunk read as zeros, which add nothing.
+        constexpr int U = kDotChunks;
+        C xn[U], rn[U][RW];
+        auto load = [&](int gb) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (i < cnt) acc[i] = Ar::add(acc[i], Ar::mul(Ar::conj(row(v0 + i, g)), xv));
+            for (int u = 0; u < U; ++u) {
+                const int gg = gb + u * gs;
+                const bool ok = gg < q.g1;
+                xn[u] = ok ? x[gg] : Ar::zero();
+#pragma unroll
+                for (int i = 0; i < RW; ++i) rn[u][i] = (ok && i < cnt) ? row(v0 + i, gg) : Ar::zero();
+            }
+        };
+        if constexpr (kDotPrefetch) load(g);
+        for (; g < q.g1; g += U * gs) {
+            if constexpr (!kDotPrefetch) load(g);
+            C xv[U], rv[U][RW];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                xv[u] = xn[u];
+#pragma unroll
+                for (int i = 0; i < RW; ++i) rv[u][i] = rn[u][i];
+            }
+            if constexpr (kDotPrefetch)
+                if (g + U * gs < q.g1) load(g + U * gs);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int i = 0; i < RW; ++i)
+                    if (i < cnt) Ar::acc_cmac(a[i], rv[u][i], xv[u]);
         }
-        warp_sum_c<8>(acc);
+        C acc[RW];
+#pragma unroll
+        for (int i = 0; i < RW; ++i) acc[i] = Ar::acc_val(a[i]);
+        warp_sum_c<RW>(acc);
         if (lane == 0) {
             for (int i = 0; i < cnt; ++i) {
                 const double2 d = Ar::to_d(acc[i]);
@@ -1003,9 +1095,10 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
     {
         const typename Ar::R invn = Ar::real(P.inv_nbox);
         for (int g = g0 + tid; g < g1; g += nt) {
-            C h = Ar::add(Ar::scalr(sticks[P.g2s[g]], invn), Ar::kinx(P, g, x[g]));
-            for (int p = 0; p < P.nproj; ++p) h = Ar::add(h, Ar::mul(coefc[p], Ar::beta(P, (size_t)p * npw + g)));
-            y[g] = h;
+            typename Ar::A h = Ar::acc_of(Ar::add(Ar::scalr(sticks[P.g2s[g]], invn), Ar::kinx(P, g, x[g])));
+#pragma unroll 8
+            for (int p = 0; p < P.nproj; ++p) Ar::acc_mac(h, coefc[p], Ar::beta(P, (size_t)p * npw + g));
+            y[g] = Ar::acc_val(h);
         }
     }
     __syncthreads();
@@ -1016,8 +1109,10 @@ __device__ __noinline__ void apply_h_block(const Plan& P, unsigned char* smem, c
         __syncthreads();
         const C zc = Ar::from_d(zsh);
         for (int g = g0 + tid; g < g1; g += nt) {
-            C h = y[g];
-            for (int v = 0; v < P.nocc; ++v) h = Ar::sub(h, Ar::mul(coefc[v], Ar::psi(P, (size_t)v * npw + g)));
+            typename Ar::A a = Ar::acc_of(y[g]);
+#pragma unroll 8
+            for (int v = 0; v < P.nocc; ++v) Ar::acc_msub(a, coefc[v], Ar::psi(P, (size_t)v * npw + g));
+            C h = Ar::acc_val(a);
             if (mode & APPLY_SUB_Z) h = Ar::sub(h, Ar::mul(zc, x[g]));
             y[g] = h;
         }
