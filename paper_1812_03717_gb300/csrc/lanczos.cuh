@@ -277,22 +277,22 @@ __device__ __noinline__ void lanczos_rhs(const Plan& P, const LanczosArgs& A, un
                     }
                     __syncthreads();
                     for (int g = g0 + tid; g < g1; g += nt) {
-                        typename Ar::A acc[TJ];
+                        C acc[TJ];
 #pragma unroll
-                        for (int t = 0; t < TJ; ++t) acc[t] = Ar::acc_of(Ar::zero());
+                        for (int t = 0; t < TJ; ++t) acc[t] = Ar::zero();
                         const C* vg = V + (size_t)k0 * npw + g;
 #pragma unroll 2
                         for (int i = 0; i < kn; ++i) {
                             const C v = vg[(size_t)i * npw];
                             const C* yr = ys + i * TJ;
 #pragma unroll
-                            for (int t = 0; t < TJ; ++t) Ar::acc_mac(acc[t], yr[t], v);
+                            for (int t = 0; t < TJ; ++t) acc[t] = Ar::add(acc[t], Ar::mul(yr[t], v));
                         }
 #pragma unroll
                         for (int t = 0; t < TJ; ++t) {
                             if (t < cnt) {
                                 double2* xo = X + (size_t)(j0 + t) * npw + g;
-                                const double2 d = Ar::to_d(Ar::acc_val(acc[t]));
+                                const double2 d = Ar::to_d(acc[t]);
                                 *xo = k0 == 0 ? d : cadd(*xo, d);
                             }
                         }

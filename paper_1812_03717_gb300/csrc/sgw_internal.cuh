@@ -386,7 +386,11 @@ struct ArDF {
     // terms -- renormalised once at the end (48 FP32 operations per complex term instead of
     // 60 for a float-float multiply and add; the same terms are kept, and the error of the
     // sum stays at the float-float level: e's own rounding is 2^-24 of terms that are
-    // themselves 2^-24 of the products).
+    // themselves 2^-24 of the products).  That holds for short sums only: e grows with the
+    // number of terms n and its own rounding with it (about n^2 2^-48 of the largest partial
+    // sum at worst), so the lazy form serves the per-thread sums of a few hundred terms (the
+    // dots' per-lane partials, the projections over the occupied states and projectors) and
+    // not the sums over thousands of Lanczos steps in x = V y.
     using A = float4;   // (s_re, e_re, s_im, e_im); a float-float value (hi, lo) is such a pair
     // (s, e) += a b + c d for the (hi, lo) words (a, al), (b, bl), (c, cl), (d, dl)
     static __device__ __forceinline__ void lazy2(float& s, float& e, float a, float al, float b, float bl, float c,
