@@ -48,7 +48,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070   # 80.5 TFLOP/s
 # DRAM bytes (read + write) per right-hand side and Lanczos step of the dominant kernel, from
 # the ncu capture in profiles/ (16 right-hand sides x 100 steps of the supercell); a launch's
 # traffic is this times its steps.  None: not captured since the kernel last changed.
-TRAFFIC_PER_RHS_STEP = {}
+TRAFFIC_PER_RHS_STEP = {"df32": (19.133e9 + 1.363e9) / 1600}
 
 
 def dist_env():
