@@ -441,8 +441,8 @@ def smooth235(n: int) -> int:
 
 
 def config4_spec(seed: int):
-    """The drawn parameters of instance `seed` of the batched uneven workload (reading of
-    SURVEY 8c item 15): n atoms uniform in [2, 64], cubic cell L = 10.26 (n/8)^(1/3) bohr, the
+    """The drawn parameters of instance `seed` of the batched uneven workload (48 seeded
+    instances of uneven size): n atoms uniform in [2, 64], cubic cell L = 10.26 (n/8)^(1/3) bohr, the
     smallest c x c x c conventional supercell holding n diamond sites, a seeded choice of n of its
     sites (fractional coordinates kept), N(0, 0.05 bohr) noise, N_occ = 2n, E_cut uniform in
     [10, 25] Ry, n_omega uniform in [16, 256], N_pert uniform in [1, 16]; k = Gamma, q = 0 and the
