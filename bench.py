@@ -550,7 +550,7 @@ BATCH_SEEDS = (27, 23, 42, 30, 34, 35, 14, 11, 47, 38, 25, 37, 43, 46, 31)
 
 
 def measure_batched(P, dev, precision, rhs_cap=32):
-    """The batched uneven workload's 15 instances with at most 3000 plane waves (2 to 43 atoms,
+    """The batched uneven workload's 15 instances with at most 3000 plane waves (2 to 36 atoms,
     boxes 15^3 to 36^3, 16 to 234 frequencies), up to `rhs_cap` right-hand sides each, solved
     (1) packed: sgw_solve_batched, one persistent launch for all (CTA size from the autotuner);
     (2) sequential: one sgw_solve_shifted per instance; (3) concurrent: one stream and host thread
