@@ -180,7 +180,7 @@ typedef struct {
                          tolerances get per-shift correction solves */
     int precond;      /* SGW_PRECOND_* of the per-shift correction solves: NONE -> shifted Lanczos
                          (one shift), PLAIN / LEARNED -> right-preconditioned BiCGstab(ell)
-                         (one CTA per vector systems only; else SGW_EUNSUPPORTED) */
+                         (one CTA per vector, or one cluster when the box is split) */
     const sgw_mlp* mlp;  /* the perceptron of SGW_PRECOND_LEARNED */
     int plain_budget; /* SGW_PRECOND_LEARNED: the plain preconditioner's typical (median) H
                          applications for systems of this size; the learned round stops at twice

@@ -1059,8 +1059,6 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
     }
     const int res_prec = precision == SGW_PREC_FP64 ? SGW_PREC_FP64 : SGW_PREC_DF32;
     const int corr_prec = precision == SGW_PREC_FP32 ? SGW_PREC_DF32 : precision;
-    if (precond != SGW_PRECOND_NONE && plan16.csize > 1)
-        return fail(SGW_EUNSUPPORTED, "preconditioned corrections need a box that fits one CTA");
     // Lanczos keeps its basis: the default budget of 16384 steps (further capped by free device
     // memory) bounds its memory; the 64-atom cell's highest frequencies need some 14 000 steps
     const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : (lanczos ? 16384 : 40000);
@@ -1963,7 +1961,6 @@ sgw_status sgw_solve_pershift(sgw_system* s, int npairs, const void* rhs, const 
     sgw_status r;
     if ((r = stage_in(rhs, vb * npairs, in, st, "rhs")) != SGW_OK) return r;
     if ((r = stage_out(x, vb * npairs, out, "x", st)) != SGW_OK) return r;
-    if (s->plan.csize > 1) return fail(SGW_EUNSUPPORTED, "per-shift BiCGstab needs a box that fits one CTA");
     int grid = 0, grid_r = 0;
     SGW_CUDA(solve_grid(s->plan, 1, npairs, &grid), "solver occupancy");
     SGW_CUDA(residual_owners(s->plan, SGW_PREC_FP64, &grid_r), "residual occupancy");

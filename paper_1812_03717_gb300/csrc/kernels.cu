@@ -107,47 +107,54 @@ __device__ __forceinline__ double2 cpowr(double2 a, int e) {
 
 }  // namespace
 
+// Dots out[v] = sum_g conj(V[v ld + g]) x[g], v < nv, over the vector's owners: the CTA's
+// block dots when one CTA holds the box, the warp-split dots and the rank-ordered cluster sum
+// when the box is split over a cluster.
+__device__ __forceinline__ void owner_dots(const Plan& P, const Part& q, Red& Rd, const double2* V, int nv, int ld,
+                                           const double2* x, double2* out) {
+    if (P.csize == 1) block_dots(V, nv, ld, x, P.npw, Rd.red, out);
+    else part_dots_f64(P, q, Rd, V, nv, ld, x, out);
+}
+
 // out = A D in with A = P_c H P_c - z and D = diag(pre) (right preconditioning of a
 // single-shift system): T1 = D in, T2 = P_c T1, out = P_c H T2 - z T1.  Without `pre` the
-// Krylov vectors already lie in range(P_c) and out = P_c H in - z in.
-// (One CTA per vector: the launcher refuses plans split over a cluster.)
-static __device__ void apply_op(const Plan& P, unsigned char* smem, const double2* in, double2* out, double2 zs,
-                                const double* pre, double2* t1, double2* t2) {
-    const ApplySmem L = apply_smem_layout(P, 16);
-    const Part q = make_part(P);
-    Red R = make_red(P, smem, L);
+// Krylov vectors already lie in range(P_c) and out = P_c H in - z in.  Each rank of a
+// cluster reads and writes its own plane waves [q.g0, q.g1) of every vector only.
+static __device__ void apply_op(const Plan& P, unsigned char* smem, const Part& q, Red& Rd, const double2* in,
+                                double2* out, double2 zs, const double* pre, double2* t1, double2* t2) {
     if (!pre) {
-        apply_h_block<ArF64>(P, smem, q, R, in, out, zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
+        apply_h_block<ArF64>(P, smem, q, Rd, in, out, zs, APPLY_PROJ_OUT | APPLY_SUB_Z);
         return;
     }
-    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    const ApplySmem L = apply_smem_layout(P, 16);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
-    const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x;
-    for (int g = tid; g < npw; g += nt) t1[g] = cscal(in[g], pre[g]);
+    const int npw = P.npw, tid = threadIdx.x, nt = blockDim.x, g0 = q.g0, g1 = q.g1;
+    for (int g = g0 + tid; g < g1; g += nt) t1[g] = cscal(in[g], pre[g]);
     __syncthreads();
-    block_dots(P.psi, P.nocc, npw, t1, npw, red, coef);
-    for (int g = tid; g < npw; g += nt) {
+    owner_dots(P, q, Rd, P.psi, P.nocc, npw, t1, coef);
+    for (int g = g0 + tid; g < g1; g += nt) {
         double2 h = t1[g];
         for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
         t2[g] = h;
     }
     __syncthreads();
-    apply_h_block<ArF64>(P, smem, q, R, t2, out, cz(), APPLY_PROJ_OUT);
-    for (int g = tid; g < npw; g += nt) out[g] = csub(out[g], cmul(zs, t1[g]));
+    apply_h_block<ArF64>(P, smem, q, Rd, t2, out, cz(), APPLY_PROJ_OUT);
+    for (int g = g0 + tid; g < g1; g += nt) out[g] = csub(out[g], cmul(zs, t1[g]));
     __syncthreads();
 }
 
 __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SeedScalars S;
-    __shared__ int s_r;
     __shared__ double2 s_dot[kRedSlots];
 
     load_twiddles<ArF64>(P, smem);
     const ApplySmem L = apply_smem_layout(P, 16);
-    double2* red = reinterpret_cast<double2*>(smem + L.red);
+    Red Rd = make_red(P, smem, L);
+    const Part q = make_part(P);
     double2* coef = reinterpret_cast<double2*>(smem + L.coef);
     const int ns = A.nshift, ell = A.ell, npw = P.npw;
+    const int g0 = q.g0, g1 = q.g1;
     const ShiftSmem Q = shift_layout(L.end, ns);
     double2* zp = reinterpret_cast<double2*>(smem + Q.zp);
     double2* zc = reinterpret_cast<double2*>(smem + Q.zc);
@@ -167,7 +174,8 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
     int* act = reinterpret_cast<int*>(smem + Q.act);
 
     const int tid = threadIdx.x, nt = blockDim.x;
-    double2* W = A.seedw + (size_t)blockIdx.x * (2 * ell + 3) * npw;
+    const int own = blockIdx.x / P.csize;   // the owner (CTA, or cluster) of the workspace slices
+    double2* W = A.seedw + (size_t)own * (2 * ell + 3) * npw;
     double2* R[kMaxEll + 1];
     double2* U[kMaxEll + 1];
     for (int i = 0; i <= kMaxEll; ++i) {
@@ -175,16 +183,13 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
         U[i] = W + (size_t)(ell + 1 + min(i, ell)) * npw;
     }
     double2* RT = W + (size_t)(2 * ell + 2) * npw;
-    double2* UW = A.uw + (size_t)blockIdx.x * ns * npw;
-    double2* T1 = A.pscr ? A.pscr + (size_t)blockIdx.x * 2 * npw : nullptr;
+    double2* UW = A.uw + (size_t)own * ns * npw;
+    double2* T1 = A.pscr ? A.pscr + (size_t)own * 2 * npw : nullptr;
     double2* T2 = T1 ? T1 + npw : nullptr;
     for (int j = tid; j < ns; j += nt) sig[j] = A.sig[j];
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_r = atomicAdd(A.counter, 1);
-        __syncthreads();
-        const int r = s_r;
+        const int r = next_item(P, A.counter);
         if (r >= A.nrhs) break;
         const double2* rhs = A.rhs + (size_t)r * npw;
         double2* X = A.x + (size_t)r * ns * npw;
@@ -192,10 +197,10 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
         const double* pre = A.pre ? A.pre + (size_t)r * npw : nullptr;   // single-shift systems only
 
         // b = -P_c rhs (Eq. 8 with the sign of the problem statement)
-        block_dots(P.psi, P.nocc, npw, rhs, npw, red, coef);
+        owner_dots(P, q, Rd, P.psi, P.nocc, npw, rhs, coef);
         {
             double2 acc[1] = {cz()};
-            for (int g = tid; g < npw; g += nt) {
+            for (int g = g0 + tid; g < g1; g += nt) {
                 double2 h = rhs[g];
                 for (int v = 0; v < P.nocc; ++v) h = csub(h, cmul(coef[v], P.psi[(size_t)v * npw + g]));
                 const double2 b = make_double2(-h.x, -h.y);
@@ -204,12 +209,13 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                 U[0][g] = cz();
                 acc[0].x += cabs2(b);
             }
-            block_sum<1>(acc, red, s_dot);
+            part_sum<1>(P, Rd, acc, s_dot);
         }
-        for (size_t i = tid; i < (size_t)ns * npw; i += nt) {
-            X[i] = cz();
-            UW[i] = cz();
-        }
+        for (int j = 0; j < ns; ++j)
+            for (int g = g0 + tid; g < g1; g += nt) {
+                X[(size_t)j * npw + g] = cz();
+                UW[(size_t)j * npw + g] = cz();
+            }
         if (tid == 0) {
             S.bnorm = sqrt(s_dot[0].x);
             S.rho0 = make_double2(1.0, 0.0);
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
             __syncthreads();
             // ---------------------------------------------------------------- BiCG part
             for (int j = 0; j < ell; ++j) {
-                block_dots(RT, 1, 0, R[j], npw, red, s_dot);
+                owner_dots(P, q, Rd, RT, 1, 0, R[j], s_dot);
                 if (tid == 0) {
                     const double2 rho1 = s_dot[0];
                     S.beta = cdiv(cmul(S.alpha, rho1), S.rho0);
@@ -255,12 +261,12 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                 if (S.fail) break;
                 {
                     const double2 be = S.beta;
-                    for (int g = tid; g < npw; g += nt)
+                    for (int g = g0 + tid; g < g1; g += nt)
                         for (int i = 0; i <= j; ++i) U[i][g] = csub(R[i][g], cmul(be, U[i][g]));
                 }
                 __syncthreads();
-                apply_op(P, smem, U[j], U[j + 1], zs, pre, T1, T2);
-                block_dots(RT, 1, 0, U[j + 1], npw, red, s_dot);
+                apply_op(P, smem, q, Rd, U[j], U[j + 1], zs, pre, T1, T2);
+                owner_dots(P, q, Rd, RT, 1, 0, U[j + 1], s_dot);
                 if (tid == 0) {
                     const double2 gam = s_dot[0];
                     if (gam.x == 0.0 && gam.y == 0.0) S.fail = SGW_PAIR_BREAKDOWN;
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                 // shift pass: u_j <- cr r + bs u_j ;  x_j <- x_j + as u_j
                 {
                     const int na = S.nact;
-                    for (int g = tid; g < npw; g += nt) {
+                    for (int g = g0 + tid; g < g1; g += nt) {
                         const double2 r0 = R[0][g];
                         for (int a = 0; a < na; ++a) {
                             const int k = act[a];
@@ -306,11 +312,11 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                 __syncthreads();
                 {
                     const double2 al = S.alpha;
-                    for (int g = tid; g < npw; g += nt)
+                    for (int g = g0 + tid; g < g1; g += nt)
                         for (int i = 0; i <= j; ++i) R[i][g] = csub(R[i][g], cmul(al, U[i + 1][g]));
                 }
                 __syncthreads();
-                apply_op(P, smem, R[j], R[j + 1], zs, pre, T1, T2);
+                apply_op(P, smem, q, Rd, R[j], R[j + 1], zs, pre, T1, T2);
                 for (int a = tid; a < S.nact; a += nt) {
                     const int k = act[a];
                     zp[k] = zc[k];
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                 double2 acc[14];
 #pragma unroll
                 for (int i = 0; i < 14; ++i) acc[i] = cz();
-                for (int g = tid; g < npw; g += nt) {
+                for (int g = g0 + tid; g < g1; g += nt) {
                     double2 rv[kMaxEll + 1];
 #pragma unroll
                     for (int t = 0; t <= kMaxEll; ++t) rv[t] = t <= ell ? R[t][g] : cz();
@@ -349,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                     for (int i = 1; i <= kMaxEll; ++i) acc[9 + i] = cadd(acc[9 + i], cmulc(rv[i], rv[0]));
                 }
                 // 10 Gram entries (indices 0..9) + 4 projections (10..13)
-                block_sum<14>(acc, red, s_dot);
+                part_sum<14>(P, Rd, acc, s_dot);
                 if (tid == 0) {
                     double2 M[kMaxEll][kMaxEll], v[kMaxEll], g[kMaxEll];
                     int q = 0;
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
             {
                 const int na = S.nact;
                 double2 acc[1] = {cz()};
-                for (int g = tid; g < npw; g += nt) {
+                for (int g = g0 + tid; g < g1; g += nt) {
                     double2 rv[kMaxEll + 1], uv[kMaxEll + 1];
 #pragma unroll
                     for (int t = 0; t <= kMaxEll; ++t) {
@@ -443,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
                     U[0][g] = u0;
                     acc[0].x += cabs2(r0);
                 }
-                block_sum<1>(acc, red, s_dot);
+                part_sum<1>(P, Rd, acc, s_dot);
             }
             if (tid == 0) S.rnorm = sqrt(s_dot[0].x);
             __syncthreads();
@@ -477,17 +483,19 @@ __global__ void __launch_bounds__(kThreads, 1) ms_solve_kernel(Plan P, SolveArgs
         }
         __syncthreads();
         if (pre) {   // the iterate solves A D y = b: x = D y
-            for (int g = tid; g < npw; g += nt) X[g] = cscal(X[g], pre[g]);
+            for (int g = g0 + tid; g < g1; g += nt) X[g] = cscal(X[g], pre[g]);
         }
-        for (int j = tid; j < ns; j += nt) {
-            int s = st[j];
-            if (s < 0) {
-                s = S.fail ? S.fail : SGW_PAIR_MAXITER;
-                mv[j] = mvc;
+        if (q.rank == 0) {   // every rank holds the same per-shift results; rank 0 writes them
+            for (int j = tid; j < ns; j += nt) {
+                int s = st[j];
+                if (s < 0) {
+                    s = S.fail ? S.fail : SGW_PAIR_MAXITER;
+                    mv[j] = mvc;
+                }
+                A.out_status[(size_t)r * ns + j] = s;
+                A.out_mv[(size_t)r * ns + j] = mv[j];
+                A.out_res[(size_t)r * ns + j] = est[j];
             }
-            A.out_status[(size_t)r * ns + j] = s;
-            A.out_mv[(size_t)r * ns + j] = mv[j];
-            A.out_res[(size_t)r * ns + j] = est[j];
         }
     }
 }
@@ -1252,26 +1260,32 @@ cudaError_t launch_owned(const void* kernel, const Plan& P, int owners, int thre
     return cudaLaunchKernelExC(&cfg, kernel, args);
 }
 
+// Vector owners of the BiCGstab kernel resident at once (CTAs, or clusters when the box is
+// split), at most nrhs and at least one.
 cudaError_t solve_grid(const Plan& P, int nshift, int nrhs, int* grid) {
-    if (P.csize > 1) return cudaErrorNotSupported;
     int g = 0;
-    cudaError_t e = resident_grid((const void*)ms_solve_kernel, solve_smem_bytes(P, nshift), &g, kThreads);
+    cudaError_t e = owner_capacity((const void*)ms_solve_kernel, P, kThreads, solve_smem_bytes(P, nshift), &g);
     if (e != cudaSuccess) return e;
     *grid = g < nrhs ? g : nrhs;
     if (*grid < 1) *grid = 1;
     return cudaSuccess;
 }
 
+// grid: vector owners (solve_grid); one CTA each, or one cluster of P0.csize CTAs each.
 cudaError_t launch_solve(const Plan& P0, const SolveArgs& a, int grid, cudaStream_t st) {
-    if (P0.csize > 1) return cudaErrorNotSupported;   // BiCGstab runs one CTA per vector
     const Plan P = tuned_plan(P0, bicg_extra(a.nshift), 16);
     const int smem = solve_smem_bytes(P0, a.nshift);
     cudaError_t e = allow_max_smem((const void*)ms_solve_kernel);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    ms_solve_kernel<<<grid, kThreads, smem, st>>>(P, a);
-    return cudaGetLastError();
+    if (P.csize == 1) {
+        ms_solve_kernel<<<grid, kThreads, smem, st>>>(P, a);
+        return cudaGetLastError();
+    }
+    SolveArgs aa = a;
+    void* args[] = {(void*)&P, (void*)&aa};
+    return launch_owned((const void*)ms_solve_kernel, P, grid, kThreads, smem, st, args);
 }
 
 namespace {

@@ -311,24 +311,6 @@ __device__ __noinline__ void lanczos_rhs(const Plan& P, const LanczosArgs& A, un
     }
 }
 
-// The next work item of the launch for this owner: rank 0 of a cluster takes it from the
-// queue and every rank reads it (rank 0 overwrites it, or exits, only after all have read).
-__device__ __forceinline__ int next_item(const Plan& P, int* counter) {
-    __shared__ int s_r;
-    if (P.csize == 1) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
-        __syncthreads();
-        return s_r;
-    }
-    cg::cluster_group cl = cg::this_cluster();
-    if (cl.block_rank() == 0 && threadIdx.x == 0) s_r = atomicAdd(counter, 1);
-    cl.sync();
-    const int r = *cl.map_shared_rank(&s_r, 0u);
-    cl.sync();
-    return r;
-}
-
 // One system: a work queue hands its right-hand sides to the owners.
 template <class Ar, int NT>
 __global__ void __launch_bounds__(NT, 1) lanczos_solve_kernel(Plan P, LanczosArgs A) {

@@ -145,6 +145,24 @@ __device__ __forceinline__ Part make_part(const Plan& P) {
     return q;
 }
 
+// The next work item of the launch for this owner: rank 0 of a cluster takes it from the
+// queue and every rank reads it (rank 0 overwrites it, or exits, only after all have read).
+__device__ __forceinline__ int next_item(const Plan& P, int* counter) {
+    __shared__ int s_r;
+    if (P.csize == 1) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
+        __syncthreads();
+        return s_r;
+    }
+    cg::cluster_group cl = cg::this_cluster();
+    if (cl.block_rank() == 0 && threadIdx.x == 0) s_r = atomicAdd(counter, 1);
+    cl.sync();
+    const int r = *cl.map_shared_rank(&s_r, 0u);
+    cl.sync();
+    return r;
+}
+
 // Scratch of the block and cluster reductions.  Cluster partial sums alternate between two
 // buffers (par), so one cluster barrier per reduction suffices: a rank writes buffer par of
 // reduction n + 2 only after the barrier of reduction n + 1, which every rank reaches after

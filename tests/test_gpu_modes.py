@@ -5,7 +5,9 @@
 * the FP32 (complex64) inner solve inside FP64 iterative refinement;
 * the certificate-aware stopping rule (every pair's |r| / (eta |x|) <= 1e-8);
 * resuming from given solutions (x0) and preconditioned corrections with the learned
-  diagonal, including the fall back to the plain diagonal.
+  diagonal, including the fall back to the plain diagonal;
+* the BiCGstab(ell) kernel (multishift, per-shift and preconditioned corrections) on
+  cluster-split boxes.
 """
 import numpy as np
 import pytest
@@ -131,6 +133,103 @@ def test_cluster_residual_and_green(sgw, cfg1):
     assert ok
     ref = O.green_columns(h, cols, z)
     assert _relerr(g, ref).max() < TOL_SOLVE
+
+
+def _theta(seed=3):
+    """Perceptron parameters with a non-zero last layer (a learned diagonal that differs from
+    the plain scaling)."""
+    from oracle import mlp_oracle as M
+    rng = np.random.default_rng(seed)
+    th = M.init_params(rng)
+    th[-(M.N_H + 1):] = (0.05 * rng.standard_normal(M.N_H + 1)).astype(np.float32)
+    return th
+
+
+def test_cluster_bicgstab_multishift(sgw, cfg1):
+    """The shifted BiCGstab(ell) kernel on a two-CTA split of config 1: every pair converges to
+    the LU's answer and to the one-CTA kernel's."""
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[:6]
+    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, cfg1.gp_miller)[:6]
+    e_ref = cfg1.e_ref(0)[:6]
+    d1, _, ok1 = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, method="bicgstab")
+    assert skq.set_split(2)[0] == 2
+    d2, rep2, ok2 = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, method="bicgstab")
+    assert ok1 and ok2, rep2["status"]
+    h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
+    ref = O.solve_shifted(h, kp.psi_kq, rref, e_ref, cfg1.omega, cfg1.eta)
+    assert _relerr(d2, ref).max() < TOL_SOLVE
+    assert _relerr(d2, d1).max() < 2 * TOL_SOLVE
+
+
+@pytest.mark.parametrize("precond", ["none", "plain", "learned"])
+def test_cluster_pershift_solves(sgw, cfg1, precond):
+    """Per-shift right-preconditioned BiCGstab on a two-CTA split of config 1: the LU's answers
+    (the diagonal changes the route, not the answer)."""
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    assert skq.set_split(2)[0] == 2
+    rows = np.array([0, 5, 13, 20, 27, 31])
+    cols = np.array([0, 3, 8, 11, 14, 15])
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[rows]
+    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, cfg1.gp_miller)[rows]
+    e = cfg1.e_ref(0)[rows]
+    om = cfg1.omega[cols]
+    mlp = sgw.MLP(_theta()) if precond == "learned" else None
+    x, rep, ok = skq.solve_pershift(rhs, e, om, cfg1.eta, tol=1e-10, precond=precond, mlp=mlp)
+    assert ok, rep["status"]
+    assert rep["rel_res"].max() <= 1e-10
+    h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
+    ref = np.stack([O.solve_shifted(h, kp.psi_kq, rref[i:i + 1], e[i:i + 1], om[i:i + 1], cfg1.eta)[0, 0]
+                    for i in range(len(rows))])
+    assert _relerr(x, ref).max() < TOL_SOLVE
+
+
+def test_cluster_pershift_config2(sgw, cfg2, h2):
+    """Per-shift solves with the plain diagonal on a four-CTA split of config 2 (1 647 plane
+    waves, frequencies from the bottom to the top of the 0-60 eV window) against the LU."""
+    kp = cfg2.kpoints[0]
+    skq, sk = _systems(sgw, cfg2)
+    assert skq.set_split(4)[0] == 4
+    npert = cfg2.n_pert
+    rows = np.array([0, 5, npert + 3, 7 * npert + 31])
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg2.gp_miller)[rows]
+    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, cfg2.gp_miller)[rows]
+    e = cfg2.e_ref(0)[rows]
+    om = cfg2.omega[[0, 20, 41, 63]]
+    x, rep, ok = skq.solve_pershift(rhs, e, om, cfg2.eta, tol=1e-10, precond="plain")
+    assert ok, rep["status"]
+    ref = np.stack([O.solve_shifted(h2, kp.psi_kq, rref[i:i + 1], e[i:i + 1], om[i:i + 1], cfg2.eta)[0, 0]
+                    for i in range(len(rows))])
+    assert _relerr(x, ref).max() < TOL_SOLVE
+
+
+def test_cluster_preconditioned_corrections(sgw, cfg1):
+    """Resuming from a perturbed solution on a two-CTA split: corrections by the learned
+    diagonal (untrained network: the plain scaling), the same with the fall back forced by a
+    plain budget of one H application, and by the plain diagonal all reach the LU."""
+    from oracle import mlp_oracle as M
+    kp = cfg1.kpoints[0]
+    skq, sk = _systems(sgw, cfg1)
+    assert skq.set_split(2)[0] == 2
+    rows = np.arange(1, 32, 4)
+    rhs = skq.make_rhs(sk, kp.psi_k, cfg1.gp_miller)[rows]
+    rref = O.make_rhs(kp.miller_kq, kp.miller_k, kp.psi_k, cfg1.gp_miller)[rows]
+    e_ref = cfg1.e_ref(0)[rows]
+    h, _, _ = O.dense_h_inst(cfg1, kp.kq_frac)
+    ref = O.solve_shifted(h, kp.psi_kq, rref, e_ref, cfg1.omega, cfg1.eta)
+    x0 = ref * (1 + 1e-3 * np.random.default_rng(6).standard_normal(ref.shape))
+    mlp = sgw.MLP(M.init_params(np.random.default_rng(0)))
+    d, rep, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, tol=1e-10, x0=x0, precond="learned", mlp=mlp)
+    assert ok and _relerr(d, ref).max() < TOL_SOLVE
+    assert rep["fallbacks"][0] == 0
+    d, rep, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, tol=1e-10, x0=x0, precond="learned", mlp=mlp,
+                                   plain_budget=1)
+    assert ok and _relerr(d, ref).max() < TOL_SOLVE
+    assert rep["fallbacks"][0] > 0
+    d, rep, ok = skq.solve_shifted(rhs, e_ref, cfg1.omega, cfg1.eta, tol=1e-10, x0=x0, precond="plain")
+    assert ok and _relerr(d, ref).max() < TOL_SOLVE
 
 
 # ------------------------------------------------------------ FP32 inner + FP64 refinement
