@@ -9,6 +9,7 @@ H-application counts of per-shift solves on held-out systems with the plain and 
 preconditioner (the residual decides convergence, so only counts may change).
 
     python -m paper_1812_03717_gb300.learned_precond --train-seeds 24 --eval-seeds 4 --out weights.npy
+    python -m paper_1812_03717_gb300.learned_precond --config2-pairs 64 --eval-seeds 0 --supercell-pairs 15
 """
 from __future__ import annotations
 
@@ -106,6 +107,78 @@ def training_set(P, seeds, pairs_per_seed=32, tol=1e-8, deltas=DELTAS, make=None
     return torch.cat(feats), torch.cat(targets), stats
 
 
+def config2_rows(P, seed=0, pairs_per_k=64, tol=1e-8, deltas=DELTAS, stats=None):
+    """Training rows from the k-points of the 8-atom cubic cell (the config-2 generator):
+    pairs_per_k seeded (right-hand side, frequency) pairs per k-point, as in training_set."""
+    import torch
+    import instances as I
+    inst = I.config2(seed)
+    feats, targets = [], []
+    for ik in range(len(inst.kpoints)):
+        s, rhs = _system(P, inst, ik)
+        rng = np.random.default_rng(20_000 + 10 * seed + ik)
+        r = rng.integers(0, rhs.shape[0], pairs_per_k)
+        j = rng.integers(0, len(inst.omega), pairs_per_k)
+        rp = rhs[torch.as_tensor(r, device=rhs.device)].contiguous()
+        f, t = pairs_rows(s, rp, inst.e_ref(ik)[r], inst.omega[j], inst.eta, tol, deltas, stats)
+        feats.append(f)
+        targets.append(t)
+        s.close()
+    return torch.cat(feats), torch.cat(targets)
+
+
+def evaluate_supercell(P, mlp, n_pairs=15, max_matvec=6000, tol=1e-10, seed=0):
+    """Per-shift solves of n_pairs seeded (band, G_p, omega) pairs of the 64-atom supercell
+    (18 277 plane waves, the 72^3 box split over a thread-block cluster), with the plain and
+    with the learned diagonal, each capped at max_matvec H applications per pair.  A pair counts
+    as solved when rel_res <= tol and its certificate <= 1e-8; the H-application gain is taken
+    over the pairs both preconditioners solve, and their solutions are compared."""
+    import torch
+    import instances as I
+    inst = I.config3()
+    kp = inst.kpoints[0]
+    rng = np.random.default_rng(30_000 + seed)
+    v = rng.integers(0, inst.n_occ, n_pairs)
+    p = rng.integers(0, inst.n_pert, n_pairs)
+    j = rng.integers(0, len(inst.omega), n_pairs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = P.System.from_instance(inst, kp.kq_frac)
+    sk = P.System.from_instance(inst, kp.k_frac)
+    s.set_occupied(torch.from_numpy(kp.psi_kq).to(dev), kp.eps_kq)
+    bands = np.unique(v)
+    rhs_b = s.make_rhs(sk, torch.from_numpy(kp.psi_k[bands]).to(dev), inst.gp_miller)
+    sk.close()
+    rows = np.searchsorted(bands, v) * inst.n_pert + p
+    rp = rhs_b[torch.as_tensor(rows, device=dev)].contiguous()
+    del rhs_b
+    e = kp.eps_k[v]
+    om = inst.omega[j]
+    out = {"pairs": n_pairs, "n_pw": s.n_pw, "cluster_ctas": s.split()[0], "max_matvec": max_matvec,
+           "omega_ev": (om * 27.211386245988).round(2).tolist()}
+    sol = {}
+    for mode in ("plain", "learned"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, rep, _ = s.solve_pershift(rp, e, om, inst.eta, tol=tol, precond=mode,
+                                     mlp=mlp if mode == "learned" else None, max_matvec=max_matvec)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ok = (rep["status"] == 0) & (rep["rel_res"] <= tol) & (rep["cert"] <= 1e-8)
+        sol[mode] = (x, ok, rep["matvecs"].astype(np.int64))
+        out[mode] = {"seconds": dt, "solved": int(ok.sum()), "solves_per_s": float(ok.sum()) / dt,
+                     "matvecs": rep["matvecs"].tolist(),
+                     "max_rel_res_solved": float(rep["rel_res"][ok].max()) if ok.any() else None}
+    both = sol["plain"][1] & sol["learned"][1]
+    out["solved_by_both"] = int(both.sum())
+    if both.any():
+        out["matvec_gain"] = float(sol["plain"][2][both].mean() / sol["learned"][2][both].mean())
+        b = torch.as_tensor(np.flatnonzero(both), device=dev)
+        x0, x1 = sol["plain"][0][b], sol["learned"][0][b]
+        out["max_diff_solved"] = float((torch.linalg.norm(x1 - x0, dim=1) / torch.linalg.norm(x0, dim=1)).max())
+    s.close()
+    return out
+
+
 def train(P, feats, targets, steps=400, lr=3e-3, batch=8192, seed=0, params=None):
     import torch
     mlp = P.MLP(init_params(seed) if params is None else params)
@@ -151,23 +224,38 @@ def main():
     ap.add_argument("--train-seeds", type=int, default=24)
     ap.add_argument("--eval-seeds", type=int, default=4)
     ap.add_argument("--pairs", type=int, default=32)
+    ap.add_argument("--config2-pairs", type=int, default=0,
+                    help="also train on this many pairs per k-point of the 8-atom cubic cell")
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--supercell-pairs", type=int, default=0,
+                    help="evaluate on this many seeded pairs of the 64-atom supercell")
+    ap.add_argument("--supercell-cap", type=int, default=6000, help="H applications per supercell pair")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
+    import torch
     import paper_1812_03717_gb300 as P
     t0 = time.time()
     feats, targets, stats = training_set(P, range(args.train_seeds), args.pairs)
+    if args.config2_pairs > 0:
+        f2, t2_ = config2_rows(P, 0, args.config2_pairs, stats=stats)
+        feats, targets = torch.cat([feats, f2]), torch.cat([targets, t2_])
     t1 = time.time()
     mlp, losses = train(P, feats, targets, steps=args.steps, lr=args.lr)
     t2 = time.time()
-    ev = evaluate(P, mlp, range(1000, 1000 + args.eval_seeds), args.pairs)
+    line = {"rows": int(feats.shape[0]), "data": stats, "loss_first": losses[0], "loss_last": losses[-1]}
+    if args.eval_seeds > 0:
+        ev = evaluate(P, mlp, range(1000, 1000 + args.eval_seeds), args.pairs)
+        line["eval"] = {k: v for k, v in ev.items() if k not in ("plain", "learned")}
     t3 = time.time()
+    print(json.dumps(line), flush=True)
+    if args.supercell_pairs > 0:
+        line["supercell"] = evaluate_supercell(P, mlp, args.supercell_pairs, args.supercell_cap)
+    t4 = time.time()
     if args.out:
         np.save(args.out, mlp.params)
-    print(json.dumps({"rows": int(feats.shape[0]), "data": stats, "loss_first": losses[0], "loss_last": losses[-1],
-                      "eval": {k: v for k, v in ev.items() if k not in ("plain", "learned")},
-                      "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2}}))
+    line["seconds"] = {"data": t1 - t0, "train": t2 - t1, "eval": t3 - t2, "supercell": t4 - t3}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
