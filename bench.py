@@ -859,7 +859,7 @@ def main():
     ap.add_argument("--variant-warmup", type=int, default=1, help="warm-up steps of the non-headline variants")
     ap.add_argument("--rhs-per-step", type=int, default=0,
                     help="right-hand sides per step (0: one per vector owner resident on the GPU)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 8-atom cell measurements")
