@@ -95,10 +95,12 @@ def solve_batched(items, eta, tol=1e-10, precision="fp64", threads=0, max_matvec
         rhs = _c128(it["rhs"])
         e_ref = np.ascontiguousarray(it["e_ref"], dtype=np.float64)
         om = np.ascontiguousarray(it["omega"], dtype=np.float64)
-        nr, nw = rhs.shape[0], len(om)
+        nr, nw = _need_rows(rhs, it["sys"].n_pw, "rhs"), len(om)
+        _need_shape(e_ref, (nr,), "e_ref")
         out = it.get("out")
         if out is None:
             out = _like(rhs, (nr, nw, it["sys"].n_pw))
+        _need_out(out, (nr, nw, it["sys"].n_pw))
         rep, crep = _report(nr, nw)
         keep += [rhs, e_ref, om, out, crep]
         citems.append(_BatchItem(it["sys"]._h.value, nr, _ptr(rhs), e_ref.ctypes.data, nw, om.ctypes.data, _ptr(out),
@@ -206,6 +208,33 @@ def _like(x, shape):
         import torch
         return torch.empty(shape, dtype=torch.complex128, device=x.device)
     return np.empty(shape, dtype=np.complex128)
+
+
+def _need_shape(x, shape, name):
+    """The C ABI sees pointers only: every buffer it reads or writes must have exactly the
+    shape the sizes passed beside it describe (a smaller one would be read or written past
+    its end on the device)."""
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(x.shape)}")
+
+
+def _need_out(out, shape, name="out"):
+    """A caller's result buffer: complex128 of exactly `shape` (the library writes all of it)."""
+    if _is_torch(out):
+        import torch
+        ok = out.dtype == torch.complex128
+    else:
+        ok = getattr(out, "dtype", None) == np.complex128
+    if not ok:
+        raise TypeError(f"{name} must be complex128")
+    _need_shape(out, shape, name)
+
+
+def _need_rows(x, ncols, name):
+    """A [rows][ncols] complex128 buffer (already converted by _c128); returns rows."""
+    if x.ndim != 2 or x.shape[1] != ncols:
+        raise ValueError(f"{name} must be [rows][{ncols}], got shape {tuple(x.shape)}")
+    return x.shape[0]
 
 
 def _stream_of(x, stream):
@@ -330,33 +359,41 @@ class System:
     def set_occupied(self, psi_v, eps_v):
         psi = _c128(psi_v)
         eps = np.ascontiguousarray(eps_v, dtype=np.float64)
+        _need_shape(psi, (len(eps), self.n_pw), "psi_v")
         _check(load().sgw_set_occupied(self._h, len(eps), _ptr(psi), eps.ctypes.data))
         self.nocc = len(eps)
 
     def make_rhs(self, sys_k, psi_k, gp_miller, out=None, stream=None):
         psi = _c128(psi_k)
         gp = np.ascontiguousarray(gp_miller, dtype=np.int32).reshape(-1, 3)
-        n_v = psi.shape[0]
+        n_v = _need_rows(psi, sys_k.n_pw, "psi_k")
         if out is None:
             out = _like(psi, (n_v * len(gp), self.n_pw))
+        _need_out(out, (n_v * len(gp), self.n_pw))
         _check(load().sgw_make_rhs(self._h, sys_k._h, n_v, _ptr(psi), len(gp), gp.ctypes.data, _ptr(out),
                                    _stream_of(psi, stream)))
         return out
 
     def apply_h(self, x, out=None, precision="fp64", stream=None):
         x = _c128(x)
+        if x.ndim not in (1, 2) or x.shape[-1] != self.n_pw:
+            raise ValueError(f"x must be [nvec][{self.n_pw}] or [{self.n_pw}], got shape {tuple(x.shape)}")
         nvec = x.shape[0] if x.ndim == 2 else 1
         if out is None:
             out = _like(x, x.shape)
+        _need_out(out, x.shape)
         _check(load().sgw_apply_h(self._h, nvec, _ptr(x), _ptr(out), _PREC[precision], _stream_of(x, stream)))
         return out
 
     def apply_shifted(self, x, z, out=None, precision="fp64", stream=None):
         x = _c128(x)
+        if x.ndim not in (1, 2) or x.shape[-1] != self.n_pw:
+            raise ValueError(f"x must be [nvec][{self.n_pw}] or [{self.n_pw}], got shape {tuple(x.shape)}")
         nvec = x.shape[0] if x.ndim == 2 else 1
         zz = np.ascontiguousarray(np.broadcast_to(np.asarray(z, dtype=np.complex128), (nvec,)))
         if out is None:
             out = _like(x, x.shape)
+        _need_out(out, x.shape)
         _check(load().sgw_apply_shifted(self._h, nvec, _ptr(x), zz.ctypes.data, _ptr(out), _PREC[precision],
                                         _stream_of(x, stream)))
         return out
@@ -368,12 +405,14 @@ class System:
         target (0: the library default 1e-8, negative: not checked); x0: initial solutions like
         dpsi (resume); precond: "none" / "plain" / "learned" for the per-shift corrections."""
         rhs = _c128(rhs)
-        nrhs = rhs.shape[0]
+        nrhs = _need_rows(rhs, self.n_pw, "rhs")
         e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
         omega = np.ascontiguousarray(omega, dtype=np.float64)
+        _need_shape(e_ref, (nrhs,), "e_ref")
         nw = len(omega)
         if out is None:
             out = _like(rhs, (nrhs, nw, self.n_pw))
+        _need_out(out, (nrhs, nw, self.n_pw))
         if x0 is not None:
             x0 = _c128(x0)
             if tuple(x0.shape) != (nrhs, nw, self.n_pw):
@@ -403,6 +442,7 @@ class System:
                 out = torch.empty((nc, nz, self.n_pw), dtype=torch.complex128, device=device)
             else:
                 out = np.empty((nc, nz, self.n_pw), dtype=np.complex128)
+        _need_out(out, (nc, nz, self.n_pw))
         rep, crep = _report(nc, nz)
         opts = _opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
                      _stream_of(out, stream), float(cert_tol))
@@ -420,16 +460,17 @@ class System:
         eps_v = np.ascontiguousarray(eps_v, dtype=np.float64)
         omega = np.ascontiguousarray(omega, dtype=np.float64)
         n_v = len(eps_v)
-        if n_v == 0 or rhs.shape[0] % n_v:
+        nr = _need_rows(rhs, self.n_pw, "rhs")
+        if n_v == 0 or nr % n_v:
             raise ValueError("rhs rows must be n_v * n_pert")
-        n_p, nw = rhs.shape[0] // n_v, len(omega)
+        n_p, nw = nr // n_v, len(omega)
         if out is None:
             if _is_torch(rhs):
                 import torch
                 out = torch.zeros((n_p, n_p, nw), dtype=torch.complex128, device=rhs.device)
             else:
                 out = np.zeros((n_p, n_p, nw), dtype=np.complex128)
-        nr = rhs.shape[0]
+        _need_out(out, (n_p, n_p, nw))
         rep, crep = _report(nr, 2 * nw)
         opts = _opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
                      _stream_of(rhs, stream), float(cert_tol))
@@ -448,16 +489,17 @@ class System:
         wc = np.asarray(w, dtype=np.complex128).ravel()
         ww = np.ascontiguousarray(np.column_stack([wc.real, wc.imag]))
         n_v = len(eps_v)
-        if n_v == 0 or rhs.shape[0] % n_v:
+        nr = _need_rows(rhs, self.n_pw, "rhs")
+        if n_v == 0 or nr % n_v:
             raise ValueError("rhs rows must be n_v * n_pert")
-        n_p, nw = rhs.shape[0] // n_v, len(wc)
+        n_p, nw = nr // n_v, len(wc)
         if out is None:
             if _is_torch(rhs):
                 import torch
                 out = torch.zeros((n_p, n_p, nw), dtype=torch.complex128, device=rhs.device)
             else:
                 out = np.zeros((n_p, n_p, nw), dtype=np.complex128)
-        nr = rhs.shape[0]
+        _need_out(out, (n_p, n_p, nw))
         rep, crep = _report(nr, 2 * nw)
         opts = _opts(METHOD_LANCZOS, _PREC[precision], 4, -1, int(max_matvec), int(max_refine), int(threads),
                      _stream_of(rhs, stream), float(cert_tol))
@@ -471,7 +513,9 @@ class System:
         dpsi = _c128(dpsi)
         e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
         omega = np.ascontiguousarray(omega, dtype=np.float64)
-        nrhs, nw = rhs.shape[0], len(omega)
+        nrhs, nw = _need_rows(rhs, self.n_pw, "rhs"), len(omega)
+        _need_shape(e_ref, (nrhs,), "e_ref")
+        _need_shape(dpsi, (nrhs, nw, self.n_pw), "dpsi")
         rel = np.zeros((nrhs, nw))
         cert = np.zeros((nrhs, nw))
         _check(load().sgw_residual(self._h, nrhs, _ptr(rhs), e_ref.ctypes.data, nw, omega.ctypes.data, float(eta),
@@ -511,12 +555,15 @@ class System:
         """Independent single-shift solves of pairs (rhs[i], z_i = e_ref[i] + omega[i] + i eta) with a
         diagonal preconditioner; returns (x [npairs][n_pw], report, converged)."""
         rhs = _c128(rhs)
-        n = rhs.shape[0]
+        n = _need_rows(rhs, self.n_pw, "rhs")
         e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
         omega = np.ascontiguousarray(omega, dtype=np.float64)
+        _need_shape(e_ref, (n,), "e_ref")
+        _need_shape(omega, (n,), "omega")
         dl = None if delta is None else np.ascontiguousarray(np.broadcast_to(delta, (n,)), dtype=np.float64)
         if out is None:
             out = _like(rhs, (n, self.n_pw))
+        _need_out(out, (n, self.n_pw))
         rep, crep = _report(n, None)
         opts = _opts(METHOD_BICGSTAB, PREC_FP64, int(ell), -1, int(max_matvec), -1, 0, _stream_of(rhs, stream))
         st = load().sgw_solve_pershift(self._h, n, _ptr(rhs), e_ref.ctypes.data, omega.ctypes.data, float(eta),
@@ -528,10 +575,12 @@ class System:
 
     def precond_diag(self, rhs, e_ref, omega, eta, precond="plain", delta=None, mlp=None):
         rhs = _c128(rhs)
-        n = rhs.shape[0]
+        n = _need_rows(rhs, self.n_pw, "rhs")
         d = np.empty((n, self.n_pw))
         e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
         omega = np.ascontiguousarray(omega, dtype=np.float64)
+        _need_shape(e_ref, (n,), "e_ref")
+        _need_shape(omega, (n,), "omega")
         dl = None if delta is None else np.ascontiguousarray(np.broadcast_to(delta, (n,)), dtype=np.float64)
         _check(load().sgw_precond_diag(self._h, n, _ptr(rhs), e_ref.ctypes.data, omega.ctypes.data, float(eta),
                                        _PRECOND[precond], dl.ctypes.data if dl is not None else None,
@@ -541,12 +590,16 @@ class System:
     def training_rows(self, rhs, e_ref, omega, eta, delta):
         """(feats [n*n_pw][4], targets [n*n_pw]) float32 CUDA tensors; rhs a CUDA tensor."""
         import torch
-        n = rhs.shape[0]
+        if not (_is_torch(rhs) and rhs.is_cuda and rhs.is_contiguous() and rhs.dtype == torch.complex128):
+            raise TypeError("training_rows takes a contiguous complex128 CUDA tensor rhs")
+        n = _need_rows(rhs, self.n_pw, "rhs")
         rows = n * self.n_pw
         feats = torch.empty((rows, 4), dtype=torch.float32, device=rhs.device)
         targets = torch.empty(rows, dtype=torch.float32, device=rhs.device)
         e_ref = np.ascontiguousarray(e_ref, dtype=np.float64)
         omega = np.ascontiguousarray(omega, dtype=np.float64)
+        _need_shape(e_ref, (n,), "e_ref")
+        _need_shape(omega, (n,), "omega")
         dl = np.ascontiguousarray(np.broadcast_to(delta, (n,)), dtype=np.float64)
         _check(load().sgw_training_rows(self._h, n, rhs.data_ptr(), e_ref.ctypes.data, omega.ctypes.data, float(eta),
                                         dl.ctypes.data, feats.data_ptr(), targets.data_ptr(), _stream_of(rhs, None)))
