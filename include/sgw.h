@@ -95,11 +95,14 @@ sgw_status sgw_create_system(const sgw_cell* cell, double ecut_ry, const double 
                              const int fft_dims[3], const double* vloc_r, const sgw_kb* kb,
                              sgw_system** out);
 
-/* Number of plane waves; optionally the Miller triples [n_pw][3] and kinetic energies
- * |k+G|^2 / 2 (Ha) [n_pw] in canonical order (host buffers, or NULL). */
+/* The plane-wave basis of Eq. 1 (Sec. 2.1) built by sgw_create_system: the number of plane
+ * waves and, optionally, the Miller triples [n_pw][3] and the kinetic energies |k+G|^2 / 2
+ * (Ha) [n_pw] in canonical order (host buffers, or NULL).  SGW_EINVAL for a NULL sys. */
 sgw_status sgw_get_gvectors(const sgw_system* sys, int* n_pw, int* miller, double* kin);
 
-/* Sphere -> box map, entry g = ((m1 mod N1) N2 + (m2 mod N2)) N3 + (m3 mod N3), host int[n_pw]. */
+/* Sphere -> FFT box map of the H application by Fourier transforms (Sec. 2.1): entry
+ * g = ((m1 mod N1) N2 + (m2 mod N2)) N3 + (m3 mod N3), written to the host int[n_pw]
+ * `map`.  SGW_EINVAL for a NULL argument. */
 sgw_status sgw_get_box_map(const sgw_system* sys, int* map);
 
 /* Split of the on-chip FFT box (an implementation choice the paper has no counterpart for:
@@ -435,9 +438,15 @@ sgw_status sgw_training_rows(sgw_system* sys, int npairs, const void* rhs, const
                              const double* omega, double eta, const double* delta, float* feats,
                              float* targets, void* stream);
 
+/* Releases a system and every device buffer it owns (resource management of this ABI; the
+ * paper has no counterpart).  NULL is a no-op.  It makes the system's device current and
+ * synchronises it first, so work still in flight on the system finishes before its memory is
+ * freed. */
 void sgw_destroy_system(sgw_system* sys);
 
-/* Message of the last failing call on this host thread ("" if none). */
+/* Message of the last failing call on this host thread ("" if none); the pointer stays
+ * valid until the thread's next call into the library (error reporting of this ABI; the
+ * paper has no counterpart). */
 const char* sgw_last_error(void);
 
 #ifdef __cplusplus
