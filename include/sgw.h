@@ -25,7 +25,9 @@
  * device pointer of the current device; the library detects which.  The library copies
  * what it keeps (the system owns its device copies); the caller owns every buffer it
  * passes.  Work is ordered on the stream given (NULL = the legacy default stream); calls
- * that return results to host memory synchronise that stream before returning.
+ * that return results to host memory synchronise that stream before returning.  A call on a
+ * system makes the system's device (the current device at sgw_create_system) current while
+ * it runs and gives the caller's current device back before it returns.
  *
  * Errors: every call returns an sgw_status; nothing throws across the ABI and nothing
  * aborts.  sgw_last_error() returns a message for the last failing call of this host

@@ -94,6 +94,28 @@ sgw_status cuda_fail(cudaError_t e, const char* what) {
         if (e__ != cudaSuccess) return cuda_fail(e__, what); \
     } while (0)
 
+// Makes a system's device current for the rest of an entry point and gives the caller's
+// current device back when it returns (work already queued on a stream is unaffected).
+// Declared before anything whose destructor frees device memory, so those frees run while
+// the system's device is still current.
+struct DeviceScope {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != dev) err = cudaSetDevice(dev);
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 bool is_device_ptr(const void* p) {
     if (p == nullptr) return false;
     cudaPointerAttributes at;
@@ -781,7 +803,8 @@ sgw_status sgw_set_split(sgw_system* s, int csize) {
     g_err.clear();
     if (!s) return fail(SGW_EINVAL, "NULL system");
     if (csize < 0 || csize > kMaxCluster) return fail(SGW_EINVAL, "csize must be in [0, 16]");
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     SGW_CUDA(cudaDeviceSynchronize(), "set_split");   // the tables may be in use by queued work
     const int prev = s->forced_csize;
     s->forced_csize = csize;
@@ -815,7 +838,8 @@ sgw_status sgw_solve_capacity(const sgw_system* s, int nomega, int precision, in
         return fail(SGW_EINVAL, "unknown precision");
     const Plan& plan = precision == SGW_PREC_FP32 ? s->plan8 : s->plan;
     if (plan.csize == 0) return fail(SGW_EUNSUPPORTED, "the FFT box does not fit on chip in FP32");
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     int n = 0;
     SGW_CUDA(lanczos_capacity(plan, nomega, threads, precision, &n), "solver occupancy");
     *owners = n;
@@ -828,7 +852,8 @@ sgw_status sgw_set_occupied(sgw_system* s, int n_occ, const void* psi_v, const d
     if (n_occ < 0 || n_occ > 4096) return fail(SGW_EINVAL, "n_occ out of range");
     if (n_occ > 0 && (!psi_v || !eps_v)) return fail(SGW_EINVAL, "NULL psi_v or eps_v");
     if (n_occ > 0 && !finite_all(eps_v, n_occ)) return fail(SGW_EINVAL, "non-finite eps_v");
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     const size_t bytes = sizeof(double2) * (size_t)n_occ * s->npw;
     double2* d_new = nullptr;
     if (n_occ > 0) {
@@ -942,7 +967,8 @@ static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const dou
     if (nvec == 0) return SGW_OK;
     if (project && s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
     if (project && (!z || !finite_all(z, 2 * (size_t)nvec))) return fail(SGW_EINVAL, "bad shifts");
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)nvec * s->npw;
     Staged in, out;
@@ -1450,7 +1476,8 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
     if (nrhs == 0) return SGW_OK;
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in, out;
     sgw_status r;
@@ -1495,7 +1522,8 @@ sgw_status sgw_solve_batched(int nitems, const sgw_batch_item* items, double eta
             return fail(SGW_EUNSUPPORTED, "too many frequencies for the on-chip shift state");
     }
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
-    SGW_CUDA(cudaSetDevice(dev), "cudaSetDevice");
+    DeviceScope dscope(dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     const int es = prec_bytes(precision);
     const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : 16384;
     // every item's buffers on the device
@@ -1665,7 +1693,8 @@ sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, con
         if (cols[c] < 0 || cols[c] >= s->npw) return fail(SGW_EINVAL, "column index outside [0, n_pw)");
     if (ncol == 0) return SGW_OK;
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     // the operator is H itself: no occupied states
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in_cols, rb, out;
@@ -1698,7 +1727,8 @@ static sgw_status density_common(sgw_system* s, int n_v, int n_pert, const void*
     const int nrhs = n_v * n_pert;
     if (nrhs == 0) return SGW_OK;
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     const size_t dn_bytes = sizeof(double2) * (size_t)n_pert * n_pert * nomega;
     Staged in, xb, dnb;
@@ -1879,7 +1909,8 @@ sgw_status sgw_precond_diag(sgw_system* s, int npairs, const void* rhs, const do
     if ((r = check_precond(precond, delta, npairs, mlp)) != SGW_OK) return r;
     if (precond == SGW_PRECOND_NONE) return fail(SGW_EINVAL, "no diagonal for SGW_PRECOND_NONE");
     if (npairs <= 0) return SGW_OK;
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in, out;
@@ -1909,7 +1940,8 @@ sgw_status sgw_training_rows(sgw_system* s, int npairs, const void* rhs, const d
     if (npairs <= 0) return SGW_OK;
     if (!is_device_ptr(rhs) || !is_device_ptr(feats) || !is_device_ptr(targets))
         return fail(SGW_EINVAL, "training rows take device buffers");
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     Carve c;
     const size_t o_e = c.take(sizeof(double) * npairs), o_o = c.take(sizeof(double) * npairs),
@@ -1955,7 +1987,8 @@ sgw_status sgw_solve_pershift(sgw_system* s, int npairs, const void* rhs, const 
     if (ell < 1 || ell > kMaxEll) return fail(SGW_EINVAL, "ell must be 1..4");
     const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : 40000;
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in, out;
     sgw_status r;
@@ -2079,7 +2112,8 @@ sgw_status sgw_residual(sgw_system* s, int nrhs, const void* rhs, const double* 
     if (s->nocc == 0) return fail(SGW_ESTATE, "sgw_set_occupied has not been called");
     const size_t np = (size_t)nrhs * nomega;
     if (np == 0) return SGW_OK;
-    SGW_CUDA(cudaSetDevice(s->dev), "cudaSetDevice");
+    DeviceScope dscope(s->dev);
+    SGW_CUDA(dscope.err, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in_r, in_x;
@@ -2114,7 +2148,7 @@ sgw_status sgw_residual(sgw_system* s, int nrhs, const void* rhs, const double* 
 
 void sgw_destroy_system(sgw_system* s) {
     if (!s) return;
-    cudaSetDevice(s->dev);
+    DeviceScope dscope(s->dev);
     cudaDeviceSynchronize();
     free_system(s);
 }
