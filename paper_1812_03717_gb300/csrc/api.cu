@@ -20,6 +20,13 @@
 #include "sgw.h"
 #include "sgw_internal.cuh"
 
+// NVTX ranges name the stages of each call for a profiler's timeline (header-only NVTX 3; a
+// no-op unless a profiler is attached).
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define SGW_HAVE_NVTX 1
+#endif
+
 namespace sgw {
 const void* solve_kernel_ptr();
 }  // namespace sgw
@@ -93,6 +100,29 @@ sgw_status cuda_fail(cudaError_t e, const char* what) {
         cudaError_t e__ = (call);                         \
         if (e__ != cudaSuccess) return cuda_fail(e__, what); \
     } while (0)
+
+// One NVTX range per stage of a call: next() closes the current stage and opens the next one;
+// the last closes when the object goes out of scope (an early error return included).
+struct Trace {
+    bool open = false;
+    explicit Trace(const char* name) { next(name); }
+    void next(const char* name) {
+#ifdef SGW_HAVE_NVTX
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+#else
+        (void)name;
+#endif
+    }
+    ~Trace() {
+#ifdef SGW_HAVE_NVTX
+        if (open) nvtxRangePop();
+#endif
+    }
+    Trace(const Trace&) = delete;
+    Trace& operator=(const Trace&) = delete;
+};
 
 // Makes a system's device current for the rest of an entry point and gives the caller's
 // current device back when it returns (work already queued on a stream is unaffected).
@@ -854,6 +884,7 @@ sgw_status sgw_set_occupied(sgw_system* s, int n_occ, const void* psi_v, const d
     if (n_occ > 0 && !finite_all(eps_v, n_occ)) return fail(SGW_EINVAL, "non-finite eps_v");
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_set_occupied");
     const size_t bytes = sizeof(double2) * (size_t)n_occ * s->npw;
     double2* d_new = nullptr;
     if (n_occ > 0) {
@@ -969,6 +1000,7 @@ static sgw_status apply_common(sgw_system* s, int nvec, const void* x, const dou
     if (project && (!z || !finite_all(z, 2 * (size_t)nvec))) return fail(SGW_EINVAL, "bad shifts");
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_apply_h");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)nvec * s->npw;
     Staged in, out;
@@ -1242,6 +1274,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
         SGW_CUDA(cudaEventCreate(&ev1), "event");
         SGW_CUDA(cudaEventRecord(ev0, st), "event");
     }
+    Trace stage("sgw: multishift pass");
     if (done) {
         // 1''. the pass ran in a packed multi-system launch: take over its per-pair results
         SGW_CUDA(cudaMemcpyAsync(w + o_mv, done->mv, sizeof(int) * np, cudaMemcpyDeviceToDevice, st), "pass copy");
@@ -1287,6 +1320,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
 
     // 2. true residual of every pair (H in FP64 for the FP64 mode, else in float-float; the
     //    assembly and the norms in FP64)
+    stage.next("sgw: FP64 residual check");
     double* d_rel = (double*)(w + o_rel);
     double* d_cert = (double*)(w + o_cert);
     const double* d_eref = (const double*)(w + o_eref);
@@ -1333,6 +1367,7 @@ static sgw_status multishift(sgw_system* s, bool project, int nrhs, const double
 
     // 3. per-shift correction solves for pairs above tol or the certificate target:
     //    A_j d = r_j, x_j += d (Lanczos in the correction precision, or preconditioned BiCGstab)
+    stage.next("sgw: correction solves");
     std::vector<int> list, mv1(chunk);
     std::vector<double> eref1(chunk), eta1(chunk), pe(chunk), po(chunk);
     int fallbacks = 0;
@@ -1478,6 +1513,7 @@ sgw_status sgw_solve_shifted(sgw_system* s, int nrhs, const void* rhs, const dou
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_solve_shifted");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in, out;
     sgw_status r;
@@ -1524,6 +1560,7 @@ sgw_status sgw_solve_batched(int nitems, const sgw_batch_item* items, double eta
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     DeviceScope dscope(dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_solve_batched");
     const int es = prec_bytes(precision);
     const int max_mv = opts && opts->max_matvec > 0 ? opts->max_matvec : 16384;
     // every item's buffers on the device
@@ -1695,6 +1732,7 @@ sgw_status sgw_solve_green(sgw_system* s, int ncol, const int* cols, int nz, con
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_solve_green");
     // the operator is H itself: no occupied states
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in_cols, rb, out;
@@ -1729,6 +1767,7 @@ static sgw_status density_common(sgw_system* s, int n_v, int n_pert, const void*
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_density_response");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     const size_t dn_bytes = sizeof(double2) * (size_t)n_pert * n_pert * nomega;
     Staged in, xb, dnb;
@@ -1911,6 +1950,7 @@ sgw_status sgw_precond_diag(sgw_system* s, int npairs, const void* rhs, const do
     if (npairs <= 0) return SGW_OK;
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_precond_diag");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in, out;
@@ -1942,6 +1982,7 @@ sgw_status sgw_training_rows(sgw_system* s, int npairs, const void* rhs, const d
         return fail(SGW_EINVAL, "training rows take device buffers");
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_training_rows");
     cudaStream_t st = (cudaStream_t)stream;
     Carve c;
     const size_t o_e = c.take(sizeof(double) * npairs), o_o = c.take(sizeof(double) * npairs),
@@ -1989,6 +2030,7 @@ sgw_status sgw_solve_pershift(sgw_system* s, int npairs, const void* rhs, const 
     cudaStream_t st = opts ? (cudaStream_t)opts->stream : nullptr;
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_solve_pershift");
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in, out;
     sgw_status r;
@@ -2114,6 +2156,7 @@ sgw_status sgw_residual(sgw_system* s, int nrhs, const void* rhs, const double* 
     if (np == 0) return SGW_OK;
     DeviceScope dscope(s->dev);
     SGW_CUDA(dscope.err, "cudaSetDevice");
+    Trace trace("sgw_residual");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t vb = sizeof(double2) * (size_t)s->npw;
     Staged in_r, in_x;
