@@ -1,4 +1,5 @@
-"""The benchmark's work model (the numerator of its roofline fraction), pinned on the CPU.
+"""The benchmark's work model (the numerator of its roofline fraction) and its clock record,
+pinned on the CPU.
 
 A float-float Lanczos step is charged for the line transforms the library runs on the pruned
 box (z-sticks through the sphere, y-columns on the x values that hold sticks, x-rows of every
@@ -63,3 +64,20 @@ def test_supercell_step_operations():
     expect = 16810 * per_line + 14 * 72 ** 3 + 18277 * (120 * (128 + 64) + 300)
     assert bench.step_df32_ops(p) == expect
     assert abs(expect - 678.48e6) < 0.01e6
+
+
+def test_clock_samples_parsing():
+    """The clock record of the timed region: median SM clock, the maximum, and every throttle
+    reason reported Active in any sample (Not Active ignored; malformed lines skipped)."""
+    lines = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2055, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "[N/A]",
+        "0, [N/A], 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    c = bench.parse_clocks(lines)
+    assert c == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c = bench.parse_clocks(lines[:1] + ["0, 1500, 2070, 1000, 0x8, Active, Not Active, Active, Not Active"])
+    assert c["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and c["sm_mhz"] == 1785.0
+    assert bench.parse_clocks([])["sm_mhz"] is None
